@@ -1,0 +1,305 @@
+#!/usr/bin/env python3
+"""Throughput of DARC's per-subject update on GB300.
+
+A step is one sweep of Algorithm 1 (arXiv 2508.10743) over the brain-MRI
+shaped synthetic cohort: every one of the 32 subjects (160x192x224 voxels)
+takes K2 = 10 subject updates (scaling and squaring with 7 squarings, warp,
+local NCC 9^3 + diffusion regulariser, hand-written adjoint, Adam), then the
+centrality activation and the NCC atlas re-estimate (20 epochs of
+mini-batch Adam, batch 4).  The metric counts subject-update voxels:
+GVoxel/s = subjects x K2 x voxels / time.
+
+The velocities start from a converged-like state (v_i = -w_i, the centred
+generating velocities), so displacements reach the 6-voxel scale of the
+workload from the first timed step.
+
+Arms: default = the CUDA library; --impl reference = the FP64 oracle on the
+host cores (bounded sample, the only other place this script runs oracle/).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="brain")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def read_traffic(kernel: str, workload: str):
+    """dram bytes per launch from a committed ncu summary (profiles/), or None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("dram_bytes_per_launch_full_size:"):
+            try:
+                return float(line.split(":", 1)[1].split()[0])
+            except ValueError:
+                return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(wl, seed):
+    """One subject update of one subject at the full workload size, in the
+    FP64 oracle; returns (seconds, voxel-updates, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_2508_10743_gb300 import synth
+    oracle.build()
+    oracle.set_num_threads(cpu_threads())
+    shape = wl.shape
+    I = synth.random_image(shape, seed, n_ell=8, radii=(4.0, 20.0)).double().numpy()
+    A = synth.random_image(shape, seed + 1, n_ell=8, radii=(4.0, 20.0)).double().numpy()
+    v = np.ascontiguousarray(synth.random_field(shape, 8.0, 6.0, seed + 2).double().numpy())
+    m, s = np.zeros_like(v), np.zeros_like(v)
+    c = wl.config
+    ocfg = oracle.make_cfg(dissim=c.dissim, window=c.ncc_window, T=c.n_squarings, lam=c.lam, lr=c.lr)
+    t0 = time.perf_counter()
+    oracle.subject_step(I, A, v, m, s, 0, ocfg)
+    dt = time.perf_counter() - t0
+    return dt, wl.voxels, oracle.num_threads()
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return 0
+    unit = "GVoxel/s"
+    times = []
+    for k in range(args.warmup + args.steps):
+        dt, vox, thr = oracle_sample(wl, 900 + k)
+        if k >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = args.steps * wl.voxels / t / 1e9
+    sample = (f"one subject update of one {wl.shape[0]}x{wl.shape[1]}x{wl.shape[2]} subject per step "
+              f"(FP64 oracle, local NCC {wl.config.ncc_window}^3, T={wl.config.n_squarings})")
+    line = {
+        "impl": "reference", "metric": "GVoxel/s per subject update (fwd+bwd)", "value": value, "unit": unit,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "subjects": 1, "shape": list(wl.shape), "inner_steps": 1},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": thr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_2508_10743_gb300 import configs
+    wl = configs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl, rank)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2508_10743_gb300 import darc, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    darc.lib()
+
+    # ---- workload: this rank's cohort (subjects are the units; weak scaling) ----
+    co = synth.make_cohort(wl.n, wl.shape, wl.seed + 7919 * rank, device=dev, keep_disp=False, **wl.gen)
+    images = co.images.contiguous()
+    cfg = wl.config
+    c = darc.Cohort(images, cfg)
+    for i in range(wl.n):
+        c.set_velocity(i, (-co.w[i]).contiguous())
+    del co
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        c.sweep(stats=False)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time, CUDA events on the launching stream ----
+    c.set_profiling(True)
+    c.profile()                         # clear
+    launches0 = c.launch_count()
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        c.sweep(stats=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = c.profile()
+    launches = c.launch_count() - launches0
+    c.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = world * wl.n * cfg.inner_steps * wl.voxels * args.steps
+    value = units / (ms / 1e3) / 1e9
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        host_imgs = images.cpu().pin_memory()
+        host_atlas = torch.empty(wl.shape, dtype=torch.float32).pin_memory()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            images.copy_(host_imgs, non_blocking=True)
+            st = c.sweep(stats=True)                 # waits; reads the step's loss
+            host_atlas.copy_(c.atlas(), non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": units / dt / 1e9, "unit": "GVoxel/s",
+               "h2d_bytes_per_step": int(images.numel() * 4),
+               "d2h_bytes_per_step": int(host_atlas.numel() * 4 + 48)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (live event times over the timed region) ----
+    peak, peak_kind = load_peaks()
+    fams = {k: v for k, v in prof.items() if k != "atlas" and v[1] > 0}
+    dom = max(fams, key=lambda k: fams[k][0])
+    tot_ms, nl, by = fams[dom]
+    achieved = by / (tot_ms / 1e3) / 1e9
+    traffic = read_traffic(dom, wl.name)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind,
+                "traffic": (traffic if traffic is None else traffic),
+                "algorithmic_bytes_per_launch": by / nl, "avg_launch_ms": tot_ms / nl,
+                "share_of_step": tot_ms / ms}
+    kernels = {k: {"ms": v[0], "launches": v[1], "GB/s": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else None,
+                   "share": v[0] / ms} for k, v in prof.items() if v[1] > 0}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        dt, vox, thr = oracle_sample(wl, 4242)
+        cpu = {"value": vox / dt / 1e9, "unit": "GVoxel/s", "cores": thr, "kind": "oracle",
+               "sample": f"one FP64 subject update of one {wl.shape[0]}x{wl.shape[1]}x{wl.shape[2]} subject "
+                         f"({dt:.1f} s)"}
+
+    line = {
+        "metric": "GVoxel/s per subject update (fwd+bwd)", "value": value, "unit": "GVoxel/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "subjects_per_gpu": wl.n, "shape": list(wl.shape),
+                   "dissimilarity": "local NCC %d^3" % cfg.ncc_window, "squarings": cfg.n_squarings,
+                   "inner_steps": cfg.inner_steps, "atlas_epochs": cfg.atlas_epochs,
+                   "atlas_batch": cfg.atlas_batch, "parallelism": f"subjects sharded over {world} GPU(s)",
+                   "l2": "inputs larger than L2 (state %.1f GB per GPU)" % (wl.n * wl.voxels * 4 * 10 / 1e9),
+                   "step": "one sweep: K2 subject updates of every subject + centrality + atlas"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks, "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

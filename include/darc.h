@@ -1,0 +1,296 @@
+/*
+ * darc.h -- C ABI of libdarc.so, a GB300 (sm_103a) implementation of the hot
+ * path of DARC, "Diffeomorphic Atlas Registration via Coordinate descent"
+ * (Zou et al., arXiv 2508.10743): the per-subject update of Eq. 3 (scaling
+ * and squaring, warp, MSE or local NCC plus the diffusion regulariser of
+ * Eq. 2, the adjoint of all of these, Adam), the centrality activation, the
+ * atlas re-estimate, and one-shot label propagation (Eq. oneshot).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A volume has D x H x W voxels (z, y, x), x fastest, V = D*H*W.
+ *  - An image is float32 [V].  A field (velocity v, displacement u,
+ *    gradient) is planar float32 [3][V]; channel a is the component along
+ *    axis a (0 = z, 1 = y, 2 = x), in voxel units.  A batch of B images or
+ *    fields is stored subject after subject: [B][V] or [B][3][V].
+ *  - Every pointer named *_dev is CUDA device memory of the current device;
+ *    *_host is host memory.  The caller owns every buffer it passes; the
+ *    library keeps no pointer past the call, except the cohort, which keeps
+ *    `images_dev` until darc_destroy.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Calls enqueue work on it and return without waiting,
+ *    unless they write a *_host output.
+ *  - Sampling is trilinear with border padding: each coordinate of the
+ *    sample point x + u(x) is clamped to [0, n_a - 1] (the paper does not
+ *    define the interpolation; this is the reading taken).
+ *  - Return value: DARC_OK (0) or a negative darc_status.  On an argument
+ *    or shape error nothing is enqueued and no state changes.
+ *    darc_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef DARC_H_
+#define DARC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DARC_OK = 0,
+    DARC_ERR_ARG = -1,        /* null pointer, bad index, bad option          */
+    DARC_ERR_SHAPE = -2,      /* a dimension < 2, an even or oversized window */
+    DARC_ERR_OOM = -3,        /* device allocation failed                      */
+    DARC_ERR_CUDA = -4,       /* a CUDA call failed (message has the detail)   */
+    DARC_ERR_NONFINITE = -5,  /* a loss came out NaN/Inf; that step's update was skipped */
+    DARC_ERR_IO = -6,         /* darc_save / darc_load file error              */
+    DARC_ERR_INTERNAL = -7
+} darc_status;
+
+typedef enum { DARC_MSE = 0, DARC_LNCC = 1 } darc_dissim;
+
+/* Method settings.  Defaults (darc_default_config) follow the paper where it
+ * gives a number: T = 7 squarings (Sec. "Diffeomorphisms"); Adam lr 1e-2 for
+ * velocities and atlas, K3 = 20 atlas epochs (Sec. "Experiments"). */
+typedef struct {
+    int dissim;            /* darc_dissim                                         */
+    int ncc_window;        /* odd edge w of the local-NCC window, 3..17           */
+    int n_squarings;       /* T, 0..20                                            */
+    float lambda;          /* weight of the diffusion regulariser (Eq. 2)         */
+    float lr, beta1, beta2, adam_eps;   /* Adam                                   */
+    float ncc_eps;         /* NCC denominator stabiliser                          */
+    int inner_steps;       /* K2: Adam steps per subject per sweep (Algorithm 1)  */
+    int atlas_epochs;      /* K3: epochs of atlas SGD (NCC)                        */
+    int atlas_batch;       /* atlas SGD mini-batch                                 */
+    int center_mode;       /* 0: centre the velocities (the only mode built)       */
+    int checkpoint_stride; /* 0: keep u_1..u_T for the adjoint; k > 0: keep every
+                              k-th and recompute the rest in the adjoint           */
+    int subject_batch;     /* subjects per launch in darc_subject_step (0 = all)  */
+    int reset_each_sweep;  /* 1: restart v and Adam each sweep (literal Algorithm 1) */
+    unsigned long long seed; /* atlas mini-batch shuffle                           */
+} darc_config;
+
+/* Per-sweep statistics (Sec. "Evaluation metrics"; Table 1's centrality). */
+typedef struct {
+    double loss_data;           /* mean over subjects of L at their last inner step   */
+    double loss_reg;            /* mean over subjects of R at their last inner step   */
+    double centrality_before;   /* mean_x |1/n sum_i v_i(x)| before the activation     */
+    double centrality_after;    /* the same after it                                  */
+    double atlas_loss;          /* NCC atlas SGD: mean loss of its last epoch (else 0) */
+    int nonfinite_subjects;     /* subjects whose update was skipped (NaN/Inf loss)    */
+} darc_sweep_stats;
+
+typedef struct darc_cohort darc_cohort;
+
+void darc_default_config(darc_config* cfg);
+const char* darc_last_error(void);
+const char* darc_version(void);
+
+/* ===================================================================== */
+/* Cohort API (Eq. 3; Algorithm 1)                                        */
+/* ===================================================================== */
+
+/* Creates a cohort of n subjects of D x H x W voxels.  images_dev [n][V]
+ * stays owned by the caller and must outlive the cohort.  Allocates v, Adam
+ * m/s (zero), the atlas A^0 = 1/n sum_i I_i (Algorithm 1 "initialize()";
+ * reading: the MSE closed form at v = 0) and all scratch.  stream: the
+ * caller's stream; every later call on the cohort is ordered after the work
+ * already on it and before the work enqueued on it afterwards.
+ * Errors: ARG, SHAPE, OOM, CUDA. */
+int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, int H, int W,
+                     const float* images_dev, void* stream);
+
+/* `steps` Adam steps of subjects first..first+count-1 against the frozen
+ * atlas (Eq. 3, lines 1..n; Algorithm 1 diffeo_pairwise_reg body): per step
+ * phi = Exp(v), E = L(I o phi, A) + lambda R(u_T), dE/dv by the hand-written
+ * adjoint, Adam.  loss_host (nullable) [count] receives each subject's E at
+ * its last step (this waits for the stream).  A subject whose loss is not
+ * finite keeps its v; the call then returns DARC_ERR_NONFINITE when
+ * loss_host is given (otherwise the next darc_sweep reports it).
+ * Errors: ARG, CUDA, NONFINITE. */
+int darc_subject_step(darc_cohort* c, int first, int count, int steps, float* loss_host);
+
+/* One outer iteration of Algorithm 1: every subject takes inner_steps steps
+ * (darc_subject_step), then darc_update_atlas.  stats (nullable) is filled
+ * after waiting for the stream.  Errors: ARG, CUDA, NONFINITE. */
+int darc_sweep(darc_cohort* c, darc_sweep_stats* stats);
+
+/* Centrality activation hat v_i = v_i - 1/n sum_j v_j (Eq. 3 line n+1) on
+ * the stored velocities, then the atlas re-estimate (Eq. 3 last line): MSE,
+ * A = 1/n sum_i I_i o Exp(hat v_i) (Sec. "Dissimilarity metrics", closed
+ * form); local NCC, atlas_epochs epochs of mini-batch Adam on A over the
+ * warped cohort (Algorithm 1 SGD_for_atlas).  stats (nullable): the
+ * centrality and atlas fields are filled (waits).  Errors: CUDA. */
+int darc_update_atlas(darc_cohort* c, darc_sweep_stats* stats);
+
+/* One-shot segmentation (Eq. oneshot): out[i] = labels o Exp(-v_i) for
+ * i = first..first+count-1, nearest voxel r(p)_a = clamp(floor(p_a + 1/2),
+ * 0, n_a - 1).  atlas_labels_dev uint8 [V]; out_dev uint8 [count][V].
+ * Errors: ARG, CUDA. */
+int darc_propagate_labels(darc_cohort* c, const uint8_t* atlas_labels_dev, uint8_t* out_dev,
+                          int first, int count);
+
+/* Copies of the state.  Velocity and atlas layouts as above.  set_velocity
+ * zeroes subject i's Adam moments and step count (a warm start).
+ * set_atlas replaces A (and its NCC window statistics).  Errors: ARG, CUDA. */
+int darc_get_atlas(darc_cohort* c, float* out_dev);
+int darc_set_atlas(darc_cohort* c, const float* atlas_dev);
+int darc_get_velocity(darc_cohort* c, int i, float* out_dev);
+int darc_set_velocity(darc_cohort* c, int i, const float* v_dev);
+/* Adam state of subject i: m, s [3][V] each and the step count. */
+int darc_get_adam_state(darc_cohort* c, int i, float* m_dev, float* s_dev, int* step_host);
+int darc_cohort_info(darc_cohort* c, int* n, int* D, int* H, int* W, darc_config* cfg);
+
+/* Checkpoint / resume: v, m, s, step counts, A, sweep index and config to a
+ * file; darc_load rebuilds a cohort on images_dev.  Errors: IO, ARG, OOM. */
+int darc_save(darc_cohort* c, const char* path);
+int darc_load(darc_cohort** out, const char* path, const float* images_dev, void* stream);
+
+void darc_destroy(darc_cohort* c);
+
+/* ===================================================================== */
+/* Measurement                                                             */
+/* ===================================================================== */
+
+/* Kernel families timed by the profiling switch. */
+typedef enum {
+    DARC_K_EXP_SQUARE = 0,      /* one squaring of Exp (24 B/voxel/subject)            */
+    DARC_K_EXP_ADJOINT = 1,     /* adjoint of one squaring (36 B/voxel/subject)        */
+    DARC_K_WARP = 2,            /* warp (20 B/voxel/subject)                           */
+    DARC_K_LNCC_FWD = 3,        /* local-NCC forward (28 B/voxel/subject)              */
+    DARC_K_LNCC_BWD_WARP_REG = 4,/* NCC adjoint + warp adjoint + regulariser (48 B)    */
+    DARC_K_MSE_WARP_REG = 5,    /* fused MSE step (32 B/voxel/subject)                 */
+    DARC_K_ADAM = 6,            /* Adam on the velocities (84 B/voxel/subject)         */
+    DARC_K_ATLAS = 7,           /* everything of the atlas re-estimate                 */
+    DARC_K_COUNT = 8
+} darc_kernel_id;
+
+/* on != 0: later calls on the cohort launch every kernel directly (no graph
+ * replay) and bracket each launch of the families above with CUDA events on
+ * the cohort's stream.  Off by default.  Errors: ARG. */
+int darc_set_profiling(darc_cohort* c, int on);
+
+/* Sums over the launches recorded since the last read (then cleared):
+ * total_ms = summed event time, launches, bytes = algorithmic bytes (each
+ * field read or written once, per the byte counts above).  Waits for the
+ * cohort's stream.  Errors: ARG, CUDA. */
+int darc_profile_read(darc_cohort* c, int kernel_id, double* total_ms, long long* launches,
+                      double* bytes);
+
+/* Kernels launched by the cohort so far (graph replays count each node). */
+long long darc_launch_count(darc_cohort* c);
+
+/* ===================================================================== */
+/* Operator API: the kernels of one subject step, for B subjects at once. */
+/* Used by the autograd wrappers and by parity tests.  `work_dev` is      */
+/* caller-owned scratch of at least the size the matching *_workspace     */
+/* query returns (bytes, 256-byte aligned).                                */
+/* ===================================================================== */
+
+/* Scaling and squaring (Sec. "Diffeomorphisms"): u_0 = sign 2^-T v,
+ * u_{t+1}(x) = u_t(x) + S(u_t, x + u_t(x)).  v_dev [B][3][V]; u_dev
+ * [T][B][3][V] receives u_1..u_T (u_T last).  sign = +1 for Exp(v), -1 for
+ * Exp(-v).  T = 0 is an error (u_0 is v scaled; nothing to store).
+ * Errors: ARG, SHAPE, CUDA. */
+int darc_exp_forward(const float* v_dev, float* u_dev, int B, int D, int H, int W, int T,
+                     float sign, void* stream);
+
+/* Adjoint of darc_exp_forward: gv = dE/dv given gT = dE/du_T.  Each squaring
+ * sends its incoming gradient to u_t(x) (identity), through dS/dp (Jacobian
+ * term) and to the 8 interpolation corners (transpose of the interpolation,
+ * a scatter).  u_dev as written by darc_exp_forward.  gv_dev [B][3][V] may
+ * alias gT_dev.  work_dev: darc_exp_backward_workspace(B, D, H, W) bytes.
+ * Errors: ARG, SHAPE, CUDA. */
+size_t darc_exp_backward_workspace(int B, int D, int H, int W);
+int darc_exp_backward(const float* v_dev, const float* u_dev, const float* gT_dev, float* gv_dev,
+                      void* work_dev, int B, int D, int H, int W, int T, float sign, void* stream);
+
+/* Warp (Eq. 2, "I o phi"): out[b](x) = S(I[b], x + u[b](x)).  I_dev [B][V]
+ * (or [V] when I_batch_stride_zero != 0: one image for every b), u_dev
+ * [B][3][V], out_dev [B][V].  Errors: ARG, SHAPE, CUDA. */
+int darc_warp(const float* I_dev, int I_batch_stride_zero, const float* u_dev, float* out_dev,
+              int B, int D, int H, int W, void* stream);
+
+/* Adjoint of the warp with respect to u: gu[b](x) = gW[b](x) dS(I[b], p)/dp
+ * at p = x + u[b](x); the derivative is 0 along a clamped axis.
+ * Errors: ARG, SHAPE, CUDA. */
+int darc_warp_backward(const float* I_dev, int I_batch_stride_zero, const float* u_dev,
+                       const float* gW_dev, float* gu_dev, int B, int D, int H, int W,
+                       void* stream);
+
+/* MSE (Sec. "Dissimilarity metrics"; reading: mean over voxels)
+ * L_b = 1/V sum_x (J[b](x) - A(x))^2.  J_dev [B][V], A_dev [V], loss_dev
+ * float [B], gJ_dev (nullable) [B][V] = dL_b/dJ[b].  work_dev:
+ * darc_loss_workspace(B, D, H, W).  Errors: ARG, SHAPE, CUDA. */
+size_t darc_loss_workspace(int B, int D, int H, int W);
+int darc_mse(const float* J_dev, const float* A_dev, float* loss_dev, float* gJ_dev,
+             void* work_dev, int B, int D, int H, int W, void* stream);
+
+/* Local NCC (Sec. "Dissimilarity metrics", patch-wise NCC; reading: squared
+ * correlation over the w^3 window with zero padding, normalised by w^3,
+ * denominator + eps): L_b = -1/V sum_x cc_b(x).  gJ_dev (nullable) [B][V] =
+ * dL_b/dJ[b]; gA_dev (nullable) [V] = sum_b dL_b/dA.  work_dev:
+ * darc_lncc_workspace(B, D, H, W).  Errors: ARG, SHAPE, CUDA. */
+size_t darc_lncc_workspace(int B, int D, int H, int W);
+int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, float* loss_dev,
+              float* gJ_dev, float* gA_dev, void* work_dev, int B, int D, int H, int W,
+              void* stream);
+
+/* Diffusion regulariser (Eq. 2 second term; reading: forward differences of
+ * the displacement, mean over the voxel pairs of each axis, mean over the
+ * three axes).  u_dev [B][3][V], loss_dev float [B], gu_dev (nullable)
+ * [B][3][V] = dR_b/du[b].  work_dev: darc_loss_workspace.
+ * Errors: ARG, SHAPE, CUDA. */
+int darc_diffusion_reg(const float* u_dev, float* loss_dev, float* gu_dev, void* work_dev, int B,
+                       int D, int H, int W, void* stream);
+
+/* One subject energy and gradient without the optimiser step (Eq. 2 for
+ * each of B subjects, as in darc_subject_step): energy_dev float [B][2]
+ * receives {L, R}; gv_dev [B][3][V] = dE/dv.  A_dev [V].  cfg supplies
+ * dissim, window, T, lambda, ncc_eps, checkpoint_stride.  work_dev:
+ * darc_subject_grad_workspace(cfg, B, D, H, W).  Errors: ARG, SHAPE, CUDA. */
+size_t darc_subject_grad_workspace(const darc_config* cfg, int B, int D, int H, int W);
+int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A_dev,
+                      const float* v_dev, float* energy_dev, float* gv_dev, void* work_dev, int B,
+                      int D, int H, int W, void* stream);
+
+/* Adam (Sec. "Experiments"; reading: PyTorch defaults, bias corrected):
+ * m = b1 m + (1-b1) g, s = b2 s + (1-b2) g^2,
+ * theta -= lr (m / (1 - b1^k)) / (sqrt(s / (1 - b2^k)) + eps).
+ * theta, m, s, g: float [N]; k >= 1 is the 1-based step.  Errors: ARG, CUDA. */
+int darc_adam(float* theta_dev, float* m_dev, float* s_dev, const float* g_dev, size_t N, int k,
+              float lr, float beta1, float beta2, float eps, void* stream);
+
+/* Centrality activation (Eq. 3): v[i] -= 1/n sum_j v[j] for v_dev [n][3][V];
+ * metrics_dev (nullable) double [2] = mean_x |1/n sum_i v_i(x)| before and
+ * after.  work_dev: darc_centrality_workspace(n, D, H, W).
+ * Errors: ARG, CUDA. */
+size_t darc_centrality_workspace(int n, int D, int H, int W);
+int darc_centrality(float* v_dev, double* metrics_dev, void* work_dev, int n, int D, int H, int W,
+                    void* stream);
+
+/* MSE atlas closed form (Sec. "Dissimilarity metrics"):
+ * A = 1/n sum_i I_i o Exp(v_i).  I_dev [n][V], v_dev [n][3][V], A_dev [V].
+ * work_dev: darc_atlas_mean_workspace(n, D, H, W).  Errors: ARG, CUDA. */
+size_t darc_atlas_mean_workspace(int n, int D, int H, int W);
+int darc_atlas_mean(const float* I_dev, const float* v_dev, float* A_dev, void* work_dev, int n,
+                    int D, int H, int W, int T, void* stream);
+
+/* Label gather of Eq. oneshot given u = the displacement of Exp(-v):
+ * out[b](x) = labels[r(x + u[b](x))].  Errors: ARG, CUDA. */
+int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* out_dev, int B,
+                      int D, int H, int W, void* stream);
+
+/* Folding report (Sec. "Evaluation metrics", |J|<0 %): det(I + grad u) by
+ * central differences (one-sided on faces) into det_dev (nullable) [B][V];
+ * count_dev (nullable) unsigned long long [B] = voxels with det <= 0.
+ * Errors: ARG, CUDA. */
+int darc_jacobian_det(const float* u_dev, float* det_dev, unsigned long long* count_dev, int B,
+                      int D, int H, int W, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DARC_H_ */

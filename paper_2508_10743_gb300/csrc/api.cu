@@ -1,0 +1,1182 @@
+// api.cu -- the C ABI of libdarc.so (include/darc.h).
+//
+// The cohort runs Algorithm 1 of arXiv 2508.10743 on the GPU: subject steps
+// (Eq. 3, lines 1..n) batched over subjects (they are uncoupled given the
+// atlas, Sec. "Coordinate descent method"), the centrality activation
+// (Eq. 3, line n+1) and the atlas re-estimate (Eq. 3, last line; closed
+// form for MSE, mini-batch Adam for local NCC).  Each subject step is
+// recorded once as a CUDA graph per (first, count) chunk and replayed.
+#include "../../include/darc.h"
+#include "kernels.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace darc_impl;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(DARC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+int check_dims(int B, int D, int H, int W)
+{
+    if (B < 1) return fail(DARC_ERR_ARG, "batch must be >= 1");
+    if (D < 2 || H < 2 || W < 2) return fail(DARC_ERR_SHAPE, "every dimension must be >= 2");
+    if ((long long)D * H * W > (1LL << 31)) return fail(DARC_ERR_SHAPE, "volume too large");
+    if ((long long)div_up(D, VT_Z) * B > 65535) return fail(DARC_ERR_SHAPE, "batch x depth too large for one launch");
+    return DARC_OK;
+}
+
+int check_window(int w, int D, int H, int W)
+{
+    if (w < 3 || w > 17 || (w % 2) == 0) return fail(DARC_ERR_SHAPE, "NCC window must be odd, 3..17");
+    if (w > D || w > H || w > W) return fail(DARC_ERR_SHAPE, "NCC window larger than the volume");
+    return DARC_OK;
+}
+
+int check_config(const darc_config* c, int D, int H, int W)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null config");
+    if (c->dissim != DARC_MSE && c->dissim != DARC_LNCC) return fail(DARC_ERR_ARG, "unknown dissimilarity");
+    if (c->dissim == DARC_LNCC) {
+        int rc = check_window(c->ncc_window, D, H, W);
+        if (rc) return rc;
+    }
+    if (c->n_squarings < 1 || c->n_squarings > 20) return fail(DARC_ERR_ARG, "n_squarings must be 1..20");
+    if (!(c->lr > 0.f) || !(c->beta1 >= 0.f && c->beta1 < 1.f) || !(c->beta2 >= 0.f && c->beta2 < 1.f) ||
+        !(c->adam_eps > 0.f) || !(c->ncc_eps >= 0.f) || !(c->lambda >= 0.f))
+        return fail(DARC_ERR_ARG, "bad optimiser or loss constant");
+    if (c->inner_steps < 1 || c->atlas_epochs < 0 || c->atlas_batch < 1 || c->subject_batch < 0)
+        return fail(DARC_ERR_ARG, "bad step / batch count");
+    if (c->center_mode != 0) return fail(DARC_ERR_ARG, "only center_mode 0 (velocities) is built");
+    if (c->checkpoint_stride != 0) return fail(DARC_ERR_ARG, "checkpoint_stride > 0 is not built in this library");
+    return DARC_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// sub-allocation of a caller workspace
+struct Carve {
+    char* base;
+    size_t off = 0;
+    explicit Carve(void* p) : base((char*)p) {}
+    template <typename T>
+    T* take(size_t count)
+    {
+        T* p = base ? (T*)(base + off) : nullptr;
+        off += align256(count * sizeof(T));
+        return p;
+    }
+};
+
+int nblk_max(const Vol& v) { return std::max(voxel_blocks(v), box_blocks(v)); }
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the k-th output of the
+// stream seeded s0 is mix(s0 + k * golden gamma).  Mini-batch order of the
+// atlas SGD: Fisher-Yates from the last position down, j = draw mod (i+1),
+// s0 = seed * 1000003 + sweep * 1009 + epoch.
+uint64_t splitmix64_at(uint64_t s0, uint64_t k)
+{
+    uint64_t z = s0 + k * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+void minibatch_order(uint64_t seed, int sweep, int epoch, int n, int* perm)
+{
+    const uint64_t s0 = seed * 1000003ULL + (uint64_t)sweep * 1009ULL + (uint64_t)epoch;
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    uint64_t k = 0;
+    for (int i = n - 1; i >= 1; --i) {
+        ++k;
+        const int j = (int)(splitmix64_at(s0, k) % (uint64_t)(i + 1));
+        std::swap(perm[i], perm[j]);
+    }
+}
+
+// Exp forward of `cnt` fields into u (T slots of cnt*3V); returns u_T
+cudaError_t exp_forward_all(const float* v, float* u, int cnt, const Vol& vol, int T, float sign,
+                            cudaStream_t s)
+{
+    const float s0 = sign * std::ldexp(1.0f, -T);
+    const float* src = v;
+    float scale = s0;
+    for (int t = 0; t < T; ++t) {
+        float* dst = u + (size_t)t * cnt * 3 * vol.V;
+        cudaError_t e = exp_square(src, scale, dst, cnt, vol, s);
+        if (e != cudaSuccess) return e;
+        src = dst;
+        scale = 1.f;
+    }
+    return cudaSuccess;
+}
+
+// Exp forward keeping two slots only (atlas / labels); returns the slot of u_T
+cudaError_t exp_forward_pingpong(const float* v, float* u2, int cnt, const Vol& vol, int T,
+                                 float sign, cudaStream_t s, float** uT)
+{
+    const float s0 = sign * std::ldexp(1.0f, -T);
+    const float* src = v;
+    float scale = s0;
+    float* dst = nullptr;
+    for (int t = 0; t < T; ++t) {
+        dst = u2 + (size_t)(t % 2) * cnt * 3 * vol.V;
+        cudaError_t e = exp_square(src, scale, dst, cnt, vol, s);
+        if (e != cudaSuccess) return e;
+        src = dst;
+        scale = 1.f;
+    }
+    *uT = dst;
+    return cudaSuccess;
+}
+
+// Adjoint of Exp: gin = gT; two ping-pong buffers gbuf [2][cnt][3V]; gv may
+// be gT when T >= 2.  u holds u_1..u_T (cnt fields per slot).
+cudaError_t exp_backward_all(const float* v, const float* u, const float* gT, float* gv, float* gbuf,
+                             int cnt, const Vol& vol, int T, float sign, cudaStream_t s)
+{
+    const float s0 = sign * std::ldexp(1.0f, -T);
+    const size_t fb = (size_t)cnt * 3 * vol.V;
+    const float* gin = gT;
+    for (int t = T - 1; t >= 0; --t) {
+        const float* src = (t == 0) ? v : u + (size_t)(t - 1) * fb;
+        const float scale = (t == 0) ? s0 : 1.f;
+        float* gout;
+        if (t == 0)
+            gout = (gv == gT && T == 1) ? gbuf : gv;
+        else
+            gout = gbuf + (size_t)((T - 1 - t) % 2) * fb;
+        cudaError_t e = cudaMemsetAsync(gout, 0, fb * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        e = exp_square_adjoint(src, scale, gin, gout, (t == 0) ? s0 : 1.f, cnt, vol, s);
+        if (e != cudaSuccess) return e;
+        gin = gout;
+    }
+    if (gv == gT && T == 1) return cudaMemcpyAsync(gv, gbuf, fb * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// ===========================================================================
+// cohort
+// ===========================================================================
+struct darc_cohort {
+    darc_config cfg;
+    int n = 0;
+    Vol vol;
+    const float* images = nullptr;
+    cudaStream_t user = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_perm = nullptr;   // last upload of perm_host (host rewrites it after this)
+    int bmax = 0;
+    int sweep = 0;
+    std::vector<void*> allocs;
+    // state
+    float *v = nullptr, *m = nullptr, *s = nullptr;
+    int* k = nullptr;
+    float2* bias = nullptr;
+    int* flags = nullptr;
+    int* nonfinite = nullptr;
+    float* loss = nullptr;       // [n][2]
+    float* A = nullptr;
+    float* astats = nullptr;     // [2][V]
+    // scratch
+    float *u_all = nullptr, *gT = nullptr, *gbuf = nullptr, *Wimg = nullptr, *coef = nullptr;
+    double *pL = nullptr, *pR = nullptr, *acc = nullptr, *cpart = nullptr, *cmetrics = nullptr;
+    float *Wcache = nullptr, *Am = nullptr, *As = nullptr, *gA = nullptr, *aloss = nullptr;
+    int *perm_dev = nullptr, *iota_dev = nullptr;
+    int* perm_host = nullptr;    // pinned [K3][n]
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    std::map<std::pair<int, int>, int> seen;
+    // measurement
+    bool profiling = false;
+    long long launches = 0;
+    struct Mark {
+        int id;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> spare;
+};
+
+namespace {
+
+template <typename T>
+int cohort_alloc(darc_cohort* c, T** p, size_t count)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DARC_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return DARC_OK;
+}
+
+void cohort_free(darc_cohort* c)
+{
+    if (!c) return;
+    for (auto& mk : c->marks) { cudaEventDestroy(mk.a); cudaEventDestroy(mk.b); }
+    for (auto e : c->spare) cudaEventDestroy(e);
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->perm_host) cudaFreeHost(c->perm_host);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->ev_perm) cudaEventDestroy(c->ev_perm);
+    if (c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+cudaEvent_t take_event(darc_cohort* c)
+{
+    if (!c->spare.empty()) {
+        cudaEvent_t e = c->spare.back();
+        c->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// RAII bracket of one kernel-family launch (active only while profiling)
+struct Prof {
+    darc_cohort* c;
+    cudaStream_t s;
+    int id;
+    double bytes;
+    cudaEvent_t a = nullptr;
+    Prof(darc_cohort* c_, cudaStream_t s_, int id_, double bytes_) : c(c_), s(s_), id(id_), bytes(bytes_)
+    {
+        if (c->profiling) {
+            a = take_event(c);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~Prof()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, s);
+            c->marks.push_back({id, a, b, bytes});
+        }
+    }
+};
+
+int begin(darc_cohort* c)
+{
+    CK(cudaEventRecord(c->ev_in, c->user));
+    CK(cudaStreamWaitEvent(c->st, c->ev_in, 0));
+    return DARC_OK;
+}
+
+int end(darc_cohort* c)
+{
+    CK(cudaEventRecord(c->ev_out, c->st));
+    CK(cudaStreamWaitEvent(c->user, c->ev_out, 0));
+    return DARC_OK;
+}
+
+// the kernels of one subject step for subjects f..f+cnt-1 (Algorithm 1 body)
+cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
+{
+    const Vol& vol = c->vol;
+    const int T = c->cfg.n_squarings;
+    const size_t fb = (size_t)cnt * 3 * vol.V;
+    const double nv = (double)cnt * (double)vol.V;     // voxels of the chunk
+    const float* vb = c->v + (size_t)f * 3 * vol.V;
+    const float* Ib = c->images + (size_t)f * vol.V;
+    cudaError_t e = cudaSuccess;
+    const float s0 = std::ldexp(1.0f, -T);
+    {
+        const float* src = vb;
+        float scale = s0;
+        for (int t = 0; t < T && e == cudaSuccess; ++t) {
+            float* dst = c->u_all + (size_t)t * fb;
+            Prof p(c, s, DARC_K_EXP_SQUARE, 24.0 * nv);
+            e = exp_square(src, scale, dst, cnt, vol, s);
+            src = dst;
+            scale = 1.f;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    const float* uT = c->u_all + (size_t)(T - 1) * fb;
+    const double *pLp, *pRp;
+    int nL, nR, sL, sR;
+    if (c->cfg.dissim == DARC_MSE) {
+        Prof p(c, s, DARC_K_MSE_WARP_REG, 32.0 * nv);
+        e = mse_warp_reg(Ib, vol.V, c->A, uT, c->cfg.lambda, c->gT, c->pL, cnt, vol, s);
+        pLp = c->pL; pRp = c->pL + 1; nL = nR = voxel_blocks(vol); sL = sR = 2;
+        c->launches += 1;
+    } else {
+        const int r = c->cfg.ncc_window / 2;
+        {
+            Prof p(c, s, DARC_K_WARP, 20.0 * nv);
+            e = warp(Ib, vol.V, uT, c->Wimg, cnt, vol, s);
+        }
+        if (e == cudaSuccess) {
+            Prof p(c, s, DARC_K_LNCC_FWD, 28.0 * nv);
+            e = lncc_forward(c->Wimg, nullptr, c->A, c->astats, r, c->cfg.ncc_eps, 0, c->coef, c->pL, cnt, vol, s);
+        }
+        if (e == cudaSuccess) {
+            Prof p(c, s, DARC_K_LNCC_BWD_WARP_REG, 48.0 * nv);
+            e = lncc_backward_warp_reg(c->Wimg, c->A, c->coef, r, Ib, vol.V, uT, c->cfg.lambda, c->gT,
+                                       c->pR, cnt, vol, s);
+        }
+        pLp = c->pL; pRp = c->pR; nL = nR = box_blocks(vol); sL = sR = 1;
+        c->launches += 3;
+    }
+    if (e != cudaSuccess) return e;
+    e = finish_step(pLp, nL, sL, pRp, nR, sR, c->loss + 2 * f, c->flags + f, c->k + f, c->bias + f,
+                    c->nonfinite, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, cnt, s);
+    if (e != cudaSuccess) return e;
+    float* gv = (T >= 2) ? c->gT : c->gbuf;
+    {
+        const float* gin = c->gT;
+        for (int t = T - 1; t >= 0 && e == cudaSuccess; --t) {
+            const float* src = (t == 0) ? vb : c->u_all + (size_t)(t - 1) * fb;
+            float* gout = (t == 0) ? gv : c->gbuf + (size_t)((T - 1 - t) % 2) * fb;
+            e = cudaMemsetAsync(gout, 0, fb * sizeof(float), s);
+            if (e != cudaSuccess) break;
+            Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
+            e = exp_square_adjoint(src, (t == 0) ? s0 : 1.f, gin, gout, (t == 0) ? s0 : 1.f, cnt, vol, s);
+            gin = gout;
+        }
+    }
+    if (e != cudaSuccess) return e;
+    Prof p(c, s, DARC_K_ADAM, 84.0 * nv);
+    c->launches += 2 * T + 2;
+    return adam_fields(c->v + (size_t)f * 3 * vol.V, c->m + (size_t)f * 3 * vol.V,
+                       c->s + (size_t)f * 3 * vol.V, gv, 1.f, c->bias + f, c->flags + f, c->cfg.beta1,
+                       c->cfg.beta2, c->cfg.adam_eps, cnt, 3 * vol.V, s);
+}
+
+int run_steps(darc_cohort* c, int first, int count, int steps)
+{
+    for (int f = first; f < first + count; f += c->bmax) {
+        const int cnt = std::min(c->bmax, first + count - f);
+        const auto key = std::make_pair(f, cnt);
+        int done = 0;
+        if (c->profiling) {
+            for (int st = 0; st < steps; ++st) CK(enqueue_step(c, f, cnt, c->st));
+            continue;
+        }
+        if (!c->seen.count(key)) {
+            // first use of this chunk: launch directly (sets kernel attributes outside capture)
+            CK(enqueue_step(c, f, cnt, c->st));
+            c->seen[key] = 1;
+            done = 1;
+        }
+        if (done >= steps) continue;
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+            const long long before = c->launches;
+            cudaError_t e = enqueue_step(c, f, cnt, c->st);
+            c->launches = before;   // recording launches nothing
+            cudaError_t e2 = cudaStreamEndCapture(c->st, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                return fail(DARC_ERR_CUDA, std::string("graph capture failed: ") +
+                                               cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            CK(e);
+            it = c->graphs.emplace(key, ex).first;
+        }
+        const long long per_step = (c->cfg.dissim == DARC_MSE ? 1 : 3) + 2LL * c->cfg.n_squarings + 2;
+        for (int s = done; s < steps; ++s) {
+            CK(cudaGraphLaunch(it->second, c->st));
+            c->launches += per_step;
+        }
+    }
+    return DARC_OK;
+}
+
+int update_atlas_body(darc_cohort* c);
+
+int update_atlas_impl(darc_cohort* c)
+{
+    const Vol& vol = c->vol;
+    const int T = c->cfg.n_squarings, n = c->n, K3 = c->cfg.atlas_epochs;
+    const int nbatch = (n + c->cfg.atlas_batch - 1) / c->cfg.atlas_batch;
+    // algorithmic bytes: centrality 24n + 12 per voxel; warped cohort (24T + 20) n;
+    // NCC SGD per mini-batch: statistics 12 + per subject 28 + 20 + Adam 24
+    double bytes = (24.0 * n + 12.0) + (24.0 * T + 20.0) * n;
+    if (c->cfg.dissim == DARC_LNCC) bytes += (double)K3 * (nbatch * (12.0 + 24.0) + n * 48.0);
+    Prof p(c, c->st, DARC_K_ATLAS, bytes * (double)vol.V);
+    const long long chunks = (n + c->bmax - 1) / c->bmax;
+    c->launches += 2 + chunks * (T + 1) +
+                   (c->cfg.dissim == DARC_LNCC ? (long long)K3 * nbatch * 5 + 1 : 1);
+    return update_atlas_body(c);
+}
+
+int update_atlas_body(darc_cohort* c)
+{
+    const Vol& vol = c->vol;
+    const int T = c->cfg.n_squarings, n = c->n;
+    cudaStream_t s = c->st;
+    CK(centrality(c->v, n, vol, c->cpart, c->cmetrics, s));
+    if (c->cfg.dissim == DARC_MSE) {
+        CK(cudaMemsetAsync(c->acc, 0, sizeof(double) * vol.V, s));
+        for (int f = 0; f < n; f += c->bmax) {
+            const int cnt = std::min(c->bmax, n - f);
+            float* uT = nullptr;
+            CK(exp_forward_pingpong(c->v + (size_t)f * 3 * vol.V, c->u_all, cnt, vol, T, 1.f, s, &uT));
+            CK(warp_accumulate(c->images, c->iota_dev + f, uT, c->acc, cnt, vol, s));
+        }
+        CK(finalize_mean(c->acc, 1.0 / n, c->A, vol, s));
+        return DARC_OK;
+    }
+    // local NCC: cache W_i = I_i o Exp(hat v_i), then K3 epochs of mini-batch Adam on A
+    for (int f = 0; f < n; f += c->bmax) {
+        const int cnt = std::min(c->bmax, n - f);
+        float* uT = nullptr;
+        CK(exp_forward_pingpong(c->v + (size_t)f * 3 * vol.V, c->u_all, cnt, vol, T, 1.f, s, &uT));
+        CK(warp(c->images + (size_t)f * vol.V, vol.V, uT, c->Wcache + (size_t)f * vol.V, cnt, vol, s));
+    }
+    const int K3 = c->cfg.atlas_epochs, B = c->cfg.atlas_batch, r = c->cfg.ncc_window / 2;
+    if (K3 > 0) {
+        CK(cudaEventSynchronize(c->ev_perm));   // the previous upload has left perm_host
+        for (int ep = 0; ep < K3; ++ep) minibatch_order(c->cfg.seed, c->sweep, ep, n, c->perm_host + (size_t)ep * n);
+        CK(cudaMemcpyAsync(c->perm_dev, c->perm_host, sizeof(int) * (size_t)K3 * n, cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(c->ev_perm, s));
+        CK(cudaMemsetAsync(c->Am, 0, sizeof(float) * vol.V, s));
+        CK(cudaMemsetAsync(c->As, 0, sizeof(float) * vol.V, s));
+        int kk = 0;
+        for (int ep = 0; ep < K3; ++ep) {
+            for (int b0 = 0; b0 < n; b0 += B) {
+                const int nb = std::min(B, n - b0);
+                const int* subj = c->perm_dev + (size_t)ep * n + b0;
+                CK(atlas_stats(c->A, c->astats, r, vol, s));
+                CK(lncc_forward(c->Wcache, subj, c->A, c->astats, r, c->cfg.ncc_eps, 1, c->coef, c->pL, nb, vol, s));
+                CK(reduce_partials(c->pL, box_blocks(vol), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
+                CK(lncc_backward(c->Wcache, subj, c->A, c->coef, r, 1, c->gA, nb, vol, s));
+                ++kk;
+                const double c1 = 1.0 - std::pow((double)c->cfg.beta1, kk);
+                const double c2 = 1.0 - std::pow((double)c->cfg.beta2, kk);
+                CK(atlas_adam(c->A, c->Am, c->As, c->gA, nb, (float)(c->cfg.lr / c1), (float)(1.0 / std::sqrt(c2)),
+                              c->cfg.beta1, c->cfg.beta2, c->cfg.adam_eps, vol, s));
+            }
+        }
+    }
+    CK(atlas_stats(c->A, c->astats, r, vol, s));
+    return DARC_OK;
+}
+
+int fill_atlas_stats(darc_cohort* c, darc_sweep_stats* stats)
+{
+    double m[2] = {0, 0};
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpy(m, c->cmetrics, sizeof(m), cudaMemcpyDeviceToHost));
+    stats->centrality_before = m[0];
+    stats->centrality_after = m[1];
+    stats->atlas_loss = 0.0;
+    if (c->cfg.dissim == DARC_LNCC && c->cfg.atlas_epochs > 0) {
+        std::vector<float> al(c->n);
+        CK(cudaMemcpy(al.data(), c->aloss + (size_t)(c->cfg.atlas_epochs - 1) * c->n, sizeof(float) * c->n,
+                      cudaMemcpyDeviceToHost));
+        double t = 0;
+        for (float x : al) t += x;
+        stats->atlas_loss = t / c->n;
+    }
+    return DARC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void darc_default_config(darc_config* c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->dissim = DARC_LNCC;
+    c->ncc_window = 9;
+    c->n_squarings = 7;
+    c->lambda = 1.0f;
+    c->lr = 1e-2f;
+    c->beta1 = 0.9f;
+    c->beta2 = 0.999f;
+    c->adam_eps = 1e-8f;
+    c->ncc_eps = 1e-5f;
+    c->inner_steps = 10;
+    c->atlas_epochs = 20;
+    c->atlas_batch = 4;
+}
+
+const char* darc_last_error(void) { return g_err.c_str(); }
+
+const char* darc_version(void) { return "darc-gb300 0.1 (sm_103a)"; }
+
+int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, int H, int W,
+                     const float* images_dev, void* stream)
+{
+    if (!out || !images_dev) return fail(DARC_ERR_ARG, "null argument");
+    *out = nullptr;
+    int rc = check_dims(1, D, H, W);
+    if (rc) return rc;
+    if (n < 1) return fail(DARC_ERR_ARG, "n must be >= 1");
+    rc = check_config(cfg, D, H, W);
+    if (rc) return rc;
+    darc_cohort* c = new darc_cohort();
+    c->cfg = *cfg;
+    c->n = n;
+    c->vol = make_vol(D, H, W);
+    c->images = images_dev;
+    c->user = (cudaStream_t)stream;
+    c->bmax = (cfg->subject_batch > 0) ? std::min(cfg->subject_batch, n) : n;
+    rc = check_dims(c->bmax, D, H, W);
+    if (rc) { delete c; return rc; }
+    const Vol& v = c->vol;
+    const int T = cfg->n_squarings;
+    const size_t F = 3 * (size_t)v.V;
+    const int bsub = std::max(c->bmax, cfg->atlas_batch);
+    const int nb = nblk_max(v);
+#define ALLOC(ptr, cnt)                      \
+    do {                                     \
+        int r_ = cohort_alloc(c, &(ptr), (cnt)); \
+        if (r_) { cohort_free(c); return r_; } \
+    } while (0)
+    if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_perm, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cohort_free(c);
+        return fail(DARC_ERR_CUDA, "stream/event creation failed");
+    }
+    ALLOC(c->v, F * n);
+    ALLOC(c->m, F * n);
+    ALLOC(c->s, F * n);
+    ALLOC(c->k, n);
+    ALLOC(c->bias, n);
+    ALLOC(c->flags, n);
+    ALLOC(c->nonfinite, 1);
+    ALLOC(c->loss, 2 * (size_t)n);
+    ALLOC(c->A, v.V);
+    ALLOC(c->u_all, F * c->bmax * std::max(T, 2));
+    ALLOC(c->gT, F * c->bmax);
+    ALLOC(c->gbuf, 2 * F * c->bmax);
+    ALLOC(c->pL, 2 * (size_t)nb * bsub);
+    ALLOC(c->pR, (size_t)nb * bsub);
+    ALLOC(c->acc, v.V);
+    ALLOC(c->cpart, 2 * (size_t)centrality_blocks(v));
+    ALLOC(c->cmetrics, 2);
+    ALLOC(c->iota_dev, n);
+    if (cfg->dissim == DARC_LNCC) {
+        ALLOC(c->astats, 2 * v.V);
+        ALLOC(c->Wimg, (size_t)v.V * c->bmax);
+        ALLOC(c->coef, 3 * (size_t)v.V * bsub);
+        ALLOC(c->Wcache, (size_t)v.V * n);
+        ALLOC(c->Am, v.V);
+        ALLOC(c->As, v.V);
+        ALLOC(c->gA, (size_t)v.V * cfg->atlas_batch);
+        ALLOC(c->aloss, (size_t)std::max(cfg->atlas_epochs, 1) * n);
+        ALLOC(c->perm_dev, (size_t)std::max(cfg->atlas_epochs, 1) * n);
+        if (cudaMallocHost(&c->perm_host, sizeof(int) * (size_t)std::max(cfg->atlas_epochs, 1) * n) != cudaSuccess) {
+            cudaGetLastError();
+            c->perm_host = nullptr;
+            cohort_free(c);
+            return fail(DARC_ERR_OOM, "pinned allocation failed");
+        }
+    }
+#undef ALLOC
+    cudaStream_t s = c->st;
+    std::vector<int> iota(n);
+    for (int i = 0; i < n; ++i) iota[i] = i;
+    const bool ok =
+        cudaEventRecord(c->ev_in, c->user) == cudaSuccess && cudaStreamWaitEvent(s, c->ev_in, 0) == cudaSuccess &&
+        cudaMemcpyAsync(c->iota_dev, iota.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+        cudaMemsetAsync(c->v, 0, sizeof(float) * F * n, s) == cudaSuccess &&
+        cudaMemsetAsync(c->m, 0, sizeof(float) * F * n, s) == cudaSuccess &&
+        cudaMemsetAsync(c->s, 0, sizeof(float) * F * n, s) == cudaSuccess &&
+        cudaMemsetAsync(c->k, 0, sizeof(int) * n, s) == cudaSuccess &&
+        cudaMemsetAsync(c->flags, 0, sizeof(int) * n, s) == cudaSuccess &&
+        cudaMemsetAsync(c->nonfinite, 0, sizeof(int), s) == cudaSuccess &&
+        cudaMemsetAsync(c->loss, 0, sizeof(float) * 2 * n, s) == cudaSuccess &&
+        cudaMemsetAsync(c->cmetrics, 0, sizeof(double) * 2, s) == cudaSuccess &&
+        image_mean_accumulate(images_dev, n, c->acc, v, s) == cudaSuccess &&
+        finalize_mean(c->acc, 1.0 / n, c->A, v, s) == cudaSuccess &&
+        (cfg->dissim != DARC_LNCC || atlas_stats(c->A, c->astats, cfg->ncc_window / 2, v, s) == cudaSuccess) &&
+        cudaStreamSynchronize(s) == cudaSuccess;
+    if (!ok) {
+        cudaError_t e = cudaGetLastError();
+        cohort_free(c);
+        return fail(DARC_ERR_CUDA, std::string("cohort initialisation failed: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return DARC_OK;
+}
+
+int darc_subject_step(darc_cohort* c, int first, int count, int steps, float* loss_host)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    if (first < 0 || count < 1 || first + count > c->n || steps < 0)
+        return fail(DARC_ERR_ARG, "subject range or step count out of bounds");
+    if (steps == 0) return DARC_OK;
+    int rc = begin(c);
+    if (rc) return rc;
+    rc = run_steps(c, first, count, steps);
+    if (rc) return rc;
+    rc = end(c);
+    if (rc) return rc;
+    if (loss_host) {
+        std::vector<float> l(2 * (size_t)count);
+        std::vector<int> fl(count);
+        CK(cudaStreamSynchronize(c->st));
+        CK(cudaMemcpy(l.data(), c->loss + 2 * (size_t)first, sizeof(float) * 2 * count, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(fl.data(), c->flags + first, sizeof(int) * count, cudaMemcpyDeviceToHost));
+        int bad = 0;
+        for (int i = 0; i < count; ++i) {
+            loss_host[i] = l[2 * i] + c->cfg.lambda * l[2 * i + 1];
+            bad += fl[i] != 0;
+        }
+        if (bad) return fail(DARC_ERR_NONFINITE, std::to_string(bad) + " subject(s) had a non-finite loss");
+    }
+    return DARC_OK;
+}
+
+int darc_update_atlas(darc_cohort* c, darc_sweep_stats* stats)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    int rc = begin(c);
+    if (rc) return rc;
+    rc = update_atlas_impl(c);
+    if (rc) return rc;
+    rc = end(c);
+    if (rc) return rc;
+    if (stats) return fill_atlas_stats(c, stats);
+    return DARC_OK;
+}
+
+int darc_sweep(darc_cohort* c, darc_sweep_stats* stats)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    int rc = begin(c);
+    if (rc) return rc;
+    const size_t F = 3 * (size_t)c->vol.V * c->n;
+    if (c->cfg.reset_each_sweep) {
+        CK(cudaMemsetAsync(c->v, 0, sizeof(float) * F, c->st));
+        CK(cudaMemsetAsync(c->m, 0, sizeof(float) * F, c->st));
+        CK(cudaMemsetAsync(c->s, 0, sizeof(float) * F, c->st));
+        CK(cudaMemsetAsync(c->k, 0, sizeof(int) * c->n, c->st));
+    }
+    rc = run_steps(c, 0, c->n, c->cfg.inner_steps);
+    if (rc) return rc;
+    rc = update_atlas_impl(c);
+    if (rc) return rc;
+    rc = end(c);
+    if (rc) return rc;
+    c->sweep += 1;
+    int nonfinite = 0;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        rc = fill_atlas_stats(c, stats);
+        if (rc) return rc;
+        std::vector<float> l(2 * (size_t)c->n);
+        CK(cudaMemcpy(l.data(), c->loss, sizeof(float) * 2 * c->n, cudaMemcpyDeviceToHost));
+        double L = 0, R = 0;
+        for (int i = 0; i < c->n; ++i) { L += l[2 * i]; R += l[2 * i + 1]; }
+        stats->loss_data = L / c->n;
+        stats->loss_reg = R / c->n;
+        CK(cudaMemcpy(&nonfinite, c->nonfinite, sizeof(int), cudaMemcpyDeviceToHost));
+        CK(cudaMemset(c->nonfinite, 0, sizeof(int)));
+        stats->nonfinite_subjects = nonfinite;
+        if (nonfinite) return fail(DARC_ERR_NONFINITE, std::to_string(nonfinite) + " subject step(s) had a non-finite loss");
+    }
+    return DARC_OK;
+}
+
+int darc_propagate_labels(darc_cohort* c, const uint8_t* labels_dev, uint8_t* out_dev, int first, int count)
+{
+    if (!c || !labels_dev || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (first < 0 || count < 1 || first + count > c->n) return fail(DARC_ERR_ARG, "subject range out of bounds");
+    int rc = begin(c);
+    if (rc) return rc;
+    const Vol& vol = c->vol;
+    for (int f = first; f < first + count; f += c->bmax) {
+        const int cnt = std::min(c->bmax, first + count - f);
+        float* uT = nullptr;
+        CK(exp_forward_pingpong(c->v + (size_t)f * 3 * vol.V, c->u_all, cnt, vol, c->cfg.n_squarings, -1.f, c->st, &uT));
+        CK(label_gather(labels_dev, uT, out_dev + (size_t)(f - first) * vol.V, cnt, vol, c->st));
+    }
+    return end(c);
+}
+
+int darc_get_atlas(darc_cohort* c, float* out_dev)
+{
+    if (!c || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out_dev, c->A, sizeof(float) * c->vol.V, cudaMemcpyDeviceToDevice, c->st));
+    return end(c);
+}
+
+int darc_set_atlas(darc_cohort* c, const float* atlas_dev)
+{
+    if (!c || !atlas_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->A, atlas_dev, sizeof(float) * c->vol.V, cudaMemcpyDeviceToDevice, c->st));
+    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->st));
+    return end(c);
+}
+
+int darc_get_velocity(darc_cohort* c, int i, float* out_dev)
+{
+    if (!c || !out_dev || i < 0 || i >= c->n) return fail(DARC_ERR_ARG, "bad argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out_dev, c->v + (size_t)i * 3 * c->vol.V, sizeof(float) * 3 * c->vol.V,
+                       cudaMemcpyDeviceToDevice, c->st));
+    return end(c);
+}
+
+int darc_set_velocity(darc_cohort* c, int i, const float* v_dev)
+{
+    if (!c || !v_dev || i < 0 || i >= c->n) return fail(DARC_ERR_ARG, "bad argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    const size_t F = 3 * (size_t)c->vol.V;
+    CK(cudaMemcpyAsync(c->v + i * F, v_dev, sizeof(float) * F, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemsetAsync(c->m + i * F, 0, sizeof(float) * F, c->st));
+    CK(cudaMemsetAsync(c->s + i * F, 0, sizeof(float) * F, c->st));
+    CK(cudaMemsetAsync(c->k + i, 0, sizeof(int), c->st));
+    return end(c);
+}
+
+int darc_get_adam_state(darc_cohort* c, int i, float* m_dev, float* s_dev, int* step_host)
+{
+    if (!c || i < 0 || i >= c->n) return fail(DARC_ERR_ARG, "bad argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    const size_t F = 3 * (size_t)c->vol.V;
+    if (m_dev) CK(cudaMemcpyAsync(m_dev, c->m + i * F, sizeof(float) * F, cudaMemcpyDeviceToDevice, c->st));
+    if (s_dev) CK(cudaMemcpyAsync(s_dev, c->s + i * F, sizeof(float) * F, cudaMemcpyDeviceToDevice, c->st));
+    rc = end(c);
+    if (rc) return rc;
+    if (step_host) {
+        CK(cudaStreamSynchronize(c->st));
+        CK(cudaMemcpy(step_host, c->k + i, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    return DARC_OK;
+}
+
+int darc_cohort_info(darc_cohort* c, int* n, int* D, int* H, int* W, darc_config* cfg)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    if (n) *n = c->n;
+    if (D) *D = c->vol.D;
+    if (H) *H = c->vol.H;
+    if (W) *W = c->vol.W;
+    if (cfg) *cfg = c->cfg;
+    return DARC_OK;
+}
+
+// checkpoint format: magic, version, config, n, D, H, W, sweep, k[n], A[V],
+// v, m, s [n][3][V] (all little-endian host copies)
+static const char kMagic[8] = {'D', 'A', 'R', 'C', 'C', 'K', 'P', '1'};
+
+int darc_save(darc_cohort* c, const char* path)
+{
+    if (!c || !path) return fail(DARC_ERR_ARG, "null argument");
+    CK(cudaStreamSynchronize(c->user));
+    CK(cudaStreamSynchronize(c->st));
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(DARC_ERR_IO, std::string("cannot open ") + path);
+    const size_t V = (size_t)c->vol.V, F = 3 * V;
+    std::vector<int> k(c->n);
+    std::vector<float> buf(std::max(F, V));
+    bool ok = cudaMemcpy(k.data(), c->k, sizeof(int) * c->n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    const int hdr[5] = {c->n, c->vol.D, c->vol.H, c->vol.W, c->sweep};
+    ok = ok && std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(&c->cfg, sizeof(darc_config), 1, fp) == 1 &&
+         std::fwrite(hdr, sizeof(int), 5, fp) == 5 && std::fwrite(k.data(), sizeof(int), c->n, fp) == (size_t)c->n;
+    ok = ok && cudaMemcpy(buf.data(), c->A, sizeof(float) * V, cudaMemcpyDeviceToHost) == cudaSuccess &&
+         std::fwrite(buf.data(), sizeof(float), V, fp) == V;
+    for (float* arr : {c->v, c->m, c->s})
+        for (int i = 0; ok && i < c->n; ++i)
+            ok = cudaMemcpy(buf.data(), arr + i * F, sizeof(float) * F, cudaMemcpyDeviceToHost) == cudaSuccess &&
+                 std::fwrite(buf.data(), sizeof(float), F, fp) == F;
+    if (std::fclose(fp) != 0) ok = false;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(DARC_ERR_IO, std::string("writing ") + path + " failed");
+    }
+    return DARC_OK;
+}
+
+int darc_load(darc_cohort** out, const char* path, const float* images_dev, void* stream)
+{
+    if (!out || !path || !images_dev) return fail(DARC_ERR_ARG, "null argument");
+    *out = nullptr;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(DARC_ERR_IO, std::string("cannot open ") + path);
+    char magic[8];
+    darc_config cfg;
+    int hdr[5];
+    if (std::fread(magic, 1, 8, fp) != 8 || std::memcmp(magic, kMagic, 8) != 0 ||
+        std::fread(&cfg, sizeof(cfg), 1, fp) != 1 || std::fread(hdr, sizeof(int), 5, fp) != 5) {
+        std::fclose(fp);
+        return fail(DARC_ERR_IO, "not a darc checkpoint");
+    }
+    darc_cohort* c = nullptr;
+    int rc = darc_init_cohort(&c, &cfg, hdr[0], hdr[1], hdr[2], hdr[3], images_dev, stream);
+    if (rc) { std::fclose(fp); return rc; }
+    c->sweep = hdr[4];
+    const size_t V = (size_t)c->vol.V, F = 3 * V;
+    std::vector<int> k(c->n);
+    std::vector<float> buf(std::max(F, V));
+    bool ok = std::fread(k.data(), sizeof(int), c->n, fp) == (size_t)c->n &&
+              cudaMemcpy(c->k, k.data(), sizeof(int) * c->n, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && std::fread(buf.data(), sizeof(float), V, fp) == V &&
+         cudaMemcpy(c->A, buf.data(), sizeof(float) * V, cudaMemcpyHostToDevice) == cudaSuccess;
+    for (float* arr : {c->v, c->m, c->s})
+        for (int i = 0; ok && i < c->n; ++i)
+            ok = std::fread(buf.data(), sizeof(float), F, fp) == F &&
+                 cudaMemcpy(arr + i * F, buf.data(), sizeof(float) * F, cudaMemcpyHostToDevice) == cudaSuccess;
+    std::fclose(fp);
+    if (ok && cfg.dissim == DARC_LNCC)
+        ok = atlas_stats(c->A, c->astats, cfg.ncc_window / 2, c->vol, c->st) == cudaSuccess &&
+             cudaStreamSynchronize(c->st) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cohort_free(c);
+        return fail(DARC_ERR_IO, std::string("reading ") + path + " failed");
+    }
+    *out = c;
+    return DARC_OK;
+}
+
+void darc_destroy(darc_cohort* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    cohort_free(c);
+}
+
+int darc_set_profiling(darc_cohort* c, int on)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    c->profiling = on != 0;
+    return DARC_OK;
+}
+
+int darc_profile_read(darc_cohort* c, int kernel_id, double* total_ms, long long* launches, double* bytes)
+{
+    if (!c || kernel_id < 0 || kernel_id >= DARC_K_COUNT) return fail(DARC_ERR_ARG, "bad argument");
+    CK(cudaStreamSynchronize(c->st));
+    double ms = 0.0, by = 0.0;
+    long long cnt = 0;
+    std::vector<darc_cohort::Mark> keep;
+    for (auto& mk : c->marks) {
+        if (mk.id != kernel_id) {
+            keep.push_back(mk);
+            continue;
+        }
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, mk.a, mk.b));
+        ms += t;
+        by += mk.bytes;
+        ++cnt;
+        c->spare.push_back(mk.a);
+        c->spare.push_back(mk.b);
+    }
+    c->marks.swap(keep);
+    if (total_ms) *total_ms = ms;
+    if (launches) *launches = cnt;
+    if (bytes) *bytes = by;
+    return DARC_OK;
+}
+
+long long darc_launch_count(darc_cohort* c) { return c ? c->launches : 0; }
+
+// ===========================================================================
+// operator API
+// ===========================================================================
+
+int darc_exp_forward(const float* v_dev, float* u_dev, int B, int D, int H, int W, int T, float sign,
+                     void* stream)
+{
+    if (!v_dev || !u_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    if (T < 1 || T > 20) return fail(DARC_ERR_ARG, "T must be 1..20");
+    CK(exp_forward_all(v_dev, u_dev, B, make_vol(D, H, W), T, sign, (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+size_t darc_exp_backward_workspace(int B, int D, int H, int W)
+{
+    return 2 * align256(sizeof(float) * 3 * (size_t)B * D * H * W);
+}
+
+int darc_exp_backward(const float* v_dev, const float* u_dev, const float* gT_dev, float* gv_dev, void* work_dev,
+                      int B, int D, int H, int W, int T, float sign, void* stream)
+{
+    if (!v_dev || !u_dev || !gT_dev || !gv_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    if (T < 1 || T > 20) return fail(DARC_ERR_ARG, "T must be 1..20");
+    const Vol v = make_vol(D, H, W);
+    Carve cv(work_dev);
+    float* gbuf = cv.take<float>(2 * 3 * (size_t)B * v.V);
+    CK(exp_backward_all(v_dev, u_dev, gT_dev, gv_dev, gbuf, B, v, T, sign, (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+int darc_warp(const float* I_dev, int I_batch_stride_zero, const float* u_dev, float* out_dev, int B, int D, int H,
+              int W, void* stream)
+{
+    if (!I_dev || !u_dev || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    const Vol v = make_vol(D, H, W);
+    CK(warp(I_dev, I_batch_stride_zero ? 0 : v.V, u_dev, out_dev, B, v, (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+int darc_warp_backward(const float* I_dev, int I_batch_stride_zero, const float* u_dev, const float* gW_dev,
+                       float* gu_dev, int B, int D, int H, int W, void* stream)
+{
+    if (!I_dev || !u_dev || !gW_dev || !gu_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    const Vol v = make_vol(D, H, W);
+    CK(warp_backward(I_dev, I_batch_stride_zero ? 0 : v.V, u_dev, gW_dev, gu_dev, B, v, (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+size_t darc_loss_workspace(int B, int D, int H, int W)
+{
+    const Vol v = make_vol(D, H, W);
+    return align256(sizeof(double) * 2 * (size_t)B * nblk_max(v));
+}
+
+int darc_mse(const float* J_dev, const float* A_dev, float* loss_dev, float* gJ_dev, void* work_dev, int B, int D,
+             int H, int W, void* stream)
+{
+    if (!J_dev || !A_dev || !loss_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    const Vol v = make_vol(D, H, W);
+    cudaStream_t s = (cudaStream_t)stream;
+    double* part = (double*)work_dev;
+    CK(mse_partials(J_dev, A_dev, gJ_dev, part, B, v, s));
+    CK(reduce_partials(part, voxel_blocks(v), 1, 1.0, loss_dev, 1, B, s));
+    return DARC_OK;
+}
+
+size_t darc_lncc_workspace(int B, int D, int H, int W)
+{
+    const Vol v = make_vol(D, H, W);
+    return align256(sizeof(float) * 2 * (size_t)v.V) + align256(sizeof(float) * 3 * (size_t)B * v.V) +
+           align256(sizeof(float) * (size_t)B * v.V) + darc_loss_workspace(B, D, H, W);
+}
+
+int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, float* loss_dev, float* gJ_dev,
+              float* gA_dev, void* work_dev, int B, int D, int H, int W, void* stream)
+{
+    if (!J_dev || !A_dev || !loss_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    rc = check_window(window, D, H, W);
+    if (rc) return rc;
+    const Vol v = make_vol(D, H, W);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int r = window / 2;
+    Carve cv(work_dev);
+    float* stats = cv.take<float>(2 * (size_t)v.V);
+    float* coef = cv.take<float>(3 * (size_t)B * v.V);
+    float* gAb = cv.take<float>((size_t)B * v.V);
+    double* part = cv.take<double>(2 * (size_t)B * nblk_max(v));
+    CK(atlas_stats(A_dev, stats, r, v, s));
+    CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 0, coef, part, B, v, s));
+    CK(reduce_partials(part, box_blocks(v), 1, 1.0, loss_dev, 1, B, s));
+    if (gJ_dev) CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 0, gJ_dev, B, v, s));
+    if (gA_dev) {
+        CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 1, coef, part, B, v, s));
+        CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 1, gAb, B, v, s));
+        CK(sum_images(gAb, B, gA_dev, v, s));
+    }
+    return DARC_OK;
+}
+
+int darc_diffusion_reg(const float* u_dev, float* loss_dev, float* gu_dev, void* work_dev, int B, int D, int H,
+                       int W, void* stream)
+{
+    if (!u_dev || !loss_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    const Vol v = make_vol(D, H, W);
+    cudaStream_t s = (cudaStream_t)stream;
+    double* part = (double*)work_dev;
+    CK(reg_partials(u_dev, gu_dev, part, B, v, s));
+    CK(reduce_partials(part, voxel_blocks(v), 1, 1.0, loss_dev, 1, B, s));
+    return DARC_OK;
+}
+
+size_t darc_subject_grad_workspace(const darc_config* cfg, int B, int D, int H, int W)
+{
+    if (!cfg) return 0;
+    const size_t V = (size_t)D * H * W, F = 3 * V * B;
+    const int T = std::max(cfg->n_squarings, 1);
+    return align256(sizeof(float) * F * T) + align256(sizeof(float) * F) + 2 * align256(sizeof(float) * F) +
+           align256(sizeof(float) * V * B) + align256(sizeof(float) * 3 * V * B) + align256(sizeof(float) * 2 * V) +
+           2 * darc_loss_workspace(B, D, H, W);
+}
+
+int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A_dev, const float* v_dev,
+                      float* energy_dev, float* gv_dev, void* work_dev, int B, int D, int H, int W, void* stream)
+{
+    if (!I_dev || !A_dev || !v_dev || !energy_dev || !gv_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    rc = check_config(cfg, D, H, W);
+    if (rc) return rc;
+    const Vol v = make_vol(D, H, W);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int T = cfg->n_squarings;
+    const size_t F = 3 * (size_t)v.V * B;
+    Carve cv(work_dev);
+    float* u_all = cv.take<float>(F * T);
+    float* gT = cv.take<float>(F);
+    float* gbuf = cv.take<float>(2 * F);
+    float* Wimg = cv.take<float>((size_t)v.V * B);
+    float* coef = cv.take<float>(3 * (size_t)v.V * B);
+    float* stats = cv.take<float>(2 * (size_t)v.V);
+    double* pL = cv.take<double>(2 * (size_t)B * nblk_max(v));
+    double* pR = cv.take<double>(2 * (size_t)B * nblk_max(v));
+    CK(exp_forward_all(v_dev, u_all, B, v, T, 1.f, s));
+    const float* uT = u_all + (size_t)(T - 1) * F;
+    if (cfg->dissim == DARC_MSE) {
+        CK(mse_warp_reg(I_dev, v.V, A_dev, uT, cfg->lambda, gT, pL, B, v, s));
+        CK(reduce_partials(pL, voxel_blocks(v), 2, 1.0, energy_dev, 2, B, s));
+    } else {
+        const int r = cfg->ncc_window / 2;
+        CK(atlas_stats(A_dev, stats, r, v, s));
+        CK(warp(I_dev, v.V, uT, Wimg, B, v, s));
+        CK(lncc_forward(Wimg, nullptr, A_dev, stats, r, cfg->ncc_eps, 0, coef, pL, B, v, s));
+        CK(lncc_backward_warp_reg(Wimg, A_dev, coef, r, I_dev, v.V, uT, cfg->lambda, gT, pR, B, v, s));
+        CK(reduce_partials(pL, box_blocks(v), 1, 1.0, energy_dev, 2, B, s));
+        CK(reduce_partials(pR, box_blocks(v), 1, 1.0, energy_dev + 1, 2, B, s));
+    }
+    CK(exp_backward_all(v_dev, u_all, gT, gv_dev, gbuf, B, v, T, 1.f, s));
+    return DARC_OK;
+}
+
+int darc_adam(float* theta_dev, float* m_dev, float* s_dev, const float* g_dev, size_t N, int k, float lr,
+              float beta1, float beta2, float eps, void* stream)
+{
+    if (!theta_dev || !m_dev || !s_dev || !g_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (k < 1) return fail(DARC_ERR_ARG, "step k must be >= 1");
+    if (N == 0) return DARC_OK;
+    const double c1 = 1.0 - std::pow((double)beta1, k), c2 = 1.0 - std::pow((double)beta2, k);
+    CK(adam_flat(theta_dev, m_dev, s_dev, g_dev, N, (float)(lr / c1), (float)(1.0 / std::sqrt(c2)), beta1, beta2,
+                 eps, (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+size_t darc_centrality_workspace(int n, int D, int H, int W)
+{
+    (void)n;
+    return align256(sizeof(double) * 2 * (size_t)centrality_blocks(make_vol(D, H, W)));
+}
+
+int darc_centrality(float* v_dev, double* metrics_dev, void* work_dev, int n, int D, int H, int W, void* stream)
+{
+    if (!v_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(1, D, H, W);
+    if (rc) return rc;
+    if (n < 1) return fail(DARC_ERR_ARG, "n must be >= 1");
+    CK(centrality(v_dev, n, make_vol(D, H, W), (double*)work_dev, metrics_dev, (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+size_t darc_atlas_mean_workspace(int n, int D, int H, int W)
+{
+    const size_t V = (size_t)D * H * W;
+    const int chunk = std::min(n, 8);
+    return align256(sizeof(double) * V) + align256(sizeof(float) * 2 * 3 * V * chunk) + align256(sizeof(int) * n);
+}
+
+int darc_atlas_mean(const float* I_dev, const float* v_dev, float* A_dev, void* work_dev, int n, int D, int H, int W,
+                    int T, void* stream)
+{
+    if (!I_dev || !v_dev || !A_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(std::min(n, 8), D, H, W);
+    if (rc) return rc;
+    if (T < 1 || T > 20) return fail(DARC_ERR_ARG, "T must be 1..20");
+    const Vol v = make_vol(D, H, W);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int chunk = std::min(n, 8);
+    Carve cv(work_dev);
+    double* acc = cv.take<double>(v.V);
+    float* u2 = cv.take<float>(2 * 3 * (size_t)v.V * chunk);
+    int* iota = cv.take<int>(n);
+    std::vector<int> h(n);
+    for (int i = 0; i < n; ++i) h[i] = i;
+    CK(cudaMemcpyAsync(iota, h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(acc, 0, sizeof(double) * v.V, s));
+    for (int f = 0; f < n; f += chunk) {
+        const int cnt = std::min(chunk, n - f);
+        float* uT = nullptr;
+        CK(exp_forward_pingpong(v_dev + (size_t)f * 3 * v.V, u2, cnt, v, T, 1.f, s, &uT));
+        CK(warp_accumulate(I_dev, iota + f, uT, acc, cnt, v, s));
+    }
+    CK(finalize_mean(acc, 1.0 / n, A_dev, v, s));
+    return DARC_OK;
+}
+
+int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* out_dev, int B, int D, int H, int W,
+                      void* stream)
+{
+    if (!labels_dev || !u_dev || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    CK(label_gather(labels_dev, u_dev, out_dev, B, make_vol(D, H, W), (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+int darc_jacobian_det(const float* u_dev, float* det_dev, unsigned long long* count_dev, int B, int D, int H, int W,
+                      void* stream)
+{
+    if (!u_dev || (!det_dev && !count_dev)) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (count_dev) CK(cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long) * B, s));
+    CK(jacobian_det(u_dev, det_dev, count_dev, B, make_vol(D, H, W), s));
+    return DARC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// common.cuh -- device helpers shared by the libdarc kernels (sm_103a).
+//
+// Layout: a volume has D x H x W voxels (z, y, x), x fastest; an image is
+// float [V]; a field is planar float [3][V] (channel a = component along
+// axis a, voxel units); batches are subject-major.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace darc_impl {
+
+struct Vol {
+    int D, H, W;
+    long long V;
+};
+
+inline Vol make_vol(int D, int H, int W) { return Vol{D, H, W, (long long)D * H * W}; }
+
+// Geometry of the per-voxel kernels: a block of 32 x 8 threads covers a
+// 32 (x) x 8 (y) x TZ (z) tile, each thread walking TZ planes.
+constexpr int VT_X = 32, VT_Y = 8, VT_Z = 4, VT_THREADS = VT_X * VT_Y;
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Cell of one axis of the sample point x + u for trilinear sampling with
+// border padding: the coordinate is clamped to [0, n - 1]; the cell is
+// i = min(floor(p), n - 2) and t = p - i.  The position is formed as the
+// integer x plus floor(u) and the fraction u - floor(u), which is exact in
+// float32, so large volume coordinates cost no precision.  `clamped` marks
+// a coordinate strictly outside [0, n - 1] (derivative 0 along that axis).
+__device__ __forceinline__ void axis_cell(int x, float u, int n, int& i, float& t, bool& clamped)
+{
+    u = fminf(fmaxf(u, -1.0e6f), 1.0e6f);   // keeps NaN/Inf inside int range (they end clamped)
+    const float fl = floorf(u);
+    const int ii = x + (int)fl;
+    const float tt = u - fl;
+    if (ii < 0) {
+        i = 0; t = 0.f; clamped = true;
+    } else if (ii >= n - 1) {
+        clamped = (ii > n - 1) || (tt > 0.f);
+        i = n - 2; t = 1.f;
+    } else {
+        i = ii; t = tt; clamped = false;
+    }
+}
+
+struct Cell {
+    long long base;        // linear index of corner (iz, iy, ix)
+    float tz, ty, tx;
+    bool cz, cy, cx;       // clamped axes
+    int iz, iy, ix;
+};
+
+__device__ __forceinline__ Cell make_cell(int z, int y, int x, float uz, float uy, float ux, const Vol& v)
+{
+    Cell c;
+    axis_cell(z, uz, v.D, c.iz, c.tz, c.cz);
+    axis_cell(y, uy, v.H, c.iy, c.ty, c.cy);
+    axis_cell(x, ux, v.W, c.ix, c.tx, c.cx);
+    c.base = ((long long)c.iz * v.H + c.iy) * v.W + c.ix;
+    return c;
+}
+
+// S(f, p): trilinear value at the cell.
+__device__ __forceinline__ float tri(const float* __restrict__ f, const Cell& c, const Vol& v)
+{
+    const long long sy = v.W, sz = (long long)v.H * v.W;
+    const float* p = f + c.base;
+    const float f000 = __ldg(p), f001 = __ldg(p + 1);
+    const float f010 = __ldg(p + sy), f011 = __ldg(p + sy + 1);
+    const float f100 = __ldg(p + sz), f101 = __ldg(p + sz + 1);
+    const float f110 = __ldg(p + sz + sy), f111 = __ldg(p + sz + sy + 1);
+    const float a00 = fmaf(c.tx, f001 - f000, f000);
+    const float a01 = fmaf(c.tx, f011 - f010, f010);
+    const float a10 = fmaf(c.tx, f101 - f100, f100);
+    const float a11 = fmaf(c.tx, f111 - f110, f110);
+    const float b0 = fmaf(c.ty, a01 - a00, a00);
+    const float b1 = fmaf(c.ty, a11 - a10, a10);
+    return fmaf(c.tz, b1 - b0, b0);
+}
+
+// S(f, p) and dS/dp (0 along clamped axes).
+__device__ __forceinline__ float tri_grad(const float* __restrict__ f, const Cell& c, const Vol& v,
+                                          float& gz, float& gy, float& gx)
+{
+    const long long sy = v.W, sz = (long long)v.H * v.W;
+    const float* p = f + c.base;
+    const float f000 = __ldg(p), f001 = __ldg(p + 1);
+    const float f010 = __ldg(p + sy), f011 = __ldg(p + sy + 1);
+    const float f100 = __ldg(p + sz), f101 = __ldg(p + sz + 1);
+    const float f110 = __ldg(p + sz + sy), f111 = __ldg(p + sz + sy + 1);
+    const float d00 = f001 - f000, d01 = f011 - f010, d10 = f101 - f100, d11 = f111 - f110;
+    const float a00 = fmaf(c.tx, d00, f000);
+    const float a01 = fmaf(c.tx, d01, f010);
+    const float a10 = fmaf(c.tx, d10, f100);
+    const float a11 = fmaf(c.tx, d11, f110);
+    const float b0 = fmaf(c.ty, a01 - a00, a00);
+    const float b1 = fmaf(c.ty, a11 - a10, a10);
+    gz = c.cz ? 0.f : (b1 - b0);
+    const float e0 = a01 - a00, e1 = a11 - a10;
+    gy = c.cy ? 0.f : fmaf(c.tz, e1 - e0, e0);
+    const float h0 = fmaf(c.ty, d01 - d00, d00), h1 = fmaf(c.ty, d11 - d10, d10);
+    gx = c.cx ? 0.f : fmaf(c.tz, h1 - h0, h0);
+    return fmaf(c.tz, b1 - b0, b0);
+}
+
+// The 8 trilinear weights in corner order (dz, dy, dx) = 000, 001, 010, ...
+__device__ __forceinline__ void tri_weights(const Cell& c, float w[8])
+{
+    const float z0 = 1.f - c.tz, y0 = 1.f - c.ty, x0 = 1.f - c.tx;
+    const float zy00 = z0 * y0, zy01 = z0 * c.ty, zy10 = c.tz * y0, zy11 = c.tz * c.ty;
+    w[0] = zy00 * x0; w[1] = zy00 * c.tx;
+    w[2] = zy01 * x0; w[3] = zy01 * c.tx;
+    w[4] = zy10 * x0; w[5] = zy10 * c.tx;
+    w[6] = zy11 * x0; w[7] = zy11 * c.tx;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Block sum of a float per thread (blockDim.x*y*z a multiple of 32, <= 1024)
+// returned in double on thread 0; fixed order, so deterministic.
+__device__ __forceinline__ double block_sum(float x, double* sh /* >= 32 doubles */)
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    double d = warp_sum((double)x);
+    if ((tid & 31) == 0) sh[tid >> 5] = d;
+    __syncthreads();
+    double tot = 0.0;
+    if (tid == 0)
+        for (int k = 0; k < (nthr >> 5); ++k) tot += sh[k];
+    __syncthreads();
+    return tot;
+}
+
+}  // namespace darc_impl

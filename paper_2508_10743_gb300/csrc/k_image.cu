@@ -1,0 +1,353 @@
+// k_image.cu -- warp, MSE, diffusion regulariser, label gather, Jacobian
+// (sm_103a).
+//
+// Warp (arXiv 2508.10743, Eq. 2 "I o phi"): W(x) = S(I, x + u(x)).
+// MSE (Sec. "Dissimilarity metrics"; mean over voxels).
+// Diffusion regulariser (Eq. 2, second term), read as forward differences
+// of the displacement, a mean over each axis' voxel pairs and a mean over
+// the three axes.
+// One-shot label gather (Eq. oneshot) and the Jacobian determinant of the
+// folding rate (Sec. "Evaluation metrics").
+//
+// Per-voxel kernels: 32 x 8 threads, each walking 4 z-planes; loss partial
+// sums per block in float, stored as double, reduced in fixed order later.
+#include "kernels.h"
+
+namespace darc_impl {
+namespace {
+
+struct RegW {
+    float z, y, x;   // 1 / (3 P_a), P_a = V (n_a - 1) / n_a voxel pairs along axis a
+};
+
+RegW reg_weights(const Vol& v)
+{
+    auto w = [&](int n) { return (float)(1.0 / (3.0 * (double)v.V * (double)(n - 1) / (double)n)); };
+    return RegW{w(v.D), w(v.H), w(v.W)};
+}
+
+// Value share of voxel x (pairs counted at their lower voxel) and gradient
+// dR/du_c(x) of the regulariser.
+__device__ __forceinline__ float reg_at(const float* __restrict__ u, const Vol& v, int z, int y,
+                                        int x, long long l, const RegW& rw, float g[3])
+{
+    const long long st[3] = {(long long)v.H * v.W, (long long)v.W, 1};
+    const int q[3] = {z, y, x};
+    const int n[3] = {v.D, v.H, v.W};
+    const float ca[3] = {rw.z, rw.y, rw.x};
+    float val = 0.f;
+    g[0] = g[1] = g[2] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool up = q[a] + 1 < n[a];
+        const bool dn = q[a] > 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* uc = u + c * v.V;
+            const float cur = __ldg(uc + l);
+            const float dup = up ? __ldg(uc + l + st[a]) - cur : 0.f;
+            const float ddn = dn ? cur - __ldg(uc + l - st[a]) : 0.f;
+            val = fmaf(ca[a] * dup, dup, val);
+            g[c] = fmaf(2.f * ca[a], ddn - dup, g[c]);
+        }
+    }
+    return val;
+}
+
+__device__ __forceinline__ int block_index_in_subject(int zt)
+{
+    return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zt);
+}
+
+__global__ void __launch_bounds__(VT_THREADS)
+warp_kernel(const float* __restrict__ I, size_t I_bstride, const float* __restrict__ u,
+            float* __restrict__ out, Vol v, int nzt)
+{
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    if (x >= v.W || y >= v.H) return;
+    const float* Ib = I + (size_t)b * I_bstride;
+    const float* ub = u + (size_t)b * 3 * v.V;
+    float* ob = out + (size_t)b * v.V;
+    for (int k = 0; k < VT_Z; ++k) {
+        const int z = zt * VT_Z + k;
+        if (z >= v.D) break;
+        const long long l = ((long long)z * v.H + y) * v.W + x;
+        const Cell c = make_cell(z, y, x, __ldg(ub + l), __ldg(ub + v.V + l), __ldg(ub + 2 * v.V + l), v);
+        ob[l] = tri(Ib, c, v);
+    }
+}
+
+__global__ void __launch_bounds__(VT_THREADS)
+warp_backward_kernel(const float* __restrict__ I, size_t I_bstride, const float* __restrict__ u,
+                     const float* __restrict__ gW, float* __restrict__ gu, Vol v, int nzt)
+{
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    if (x >= v.W || y >= v.H) return;
+    const float* Ib = I + (size_t)b * I_bstride;
+    const float* ub = u + (size_t)b * 3 * v.V;
+    const float* gb = gW + (size_t)b * v.V;
+    float* ob = gu + (size_t)b * 3 * v.V;
+    for (int k = 0; k < VT_Z; ++k) {
+        const int z = zt * VT_Z + k;
+        if (z >= v.D) break;
+        const long long l = ((long long)z * v.H + y) * v.W + x;
+        const Cell c = make_cell(z, y, x, __ldg(ub + l), __ldg(ub + v.V + l), __ldg(ub + 2 * v.V + l), v);
+        float dz, dy, dx;
+        tri_grad(Ib, c, v, dz, dy, dx);
+        const float g = __ldg(gb + l);
+        ob[l] = g * dz;
+        ob[l + v.V] = g * dy;
+        ob[l + 2 * v.V] = g * dx;
+    }
+}
+
+__global__ void __launch_bounds__(VT_THREADS)
+mse_kernel(const float* __restrict__ J, const float* __restrict__ A, float* __restrict__ gJ,
+           double* __restrict__ partials, Vol v, int nzt, float invV)
+{
+    __shared__ double sh[32];
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    const float* Jb = J + (size_t)b * v.V;
+    float acc = 0.f;
+    if (x < v.W && y < v.H) {
+        for (int k = 0; k < VT_Z; ++k) {
+            const int z = zt * VT_Z + k;
+            if (z >= v.D) break;
+            const long long l = ((long long)z * v.H + y) * v.W + x;
+            const float d = __ldg(Jb + l) - __ldg(A + l);
+            acc = fmaf(d * invV, d, acc);
+            if (gJ) gJ[(size_t)b * v.V + l] = 2.f * invV * d;
+        }
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        partials[(size_t)b * gridDim.x * gridDim.y * nzt + block_index_in_subject(zt)] = s;
+}
+
+__global__ void __launch_bounds__(VT_THREADS)
+reg_kernel(const float* __restrict__ u, float* __restrict__ gu, double* __restrict__ partials,
+           Vol v, int nzt, RegW rw)
+{
+    __shared__ double sh[32];
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    const float* ub = u + (size_t)b * 3 * v.V;
+    float acc = 0.f;
+    if (x < v.W && y < v.H) {
+        for (int k = 0; k < VT_Z; ++k) {
+            const int z = zt * VT_Z + k;
+            if (z >= v.D) break;
+            const long long l = ((long long)z * v.H + y) * v.W + x;
+            float g[3];
+            acc += reg_at(ub, v, z, y, x, l, rw, g);
+            if (gu) {
+                float* gb = gu + (size_t)b * 3 * v.V;
+                gb[l] = g[0];
+                gb[l + v.V] = g[1];
+                gb[l + 2 * v.V] = g[2];
+            }
+        }
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        partials[(size_t)b * gridDim.x * gridDim.y * nzt + block_index_in_subject(zt)] = s;
+}
+
+// MSE subject step, fused: W = S(I, x + u_T), L = mean (W - A)^2,
+// gT = (2 (W - A)/V) dS(I)/dp + lambda dR/du_T; partials {L, R} per block.
+__global__ void __launch_bounds__(VT_THREADS)
+mse_warp_reg_kernel(const float* __restrict__ I, size_t I_bstride, const float* __restrict__ A,
+                    const float* __restrict__ uT, float lambda, float* __restrict__ gT,
+                    double* __restrict__ partials, Vol v, int nzt, float invV, RegW rw)
+{
+    __shared__ double sh[32];
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    const float* Ib = I + (size_t)b * I_bstride;
+    const float* ub = uT + (size_t)b * 3 * v.V;
+    float* gb = gT + (size_t)b * 3 * v.V;
+    float accL = 0.f, accR = 0.f;
+    if (x < v.W && y < v.H) {
+        for (int k = 0; k < VT_Z; ++k) {
+            const int z = zt * VT_Z + k;
+            if (z >= v.D) break;
+            const long long l = ((long long)z * v.H + y) * v.W + x;
+            const Cell c = make_cell(z, y, x, __ldg(ub + l), __ldg(ub + v.V + l), __ldg(ub + 2 * v.V + l), v);
+            float dz, dy, dx;
+            const float Wv = tri_grad(Ib, c, v, dz, dy, dx);
+            const float d = Wv - __ldg(A + l);
+            accL = fmaf(d * invV, d, accL);
+            const float gW = 2.f * invV * d;
+            float g[3];
+            accR += reg_at(ub, v, z, y, x, l, rw, g);
+            gb[l] = fmaf(gW, dz, lambda * g[0]);
+            gb[l + v.V] = fmaf(gW, dy, lambda * g[1]);
+            gb[l + 2 * v.V] = fmaf(gW, dx, lambda * g[2]);
+        }
+    }
+    const double sL = block_sum(accL, sh);
+    const double sR = block_sum(accR, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const size_t j = (size_t)b * gridDim.x * gridDim.y * nzt + block_index_in_subject(zt);
+        partials[2 * j] = sL;
+        partials[2 * j + 1] = sR;
+    }
+}
+
+__global__ void __launch_bounds__(VT_THREADS)
+label_gather_kernel(const uint8_t* __restrict__ lab, const float* __restrict__ u,
+                    uint8_t* __restrict__ out, Vol v, int nzt)
+{
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    if (x >= v.W || y >= v.H) return;
+    const float* ub = u + (size_t)b * 3 * v.V;
+    for (int k = 0; k < VT_Z; ++k) {
+        const int z = zt * VT_Z + k;
+        if (z >= v.D) break;
+        const long long l = ((long long)z * v.H + y) * v.W + x;
+        // nearest voxel: r(x + u) = x + floor(u + 1/2) for integer x, clamped
+        const int q[3] = {z, y, x};
+        const int n[3] = {v.D, v.H, v.W};
+        int r[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float ua = fminf(fmaxf(__ldg(ub + a * v.V + l), -1.0e6f), 1.0e6f);
+            int ra = q[a] + (int)floorf(ua + 0.5f);
+            r[a] = min(max(ra, 0), n[a] - 1);
+        }
+        out[(size_t)b * v.V + l] = lab[((long long)r[0] * v.H + r[1]) * v.W + r[2]];
+    }
+}
+
+__global__ void __launch_bounds__(VT_THREADS)
+jacobian_kernel(const float* __restrict__ u, float* __restrict__ det,
+                unsigned long long* __restrict__ count, Vol v, int nzt)
+{
+    __shared__ unsigned int nneg;
+    if (threadIdx.x == 0 && threadIdx.y == 0) nneg = 0;
+    __syncthreads();
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    const float* ub = u + (size_t)b * 3 * v.V;
+    unsigned int mine = 0;
+    if (x < v.W && y < v.H) {
+        const int n[3] = {v.D, v.H, v.W};
+        const long long st[3] = {(long long)v.H * v.W, (long long)v.W, 1};
+        for (int k = 0; k < VT_Z; ++k) {
+            const int z = zt * VT_Z + k;
+            if (z >= v.D) break;
+            const int q[3] = {z, y, x};
+            const long long l = ((long long)z * v.H + y) * v.W + x;
+            float J[3][3];
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+                long long lo = l, hi = l;
+                float h;
+                if (q[bb] == 0) { hi = l + st[bb]; h = 1.f; }
+                else if (q[bb] == n[bb] - 1) { lo = l - st[bb]; h = 1.f; }
+                else { lo = l - st[bb]; hi = l + st[bb]; h = 2.f; }
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    J[a][bb] = (a == bb ? 1.f : 0.f) + (__ldg(ub + a * v.V + hi) - __ldg(ub + a * v.V + lo)) / h;
+            }
+            const float d = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                            J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            if (det) det[(size_t)b * v.V + l] = d;
+            mine += (d <= 0.f);
+        }
+    }
+    if (mine) atomicAdd(&nneg, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0 && count && nneg)
+        atomicAdd(count + b, (unsigned long long)nneg);
+}
+
+dim3 vgrid(int B, const Vol& v, int& nzt)
+{
+    nzt = div_up(v.D, VT_Z);
+    return dim3(div_up(v.W, VT_X), div_up(v.H, VT_Y), nzt * B);
+}
+
+}  // namespace
+
+int voxel_blocks(const Vol& v) { return div_up(v.W, VT_X) * div_up(v.H, VT_Y) * div_up(v.D, VT_Z); }
+
+cudaError_t warp(const float* I, size_t I_bstride, const float* u, float* out, int B, const Vol& v,
+                 cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    warp_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, u, out, v, nzt);
+    return cudaGetLastError();
+}
+
+cudaError_t warp_backward(const float* I, size_t I_bstride, const float* u, const float* gW,
+                          float* gu, int B, const Vol& v, cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    warp_backward_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, u, gW, gu, v, nzt);
+    return cudaGetLastError();
+}
+
+cudaError_t mse_partials(const float* J, const float* A, float* gJ, double* partials, int B,
+                         const Vol& v, cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    mse_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(J, A, gJ, partials, v, nzt, (float)(1.0 / (double)v.V));
+    return cudaGetLastError();
+}
+
+cudaError_t reg_partials(const float* u, float* gu, double* partials, int B, const Vol& v,
+                         cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    reg_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(u, gu, partials, v, nzt, reg_weights(v));
+    return cudaGetLastError();
+}
+
+cudaError_t mse_warp_reg(const float* I, size_t I_bstride, const float* A, const float* uT,
+                         float lambda, float* gT, double* partials, int B, const Vol& v,
+                         cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    mse_warp_reg_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, A, uT, lambda, gT, partials, v,
+                                                      nzt, (float)(1.0 / (double)v.V),
+                                                      reg_weights(v));
+    return cudaGetLastError();
+}
+
+cudaError_t label_gather(const uint8_t* labels, const float* u, uint8_t* out, int B, const Vol& v,
+                         cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    label_gather_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(labels, u, out, v, nzt);
+    return cudaGetLastError();
+}
+
+cudaError_t jacobian_det(const float* u, float* det, unsigned long long* count, int B,
+                         const Vol& v, cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    jacobian_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(u, det, count, v, nzt);
+    return cudaGetLastError();
+}
+
+}  // namespace darc_impl

@@ -1,0 +1,98 @@
+// kernels.h -- host launchers of the libdarc kernels (internal interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace darc_impl {
+
+// ---- scaling and squaring (k_exp.cu) ----
+// dst[b] = u + S(u, x + u(x)) with u = scale * src[b]; B fields of [3][V].
+cudaError_t exp_square(const float* src, float scale, float* dst, int B, const Vol& v,
+                       cudaStream_t s);
+// Adjoint of one squaring: gout[b] += out_scale * (identity + Jacobian +
+// transpose-interpolation terms of gin[b]); u = scale * src[b].
+// gout must hold zeros (or a sum to add to) before the call.
+cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, float* gout,
+                               float out_scale, int B, const Vol& v, cudaStream_t s);
+
+// ---- images (k_image.cu) ----
+cudaError_t warp(const float* I, size_t I_bstride, const float* u, float* out, int B, const Vol& v,
+                 cudaStream_t s);
+cudaError_t warp_backward(const float* I, size_t I_bstride, const float* u, const float* gW,
+                          float* gu, int B, const Vol& v, cudaStream_t s);
+// partials: double [B][nblk] laid out per subject, nblk = voxel_blocks(v)
+int voxel_blocks(const Vol& v);
+cudaError_t mse_partials(const float* J, const float* A, float* gJ, double* partials, int B,
+                         const Vol& v, cudaStream_t s);
+cudaError_t reg_partials(const float* u, float* gu, double* partials, int B, const Vol& v,
+                         cudaStream_t s);
+// fused MSE subject step: from u_T and I: W, MSE, its gradient through the
+// warp, plus lambda * the regulariser gradient -> gT; partials [B][nblk][2]
+cudaError_t mse_warp_reg(const float* I, size_t I_bstride, const float* A, const float* uT,
+                         float lambda, float* gT, double* partials, int B, const Vol& v,
+                         cudaStream_t s);
+cudaError_t label_gather(const uint8_t* labels, const float* u, uint8_t* out, int B, const Vol& v,
+                         cudaStream_t s);
+cudaError_t jacobian_det(const float* u, float* det, unsigned long long* count, int B,
+                         const Vol& v, cudaStream_t s);
+
+// ---- reductions and optimiser (k_optim.cu) ----
+// out[b * out_stride + k] = scale * sum_j partials[(b * nblk + j) * nval + k], k < nval
+cudaError_t reduce_partials(const double* partials, int nblk, int nval, double scale, float* out,
+                            int out_stride, int B, cudaStream_t s);
+// cohort bookkeeping after a subject step: loss[b] = {L, R}; finite check;
+// step counts and Adam bias factors for subjects first..first+B-1
+// pL / pR: per-subject partial sums of L and R, element (b, j) at
+// p[(b * nblk + j) * stride]
+cudaError_t finish_step(const double* pL, int nblkL, int strideL, const double* pR, int nblkR,
+                        int strideR, float* loss, int* flags, int* k, float2* bias,
+                        int* nonfinite_total, float lr, float beta1, float beta2, int B,
+                        cudaStream_t s);
+// Adam on B fields [3][V] with per-subject factors bias[b] = {lr/c1, 1/sqrt(c2)};
+// skipped where flags[b] != 0 (flags may be null)
+cudaError_t adam_fields(float* theta, float* m, float* s_, const float* g, float g_scale,
+                        const float2* bias, const int* flags, float beta1, float beta2, float eps,
+                        int B, long long N, cudaStream_t st);
+cudaError_t adam_flat(float* theta, float* m, float* s_, const float* g, size_t N, float lr_c1,
+                      float inv_sqrt_c2, float beta1, float beta2, float eps, cudaStream_t st);
+int centrality_blocks(const Vol& v);
+cudaError_t centrality(float* v_all, int n, const Vol& v, double* partials, double* metrics,
+                       cudaStream_t s);
+// acc[l] (double) += sum over b of S(I[idx_b], x + u[b](x)) in fixed b order
+cudaError_t warp_accumulate(const float* I, const int* subj, const float* u, double* acc, int B,
+                            const Vol& v, cudaStream_t s);
+cudaError_t image_mean_accumulate(const float* I, int n, double* acc, const Vol& v,
+                                  cudaStream_t s);
+cudaError_t finalize_mean(const double* acc, double inv_n, float* A, const Vol& v, cudaStream_t s);
+// A -= Adam(mean_b g[b]) for the atlas SGD; g [B][V]
+cudaError_t atlas_adam(float* A, float* m, float* s_, const float* g, int B, float lr_c1,
+                       float inv_sqrt_c2, float beta1, float beta2, float eps, const Vol& v,
+                       cudaStream_t st);
+
+// ---- local NCC (k_lncc.cu) ----
+int box_blocks(const Vol& v);
+// window statistics of the atlas: stats[0] = Box(A), stats[1] = Box(A^2)
+cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, cudaStream_t s);
+// forward: box sums of J, J^2, J*A; cc; loss partials [B][nblk]; per-voxel
+// coefficients coef [B][3][V]: wrt_atlas = 0 -> dcc/d(S_J, S_JJ, S_JA),
+// 1 -> dcc/d(S_A, S_AA, S_JA).  J rows are J + subj[b]*V when subj != null.
+cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const float* stats,
+                         int r, float eps, int wrt_atlas, float* coef, double* partials, int B,
+                         const Vol& v, cudaStream_t s);
+// backward: g = -1/V [Box(c0) + 2 X Box(c1) + Y Box(c2)], X = J (Y = A) or,
+// for wrt_atlas, X = A (Y = J); writes g [B][V]
+cudaError_t lncc_backward(const float* J, const int* subj, const float* A, const float* coef,
+                          int r, int wrt_atlas, float* g, int B, const Vol& v, cudaStream_t s);
+// backward fused with the warp adjoint and the regulariser:
+// gT = gJ * dS(I, x + uT)/dp + lambda dR/du_T; reg partials [B][nblk]
+cudaError_t lncc_backward_warp_reg(const float* J, const float* A, const float* coef, int r,
+                                   const float* I, size_t I_bstride, const float* uT,
+                                   float lambda, float* gT, double* partials, int B, const Vol& v,
+                                   cudaStream_t s);
+cudaError_t sum_images(const float* g, int B, float* out, const Vol& v, cudaStream_t s);
+
+}  // namespace darc_impl

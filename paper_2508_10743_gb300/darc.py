@@ -1,0 +1,546 @@
+"""Thin Python binding of libdarc.so (include/darc.h).
+
+Argument marshalling only: every step of the registration runs in the
+library's CUDA kernels.  torch supplies device memory and the current
+stream.  If the library is missing this module raises on first use; there is
+no CPU fallback.
+
+* ``Cohort`` wraps the cohort API (Eq. 3 / Algorithm 1 of arXiv 2508.10743).
+* ``exp_forward`` ... ``jacobian_det`` wrap the operator API.
+* ``ExpSS``, ``Warp``, ``MSELoss``, ``NCCLoss``, ``DiffusionReg`` are
+  ``torch.autograd.Function``s whose backward calls the hand-written adjoint
+  kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import torch
+
+from . import configs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdarc.so")
+
+DARC_OK, DARC_ERR_ARG, DARC_ERR_SHAPE, DARC_ERR_OOM, DARC_ERR_CUDA, DARC_ERR_NONFINITE, \
+    DARC_ERR_IO, DARC_ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
+
+
+class DarcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"darc error {code}: {msg}")
+        self.code = code
+
+
+class CConfig(ctypes.Structure):
+    """Mirror of ``darc_config``."""
+    _fields_ = [
+        ("dissim", ctypes.c_int), ("ncc_window", ctypes.c_int), ("n_squarings", ctypes.c_int),
+        ("lam", ctypes.c_float), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+        ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float), ("ncc_eps", ctypes.c_float),
+        ("inner_steps", ctypes.c_int), ("atlas_epochs", ctypes.c_int), ("atlas_batch", ctypes.c_int),
+        ("center_mode", ctypes.c_int), ("checkpoint_stride", ctypes.c_int),
+        ("subject_batch", ctypes.c_int), ("reset_each_sweep", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+    ]
+
+
+class CSweepStats(ctypes.Structure):
+    """Mirror of ``darc_sweep_stats``."""
+    _fields_ = [
+        ("loss_data", ctypes.c_double), ("loss_reg", ctypes.c_double),
+        ("centrality_before", ctypes.c_double), ("centrality_after", ctypes.c_double),
+        ("atlas_loss", ctypes.c_double), ("nonfinite_subjects", ctypes.c_int),
+    ]
+
+
+_vp, _i, _f, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+_SIGS = {
+    "darc_default_config": (None, [ctypes.POINTER(CConfig)]),
+    "darc_last_error": (ctypes.c_char_p, []),
+    "darc_version": (ctypes.c_char_p, []),
+    "darc_init_cohort": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(CConfig), _i, _i, _i, _i, _vp, _vp]),
+    "darc_subject_step": (_i, [_vp, _i, _i, _i, _vp]),
+    "darc_sweep": (_i, [_vp, ctypes.POINTER(CSweepStats)]),
+    "darc_update_atlas": (_i, [_vp, ctypes.POINTER(CSweepStats)]),
+    "darc_propagate_labels": (_i, [_vp, _vp, _vp, _i, _i]),
+    "darc_get_atlas": (_i, [_vp, _vp]),
+    "darc_set_atlas": (_i, [_vp, _vp]),
+    "darc_get_velocity": (_i, [_vp, _i, _vp]),
+    "darc_set_velocity": (_i, [_vp, _i, _vp]),
+    "darc_get_adam_state": (_i, [_vp, _i, _vp, _vp, ctypes.POINTER(_i)]),
+    "darc_cohort_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                              ctypes.POINTER(_i), ctypes.POINTER(CConfig)]),
+    "darc_save": (_i, [_vp, ctypes.c_char_p]),
+    "darc_load": (_i, [ctypes.POINTER(_vp), ctypes.c_char_p, _vp, _vp]),
+    "darc_destroy": (None, [_vp]),
+    "darc_exp_forward": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
+    "darc_exp_backward_workspace": (_sz, [_i, _i, _i, _i]),
+    "darc_exp_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
+    "darc_warp": (_i, [_vp, _i, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_warp_backward": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_loss_workspace": (_sz, [_i, _i, _i, _i]),
+    "darc_mse": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_lncc_workspace": (_sz, [_i, _i, _i, _i]),
+    "darc_lncc": (_i, [_vp, _vp, _i, _f, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_diffusion_reg": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_subject_grad_workspace": (_sz, [ctypes.POINTER(CConfig), _i, _i, _i, _i]),
+    "darc_subject_grad": (_i, [ctypes.POINTER(CConfig), _vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _i,
+                               _i, _vp]),
+    "darc_adam": (_i, [_vp, _vp, _vp, _vp, _sz, _i, _f, _f, _f, _f, _vp]),
+    "darc_centrality_workspace": (_sz, [_i, _i, _i, _i]),
+    "darc_centrality": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_atlas_mean_workspace": (_sz, [_i, _i, _i, _i]),
+    "darc_atlas_mean": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "darc_label_gather": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_jacobian_det": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_set_profiling": (_i, [_vp, _i]),
+    "darc_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                               ctypes.POINTER(ctypes.c_double)]),
+    "darc_launch_count": (ctypes.c_longlong, [_vp]),
+}
+
+KERNEL_IDS = {"exp_square": 0, "exp_adjoint": 1, "warp": 2, "lncc_fwd": 3, "lncc_bwd_warp_reg": 4,
+              "mse_warp_reg": 5, "adam": 6, "atlas": 7}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libdarc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libdarc.so not built ({LIB_PATH}); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _check(rc: int):
+    if rc != DARC_OK:
+        raise DarcError(rc, lib().darc_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+def _work(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def to_cconfig(cfg: configs.DarcConfig) -> CConfig:
+    return CConfig(cfg.dissim, cfg.ncc_window, cfg.n_squarings, cfg.lam, cfg.lr, cfg.beta1,
+                   cfg.beta2, cfg.adam_eps, cfg.ncc_eps, cfg.inner_steps, cfg.atlas_epochs,
+                   cfg.atlas_batch, cfg.center_mode, cfg.checkpoint_stride, cfg.subject_batch,
+                   cfg.reset_each_sweep, cfg.seed)
+
+
+def version() -> str:
+    return lib().darc_version().decode()
+
+
+def default_config() -> CConfig:
+    c = CConfig()
+    lib().darc_default_config(ctypes.byref(c))
+    return c
+
+
+# ---------------------------------------------------------------------------
+# cohort
+# ---------------------------------------------------------------------------
+
+
+class Cohort:
+    """A cohort of subjects on the GPU (Eq. 3, Algorithm 1).
+
+    images: CUDA float32 [n, D, H, W]; kept alive by this object."""
+
+    def __init__(self, images: torch.Tensor, cfg: configs.DarcConfig, _handle=None):
+        _need(images, "images")
+        self.images = images
+        self.cfg = cfg
+        self.n, self.D, self.H, self.W = (int(s) for s in images.shape)
+        self.device = images.device
+        if _handle is not None:
+            self._h = _handle
+            return
+        h = ctypes.c_void_p()
+        cc = to_cconfig(cfg)
+        _check(lib().darc_init_cohort(ctypes.byref(h), ctypes.byref(cc), self.n, self.D, self.H,
+                                      self.W, _ptr(images), _stream()))
+        self._h = h
+
+    @property
+    def shape(self):
+        return (self.D, self.H, self.W)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().darc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def subject_step(self, first: int = 0, count: Optional[int] = None, steps: int = 1,
+                     want_loss: bool = False):
+        count = self.n - first if count is None else count
+        if want_loss:
+            out = (ctypes.c_float * count)()
+            _check(lib().darc_subject_step(self._h, first, count, steps, ctypes.cast(out, ctypes.c_void_p)))
+            return list(out)
+        _check(lib().darc_subject_step(self._h, first, count, steps, None))
+        return None
+
+    def sweep(self, stats: bool = True):
+        st = CSweepStats()
+        _check(lib().darc_sweep(self._h, ctypes.byref(st) if stats else None))
+        if not stats:
+            return None
+        return {k: getattr(st, k) for k, _ in CSweepStats._fields_}
+
+    def update_atlas(self, stats: bool = True):
+        st = CSweepStats()
+        _check(lib().darc_update_atlas(self._h, ctypes.byref(st) if stats else None))
+        return {k: getattr(st, k) for k, _ in CSweepStats._fields_} if stats else None
+
+    def propagate_labels(self, atlas_labels: torch.Tensor, first: int = 0,
+                         count: Optional[int] = None) -> torch.Tensor:
+        _need(atlas_labels, "atlas_labels", torch.uint8)
+        count = self.n - first if count is None else count
+        out = torch.empty((count, self.D, self.H, self.W), dtype=torch.uint8, device=self.device)
+        _check(lib().darc_propagate_labels(self._h, _ptr(atlas_labels), _ptr(out), first, count))
+        return out
+
+    def atlas(self) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        _check(lib().darc_get_atlas(self._h, _ptr(out)))
+        return out
+
+    def set_atlas(self, A: torch.Tensor):
+        _need(A, "atlas")
+        _check(lib().darc_set_atlas(self._h, _ptr(A)))
+
+    def velocity(self, i: int) -> torch.Tensor:
+        out = torch.empty((3, *self.shape), dtype=torch.float32, device=self.device)
+        _check(lib().darc_get_velocity(self._h, i, _ptr(out)))
+        return out
+
+    def velocities(self) -> torch.Tensor:
+        return torch.stack([self.velocity(i) for i in range(self.n)])
+
+    def set_velocity(self, i: int, v: torch.Tensor):
+        _need(v, "velocity")
+        _check(lib().darc_set_velocity(self._h, i, _ptr(v)))
+
+    def adam_state(self, i: int):
+        m = torch.empty((3, *self.shape), dtype=torch.float32, device=self.device)
+        s = torch.empty_like(m)
+        k = ctypes.c_int(0)
+        _check(lib().darc_get_adam_state(self._h, i, _ptr(m), _ptr(s), ctypes.byref(k)))
+        return m, s, k.value
+
+    def set_profiling(self, on: bool):
+        _check(lib().darc_set_profiling(self._h, int(on)))
+
+    def profile(self):
+        """{family: (total_ms, launches, algorithmic bytes)} since the last read."""
+        out = {}
+        for name, kid in KERNEL_IDS.items():
+            ms, n, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            _check(lib().darc_profile_read(self._h, kid, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
+            out[name] = (ms.value, n.value, by.value)
+        return out
+
+    def launch_count(self) -> int:
+        return int(lib().darc_launch_count(self._h))
+
+    def save(self, path: str):
+        _check(lib().darc_save(self._h, path.encode()))
+
+    @classmethod
+    def load(cls, path: str, images: torch.Tensor, cfg: Optional[configs.DarcConfig] = None):
+        _need(images, "images")
+        h = ctypes.c_void_p()
+        _check(lib().darc_load(ctypes.byref(h), path.encode(), _ptr(images), _stream()))
+        cc = CConfig()
+        lib().darc_cohort_info(h, None, None, None, None, ctypes.byref(cc))
+        dc = configs.DarcConfig(**{f.name: getattr(cc, f.name)
+                                   for f in configs.dataclasses.fields(configs.DarcConfig)})
+        return cls(images, cfg or dc, _handle=h)
+
+
+# ---------------------------------------------------------------------------
+# operator API
+# ---------------------------------------------------------------------------
+
+
+def _dims(t: torch.Tensor):
+    return tuple(int(s) for s in t.shape[-3:])
+
+
+def exp_forward(v: torch.Tensor, T: int, sign: float = 1.0) -> torch.Tensor:
+    """u_1..u_T of scaling and squaring, [T, B, 3, D, H, W] for v [B, 3, D, H, W]."""
+    _need(v, "v")
+    B = v.shape[0]
+    D, H, W = _dims(v)
+    u = torch.empty((T, B, 3, D, H, W), dtype=torch.float32, device=v.device)
+    _check(lib().darc_exp_forward(_ptr(v), _ptr(u), B, D, H, W, T, sign, _stream()))
+    return u
+
+
+def exp_backward(v: torch.Tensor, u: torch.Tensor, gT: torch.Tensor, sign: float = 1.0) -> torch.Tensor:
+    for t, nm in ((v, "v"), (u, "u"), (gT, "gT")):
+        _need(t, nm)
+    B = v.shape[0]
+    D, H, W = _dims(v)
+    T = u.shape[0]
+    gv = torch.empty_like(v)
+    work = _work(lib().darc_exp_backward_workspace(B, D, H, W), v.device)
+    _check(lib().darc_exp_backward(_ptr(v), _ptr(u), _ptr(gT), _ptr(gv), _ptr(work), B, D, H, W, T,
+                                   sign, _stream()))
+    return gv
+
+
+def warp(I: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+    """W[b] = S(I[b], x + u[b](x)); I [B, D, H, W] or [D, H, W] (shared)."""
+    _need(I, "I")
+    _need(u, "u")
+    B = u.shape[0]
+    D, H, W = _dims(u)
+    out = torch.empty((B, D, H, W), dtype=torch.float32, device=u.device)
+    _check(lib().darc_warp(_ptr(I), int(I.dim() == 3), _ptr(u), _ptr(out), B, D, H, W, _stream()))
+    return out
+
+
+def warp_backward(I: torch.Tensor, u: torch.Tensor, gW: torch.Tensor) -> torch.Tensor:
+    for t, nm in ((I, "I"), (u, "u"), (gW, "gW")):
+        _need(t, nm)
+    B = u.shape[0]
+    D, H, W = _dims(u)
+    gu = torch.empty_like(u)
+    _check(lib().darc_warp_backward(_ptr(I), int(I.dim() == 3), _ptr(u), _ptr(gW), _ptr(gu), B, D,
+                                    H, W, _stream()))
+    return gu
+
+
+def mse(J: torch.Tensor, A: torch.Tensor, want_grad: bool = True):
+    _need(J, "J")
+    _need(A, "A")
+    B = J.shape[0]
+    D, H, W = _dims(J)
+    loss = torch.empty(B, dtype=torch.float32, device=J.device)
+    gJ = torch.empty_like(J) if want_grad else None
+    work = _work(lib().darc_loss_workspace(B, D, H, W), J.device)
+    _check(lib().darc_mse(_ptr(J), _ptr(A), _ptr(loss), _ptr(gJ), _ptr(work), B, D, H, W, _stream()))
+    return loss, gJ
+
+
+def lncc(J: torch.Tensor, A: torch.Tensor, window: int, eps: float = 1e-5, grad_J: bool = True,
+         grad_A: bool = False):
+    _need(J, "J")
+    _need(A, "A")
+    B = J.shape[0]
+    D, H, W = _dims(J)
+    loss = torch.empty(B, dtype=torch.float32, device=J.device)
+    gJ = torch.empty_like(J) if grad_J else None
+    gA = torch.empty_like(A) if grad_A else None
+    work = _work(lib().darc_lncc_workspace(B, D, H, W), J.device)
+    _check(lib().darc_lncc(_ptr(J), _ptr(A), window, eps, _ptr(loss), _ptr(gJ), _ptr(gA), _ptr(work),
+                           B, D, H, W, _stream()))
+    return loss, gJ, gA
+
+
+def diffusion_reg(u: torch.Tensor, want_grad: bool = True):
+    _need(u, "u")
+    B = u.shape[0]
+    D, H, W = _dims(u)
+    loss = torch.empty(B, dtype=torch.float32, device=u.device)
+    gu = torch.empty_like(u) if want_grad else None
+    work = _work(lib().darc_loss_workspace(B, D, H, W), u.device)
+    _check(lib().darc_diffusion_reg(_ptr(u), _ptr(loss), _ptr(gu), _ptr(work), B, D, H, W, _stream()))
+    return loss, gu
+
+
+def subject_grad(cfg: configs.DarcConfig, I: torch.Tensor, A: torch.Tensor, v: torch.Tensor):
+    """({L, R} per subject [B, 2], dE/dv) without the optimiser step."""
+    for t, nm in ((I, "I"), (A, "A"), (v, "v")):
+        _need(t, nm)
+    B = v.shape[0]
+    D, H, W = _dims(v)
+    cc = to_cconfig(cfg)
+    energy = torch.empty((B, 2), dtype=torch.float32, device=v.device)
+    gv = torch.empty_like(v)
+    work = _work(lib().darc_subject_grad_workspace(ctypes.byref(cc), B, D, H, W), v.device)
+    _check(lib().darc_subject_grad(ctypes.byref(cc), _ptr(I), _ptr(A), _ptr(v), _ptr(energy), _ptr(gv),
+                                   _ptr(work), B, D, H, W, _stream()))
+    return energy, gv
+
+
+def adam(theta, m, s, g, k: int, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+    for t, nm in ((theta, "theta"), (m, "m"), (s, "s"), (g, "g")):
+        _need(t, nm)
+    _check(lib().darc_adam(_ptr(theta), _ptr(m), _ptr(s), _ptr(g), theta.numel(), k, lr, beta1, beta2,
+                           eps, _stream()))
+
+
+def centrality(v: torch.Tensor) -> torch.Tensor:
+    """In place on v [n, 3, D, H, W]; returns metrics [before, after] (float64)."""
+    _need(v, "v")
+    n = v.shape[0]
+    D, H, W = _dims(v)
+    metrics = torch.empty(2, dtype=torch.float64, device=v.device)
+    work = _work(lib().darc_centrality_workspace(n, D, H, W), v.device)
+    _check(lib().darc_centrality(_ptr(v), _ptr(metrics), _ptr(work), n, D, H, W, _stream()))
+    return metrics
+
+
+def atlas_mean(I: torch.Tensor, v: torch.Tensor, T: int) -> torch.Tensor:
+    _need(I, "I")
+    _need(v, "v")
+    n = v.shape[0]
+    D, H, W = _dims(v)
+    A = torch.empty((D, H, W), dtype=torch.float32, device=v.device)
+    work = _work(lib().darc_atlas_mean_workspace(n, D, H, W), v.device)
+    _check(lib().darc_atlas_mean(_ptr(I), _ptr(v), _ptr(A), _ptr(work), n, D, H, W, T, _stream()))
+    return A
+
+
+def label_gather(labels: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+    _need(labels, "labels", torch.uint8)
+    _need(u, "u")
+    B = u.shape[0]
+    D, H, W = _dims(u)
+    out = torch.empty((B, D, H, W), dtype=torch.uint8, device=u.device)
+    _check(lib().darc_label_gather(_ptr(labels), _ptr(u), _ptr(out), B, D, H, W, _stream()))
+    return out
+
+
+def jacobian_det(u: torch.Tensor):
+    _need(u, "u")
+    B = u.shape[0]
+    D, H, W = _dims(u)
+    det = torch.empty((B, D, H, W), dtype=torch.float32, device=u.device)
+    cnt = torch.empty(B, dtype=torch.int64, device=u.device)
+    _check(lib().darc_jacobian_det(_ptr(u), _ptr(det), _ptr(cnt), B, D, H, W, _stream()))
+    return det, cnt
+
+
+# ---------------------------------------------------------------------------
+# autograd wrappers (hand-written backward kernels)
+# ---------------------------------------------------------------------------
+
+
+class ExpSS(torch.autograd.Function):
+    """phi = Exp(v) by scaling and squaring; returns the displacement u_T."""
+
+    @staticmethod
+    def forward(ctx, v, T: int, sign: float = 1.0):
+        v = v.contiguous()
+        u = exp_forward(v, T, sign)
+        ctx.save_for_backward(v, u)
+        ctx.sign = sign
+        return u[-1]
+
+    @staticmethod
+    def backward(ctx, g):
+        v, u = ctx.saved_tensors
+        return exp_backward(v, u, g.contiguous(), ctx.sign), None, None
+
+
+class Warp(torch.autograd.Function):
+    """I o (id + u); differentiable in u (the images are data)."""
+
+    @staticmethod
+    def forward(ctx, I, u):
+        I, u = I.contiguous(), u.contiguous()
+        ctx.save_for_backward(I, u)
+        return warp(I, u)
+
+    @staticmethod
+    def backward(ctx, g):
+        I, u = ctx.saved_tensors
+        return None, warp_backward(I, u, g.contiguous())
+
+
+class MSELoss(torch.autograd.Function):
+    """Per-subject MSE to the atlas, [B]."""
+
+    @staticmethod
+    def forward(ctx, J, A):
+        loss, gJ = mse(J.contiguous(), A.contiguous())
+        ctx.save_for_backward(gJ)
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        (gJ,) = ctx.saved_tensors
+        return gJ * g.view(-1, 1, 1, 1), None
+
+
+class NCCLoss(torch.autograd.Function):
+    """Per-subject local NCC loss -1/V sum cc, [B]; differentiable in J and A."""
+
+    @staticmethod
+    def forward(ctx, J, A, window: int, eps: float = 1e-5):
+        J, A = J.contiguous(), A.contiguous()
+        loss, _, _ = lncc(J, A, window, eps, grad_J=False, grad_A=False)
+        ctx.save_for_backward(J, A)
+        ctx.window, ctx.eps = window, eps
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        J, A = ctx.saved_tensors
+        need_J, need_A = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gJ = gA = None
+        if need_J:
+            # per-subject weights: run per subject when they differ
+            _, gJ, _ = lncc(J, A, ctx.window, ctx.eps, grad_J=True, grad_A=False)
+            gJ = gJ * g.view(-1, 1, 1, 1)
+        if need_A:
+            parts = []
+            for b in range(J.shape[0]):
+                _, _, gAb = lncc(J[b:b + 1].contiguous(), A, ctx.window, ctx.eps, grad_J=False, grad_A=True)
+                parts.append(gAb * g[b])
+            gA = torch.stack(parts).sum(0)
+        return gJ, gA, None, None
+
+
+class DiffusionReg(torch.autograd.Function):
+    """Per-subject diffusion regulariser of the displacement, [B]."""
+
+    @staticmethod
+    def forward(ctx, u):
+        loss, gu = diffusion_reg(u.contiguous())
+        ctx.save_for_backward(gu)
+        return loss
+
+    @staticmethod
+    def backward(ctx, g):
+        (gu,) = ctx.saved_tensors
+        return gu * g.view(-1, 1, 1, 1, 1)

@@ -1,0 +1,91 @@
+"""The C ABI of libdarc.so, checked without a GPU: the library builds and
+loads, exports every function include/darc.h declares, the Python binding
+binds each of them, the struct layouts agree, and host-side argument checks
+reject bad calls before any CUDA work is enqueued."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "darc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(darc_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def darc():
+    from paper_2508_10743_gb300 import build
+    build.build()
+    from paper_2508_10743_gb300 import darc as d
+    d.lib()
+    return d
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("darc_init_cohort", "darc_subject_step", "darc_sweep", "darc_update_atlas",
+                     "darc_propagate_labels", "darc_destroy", "darc_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(darc):
+    lib = ctypes.CDLL(darc.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(darc):
+    assert set(declared_functions()) == set(darc._SIGS)
+
+
+def test_struct_layouts(darc):
+    assert ctypes.sizeof(darc.CConfig) == 72
+    assert darc.CConfig.seed.offset == 64
+    assert ctypes.sizeof(darc.CSweepStats) == 48
+    c = darc.default_config()
+    assert (c.dissim, c.ncc_window, c.n_squarings) == (1, 9, 7)
+    assert c.lr == pytest.approx(1e-2) and c.atlas_epochs == 20 and c.atlas_batch == 4
+    assert "sm_103a" in darc.version()
+
+
+def test_host_argument_checks(darc):
+    L = darc.lib()
+    cfg = darc.default_config()
+    h = ctypes.c_void_p()
+    assert L.darc_init_cohort(ctypes.byref(h), ctypes.byref(cfg), 2, 8, 8, 8, None, None) == darc.DARC_ERR_ARG
+    fake = ctypes.c_void_p(0x1000)
+    assert L.darc_init_cohort(ctypes.byref(h), ctypes.byref(cfg), 2, 1, 8, 8, fake, None) == darc.DARC_ERR_SHAPE
+    cfg.ncc_window = 8
+    assert L.darc_init_cohort(ctypes.byref(h), ctypes.byref(cfg), 2, 16, 16, 16, fake, None) == darc.DARC_ERR_SHAPE
+    cfg.ncc_window = 9
+    assert L.darc_init_cohort(ctypes.byref(h), ctypes.byref(cfg), 2, 8, 16, 16, fake, None) == darc.DARC_ERR_SHAPE
+    assert "window" in L.darc_last_error().decode()
+    cfg.ncc_window, cfg.n_squarings = 5, 0
+    assert L.darc_init_cohort(ctypes.byref(h), ctypes.byref(cfg), 2, 8, 16, 16, fake, None) == darc.DARC_ERR_ARG
+    assert L.darc_exp_forward(fake, fake, 0, 8, 8, 8, 7, 1.0, None) == darc.DARC_ERR_ARG
+    assert L.darc_exp_forward(fake, fake, 1, 8, 8, 8, 0, 1.0, None) == darc.DARC_ERR_ARG
+    assert L.darc_lncc(fake, fake, 4, 1e-5, fake, None, None, fake, 1, 8, 8, 8, None) == darc.DARC_ERR_SHAPE
+    assert L.darc_adam(fake, fake, fake, fake, 10, 0, 1e-2, 0.9, 0.999, 1e-8, None) == darc.DARC_ERR_ARG
+    assert L.darc_subject_step(None, 0, 1, 1, None) == darc.DARC_ERR_ARG
+
+
+def test_workspace_queries_are_host_only(darc):
+    L = darc.lib()
+    assert L.darc_exp_backward_workspace(2, 8, 8, 8) == 2 * (2 * 3 * 512 * 4)
+    assert L.darc_lncc_workspace(1, 16, 16, 16) > 4 * 16 ** 3 * 6
+    cfg = darc.default_config()
+    assert L.darc_subject_grad_workspace(ctypes.byref(cfg), 1, 16, 16, 16) > 4 * 3 * 16 ** 3 * 7
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    from paper_2508_10743_gb300 import darc as d
+    monkeypatch.setattr(d, "_lib", None)
+    monkeypatch.setattr(d, "LIB_PATH", "/nonexistent/libdarc.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        d.lib()
