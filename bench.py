@@ -212,10 +212,12 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     ev0.record()
     for _ in range(args.steps):
         c.sweep(stats=False)
     ev1.record()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()

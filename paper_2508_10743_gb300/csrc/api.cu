@@ -205,6 +205,8 @@ struct darc_cohort {
     float *u_all = nullptr, *gT = nullptr, *gbuf = nullptr, *Wimg = nullptr, *coef = nullptr;
     double *pL = nullptr, *pR = nullptr, *acc = nullptr, *cpart = nullptr, *cmetrics = nullptr;
     float *Wcache = nullptr, *Am = nullptr, *As = nullptr, *gA = nullptr, *aloss = nullptr;
+    float *jstats = nullptr, *gsh = nullptr;   // [n][2][V] window stats of W_i; [V] shared gradient
+    float* boxbuf = nullptr;                   // [max(bmax, atlas batch)][3][V] 2-D window sums
     int *perm_dev = nullptr, *iota_dev = nullptr;
     int* perm_host = nullptr;    // pinned [K3][n]
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
@@ -341,12 +343,13 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
         }
         if (e == cudaSuccess) {
             Prof p(c, s, DARC_K_LNCC_FWD, 28.0 * nv);
-            e = lncc_forward(c->Wimg, nullptr, c->A, c->astats, r, c->cfg.ncc_eps, 0, c->coef, c->pL, cnt, vol, s);
+            e = lncc_forward(c->Wimg, nullptr, c->A, c->astats, r, c->cfg.ncc_eps, 0, c->coef, c->pL, cnt, vol,
+                             c->boxbuf, s);
         }
         if (e == cudaSuccess) {
             Prof p(c, s, DARC_K_LNCC_BWD_WARP_REG, 48.0 * nv);
             e = lncc_backward_warp_reg(c->Wimg, c->A, c->coef, r, Ib, vol.V, uT, c->cfg.lambda, c->gT,
-                                       c->pR, cnt, vol, s);
+                                       c->pR, cnt, vol, c->boxbuf, s);
         }
         pLp = c->pL; pRp = c->pR; nL = nR = box_blocks(vol); sL = sR = 1;
         c->launches += 3;
@@ -432,11 +435,11 @@ int update_atlas_impl(darc_cohort* c)
     // algorithmic bytes: centrality 24n + 12 per voxel; warped cohort (24T + 20) n;
     // NCC SGD per mini-batch: statistics 12 + per subject 28 + 20 + Adam 24
     double bytes = (24.0 * n + 12.0) + (24.0 * T + 20.0) * n;
-    if (c->cfg.dissim == DARC_LNCC) bytes += (double)K3 * (nbatch * (12.0 + 24.0) + n * 48.0);
+    if (c->cfg.dissim == DARC_LNCC) bytes += 12.0 * n + (double)K3 * (nbatch * (12.0 + 24.0) + n * 48.0);
     Prof p(c, c->st, DARC_K_ATLAS, bytes * (double)vol.V);
     const long long chunks = (n + c->bmax - 1) / c->bmax;
     c->launches += 2 + chunks * (T + 1) +
-                   (c->cfg.dissim == DARC_LNCC ? (long long)K3 * nbatch * 5 + 1 : 1);
+                   (c->cfg.dissim == DARC_LNCC ? chunks + (long long)K3 * nbatch * 6 + 1 : 1);
     return update_atlas_body(c);
 }
 
@@ -466,6 +469,12 @@ int update_atlas_body(darc_cohort* c)
     }
     const int K3 = c->cfg.atlas_epochs, B = c->cfg.atlas_batch, r = c->cfg.ncc_window / 2;
     if (K3 > 0) {
+        // Box(W_i), Box(W_i^2) do not depend on A: once per atlas update
+        for (int f = 0; f < n; f += c->bmax) {
+            const int cnt = std::min(c->bmax, n - f);
+            CK(image_stats(c->Wcache + (size_t)f * vol.V, c->jstats + (size_t)f * 2 * vol.V, cnt, r, vol,
+                           c->boxbuf, s));
+        }
         CK(cudaEventSynchronize(c->ev_perm));   // the previous upload has left perm_host
         for (int ep = 0; ep < K3; ++ep) minibatch_order(c->cfg.seed, c->sweep, ep, n, c->perm_host + (size_t)ep * n);
         CK(cudaMemcpyAsync(c->perm_dev, c->perm_host, sizeof(int) * (size_t)K3 * n, cudaMemcpyHostToDevice, s));
@@ -477,19 +486,22 @@ int update_atlas_body(darc_cohort* c)
             for (int b0 = 0; b0 < n; b0 += B) {
                 const int nb = std::min(B, n - b0);
                 const int* subj = c->perm_dev + (size_t)ep * n + b0;
-                CK(atlas_stats(c->A, c->astats, r, vol, s));
-                CK(lncc_forward(c->Wcache, subj, c->A, c->astats, r, c->cfg.ncc_eps, 1, c->coef, c->pL, nb, vol, s));
+                CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));
+                CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps, c->coef,
+                                     c->pL, nb, vol, c->boxbuf, s));
                 CK(reduce_partials(c->pL, box_blocks(vol), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
-                CK(lncc_backward(c->Wcache, subj, c->A, c->coef, r, 1, c->gA, nb, vol, s));
+                CK(atlas_sgd_backward(c->Wcache, subj, c->A, c->coef, r, c->gsh, c->gA, nb, vol, c->boxbuf, s));
                 ++kk;
                 const double c1 = 1.0 - std::pow((double)c->cfg.beta1, kk);
                 const double c2 = 1.0 - std::pow((double)c->cfg.beta2, kk);
-                CK(atlas_adam(c->A, c->Am, c->As, c->gA, nb, (float)(c->cfg.lr / c1), (float)(1.0 / std::sqrt(c2)),
-                              c->cfg.beta1, c->cfg.beta2, c->cfg.adam_eps, vol, s));
+                // mean over the batch of dL_i/dA = -1/V [gshared + sum_b gsubj_b] / nb
+                CK(atlas_adam(c->A, c->Am, c->As, c->gsh, c->gA, nb, (float)(-1.0 / ((double)vol.V * nb)),
+                              (float)(c->cfg.lr / c1), (float)(1.0 / std::sqrt(c2)), c->cfg.beta1,
+                              c->cfg.beta2, c->cfg.adam_eps, vol, s));
             }
         }
     }
-    CK(atlas_stats(c->A, c->astats, r, vol, s));
+    CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));
     return DARC_OK;
 }
 
@@ -595,12 +607,15 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     ALLOC(c->iota_dev, n);
     if (cfg->dissim == DARC_LNCC) {
         ALLOC(c->astats, 2 * v.V);
+        ALLOC(c->boxbuf, 3 * (size_t)v.V * bsub);
         ALLOC(c->Wimg, (size_t)v.V * c->bmax);
         ALLOC(c->coef, 3 * (size_t)v.V * bsub);
         ALLOC(c->Wcache, (size_t)v.V * n);
         ALLOC(c->Am, v.V);
         ALLOC(c->As, v.V);
         ALLOC(c->gA, (size_t)v.V * cfg->atlas_batch);
+        ALLOC(c->gsh, (size_t)v.V);
+        ALLOC(c->jstats, 2 * (size_t)v.V * n);
         ALLOC(c->aloss, (size_t)std::max(cfg->atlas_epochs, 1) * n);
         ALLOC(c->perm_dev, (size_t)std::max(cfg->atlas_epochs, 1) * n);
         if (cudaMallocHost(&c->perm_host, sizeof(int) * (size_t)std::max(cfg->atlas_epochs, 1) * n) != cudaSuccess) {
@@ -627,7 +642,7 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
         cudaMemsetAsync(c->cmetrics, 0, sizeof(double) * 2, s) == cudaSuccess &&
         image_mean_accumulate(images_dev, n, c->acc, v, s) == cudaSuccess &&
         finalize_mean(c->acc, 1.0 / n, c->A, v, s) == cudaSuccess &&
-        (cfg->dissim != DARC_LNCC || atlas_stats(c->A, c->astats, cfg->ncc_window / 2, v, s) == cudaSuccess) &&
+        (cfg->dissim != DARC_LNCC || atlas_stats(c->A, c->astats, cfg->ncc_window / 2, v, c->boxbuf, s) == cudaSuccess) &&
         cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) {
         cudaError_t e = cudaGetLastError();
@@ -748,7 +763,7 @@ int darc_set_atlas(darc_cohort* c, const float* atlas_dev)
     int rc = begin(c);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->A, atlas_dev, sizeof(float) * c->vol.V, cudaMemcpyDeviceToDevice, c->st));
-    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->st));
+    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
     return end(c);
 }
 
@@ -866,7 +881,7 @@ int darc_load(darc_cohort** out, const char* path, const float* images_dev, void
                  cudaMemcpy(arr + i * F, buf.data(), sizeof(float) * F, cudaMemcpyHostToDevice) == cudaSuccess;
     std::fclose(fp);
     if (ok && cfg.dissim == DARC_LNCC)
-        ok = atlas_stats(c->A, c->astats, cfg.ncc_window / 2, c->vol, c->st) == cudaSuccess &&
+        ok = atlas_stats(c->A, c->astats, cfg.ncc_window / 2, c->vol, c->boxbuf, c->st) == cudaSuccess &&
              cudaStreamSynchronize(c->st) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -1000,7 +1015,8 @@ size_t darc_lncc_workspace(int B, int D, int H, int W)
 {
     const Vol v = make_vol(D, H, W);
     return align256(sizeof(float) * 2 * (size_t)v.V) + align256(sizeof(float) * 3 * (size_t)B * v.V) +
-           align256(sizeof(float) * (size_t)B * v.V) + darc_loss_workspace(B, D, H, W);
+           align256(sizeof(float) * (size_t)B * v.V) + darc_loss_workspace(B, D, H, W) +
+           align256(sizeof(float) * 3 * (size_t)B * v.V);
 }
 
 int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, float* loss_dev, float* gJ_dev,
@@ -1019,13 +1035,14 @@ int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, flo
     float* coef = cv.take<float>(3 * (size_t)B * v.V);
     float* gAb = cv.take<float>((size_t)B * v.V);
     double* part = cv.take<double>(2 * (size_t)B * nblk_max(v));
-    CK(atlas_stats(A_dev, stats, r, v, s));
-    CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 0, coef, part, B, v, s));
+    float* P = cv.take<float>(3 * (size_t)B * v.V);
+    CK(atlas_stats(A_dev, stats, r, v, P, s));
+    CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 0, coef, part, B, v, P, s));
     CK(reduce_partials(part, box_blocks(v), 1, 1.0, loss_dev, 1, B, s));
-    if (gJ_dev) CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 0, gJ_dev, B, v, s));
+    if (gJ_dev) CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 0, gJ_dev, B, v, P, s));
     if (gA_dev) {
-        CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 1, coef, part, B, v, s));
-        CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 1, gAb, B, v, s));
+        CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 1, coef, part, B, v, P, s));
+        CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 1, gAb, B, v, P, s));
         CK(sum_images(gAb, B, gA_dev, v, s));
     }
     return DARC_OK;
@@ -1052,7 +1069,7 @@ size_t darc_subject_grad_workspace(const darc_config* cfg, int B, int D, int H, 
     const int T = std::max(cfg->n_squarings, 1);
     return align256(sizeof(float) * F * T) + align256(sizeof(float) * F) + 2 * align256(sizeof(float) * F) +
            align256(sizeof(float) * V * B) + align256(sizeof(float) * 3 * V * B) + align256(sizeof(float) * 2 * V) +
-           2 * darc_loss_workspace(B, D, H, W);
+           2 * darc_loss_workspace(B, D, H, W) + align256(sizeof(float) * 3 * V * B);
 }
 
 int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A_dev, const float* v_dev,
@@ -1076,6 +1093,7 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     float* stats = cv.take<float>(2 * (size_t)v.V);
     double* pL = cv.take<double>(2 * (size_t)B * nblk_max(v));
     double* pR = cv.take<double>(2 * (size_t)B * nblk_max(v));
+    float* P = cv.take<float>(3 * (size_t)B * v.V);
     CK(exp_forward_all(v_dev, u_all, B, v, T, 1.f, s));
     const float* uT = u_all + (size_t)(T - 1) * F;
     if (cfg->dissim == DARC_MSE) {
@@ -1083,10 +1101,10 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
         CK(reduce_partials(pL, voxel_blocks(v), 2, 1.0, energy_dev, 2, B, s));
     } else {
         const int r = cfg->ncc_window / 2;
-        CK(atlas_stats(A_dev, stats, r, v, s));
+        CK(atlas_stats(A_dev, stats, r, v, P, s));
         CK(warp(I_dev, v.V, uT, Wimg, B, v, s));
-        CK(lncc_forward(Wimg, nullptr, A_dev, stats, r, cfg->ncc_eps, 0, coef, pL, B, v, s));
-        CK(lncc_backward_warp_reg(Wimg, A_dev, coef, r, I_dev, v.V, uT, cfg->lambda, gT, pR, B, v, s));
+        CK(lncc_forward(Wimg, nullptr, A_dev, stats, r, cfg->ncc_eps, 0, coef, pL, B, v, P, s));
+        CK(lncc_backward_warp_reg(Wimg, A_dev, coef, r, I_dev, v.V, uT, cfg->lambda, gT, pR, B, v, P, s));
         CK(reduce_partials(pL, box_blocks(v), 1, 1.0, energy_dev, 2, B, s));
         CK(reduce_partials(pR, box_blocks(v), 1, 1.0, energy_dev + 1, 2, B, s));
     }

@@ -46,7 +46,7 @@ __device__ __forceinline__ void axis_cell(int x, float u, int n, int& i, float& 
 }
 
 struct Cell {
-    long long base;        // linear index of corner (iz, iy, ix)
+    int base;              // linear index of corner (iz, iy, ix) (V < 2^31)
     float tz, ty, tx;
     bool cz, cy, cx;       // clamped axes
     int iz, iy, ix;
@@ -58,14 +58,14 @@ __device__ __forceinline__ Cell make_cell(int z, int y, int x, float uz, float u
     axis_cell(z, uz, v.D, c.iz, c.tz, c.cz);
     axis_cell(y, uy, v.H, c.iy, c.ty, c.cy);
     axis_cell(x, ux, v.W, c.ix, c.tx, c.cx);
-    c.base = ((long long)c.iz * v.H + c.iy) * v.W + c.ix;
+    c.base = (c.iz * v.H + c.iy) * v.W + c.ix;
     return c;
 }
 
 // S(f, p): trilinear value at the cell.
 __device__ __forceinline__ float tri(const float* __restrict__ f, const Cell& c, const Vol& v)
 {
-    const long long sy = v.W, sz = (long long)v.H * v.W;
+    const int sy = v.W, sz = v.H * v.W;
     const float* p = f + c.base;
     const float f000 = __ldg(p), f001 = __ldg(p + 1);
     const float f010 = __ldg(p + sy), f011 = __ldg(p + sy + 1);
@@ -84,7 +84,7 @@ __device__ __forceinline__ float tri(const float* __restrict__ f, const Cell& c,
 __device__ __forceinline__ float tri_grad(const float* __restrict__ f, const Cell& c, const Vol& v,
                                           float& gz, float& gy, float& gx)
 {
-    const long long sy = v.W, sz = (long long)v.H * v.W;
+    const int sy = v.W, sz = v.H * v.W;
     const float* p = f + c.base;
     const float f000 = __ldg(p), f001 = __ldg(p + 1);
     const float f010 = __ldg(p + sy), f011 = __ldg(p + sy + 1);

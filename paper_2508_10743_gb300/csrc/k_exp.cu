@@ -7,12 +7,12 @@
 // Forward: one thread per voxel, the 8 corners of each channel gathered
 // through the read-only cache (neighbouring threads share cells, so the
 // gathers hit L1).  Adjoint: the transpose of the interpolation is a
-// scatter.  A block stages its sources' contributions in a shared-memory
-// window that covers every cell its 32x8x4 tile of sources can reach
-// (computed per block from the data), adds them there with shared atomics,
-// and flushes the window to global memory with one atomic add per non-zero
-// cell and channel.  A block whose window exceeds the budget scatters
-// straight to global memory.
+// scatter, done with float atomics that the L2 resolves (measured faster on
+// GB300 than staging the block's contributions in shared memory, which cost
+// occupancy and barriers).  A warp is one x-row of 32 sources; neighbouring
+// lanes usually share an x-corner, so a lane hands its upper x-corner
+// contribution to the next lane when the cells coincide, and sends the two
+// x-corners of a (z, y) pair as one 8-byte atomic when they are aligned.
 #include "kernels.h"
 
 #include <climits>
@@ -46,17 +46,25 @@ exp_square_kernel(const float* __restrict__ src, float scale, float* __restrict_
     }
 }
 
-// shared-memory window budget of the adjoint: cells x 3 channels x 4 B
-constexpr int WIN_CELLS = 4096;
-constexpr size_t WIN_BYTES = (size_t)WIN_CELLS * 3 * sizeof(float);
+// Adjoint tiles: 32 x 8 x ADJ_Z sources per block (each thread walks ADJ_Z
+// planes).  PAIR: lanes hand coinciding x-corners to their neighbour;
+// VEC2: a lane's two x-corners go out as one 8-byte atomic when aligned.
+#ifndef DARC_ADJ_Z
+#define DARC_ADJ_Z 4
+#endif
+#ifndef DARC_ADJ_PAIR
+#define DARC_ADJ_PAIR 1
+#endif
+#ifndef DARC_ADJ_VEC2
+#define DARC_ADJ_VEC2 1
+#endif
+constexpr int ADJ_Z = DARC_ADJ_Z;
 
 __global__ void __launch_bounds__(VT_THREADS)
 exp_square_adjoint_kernel(const float* __restrict__ src, float scale, const float* __restrict__ gin,
-                          float* __restrict__ gout, float out_scale, Vol v, int nzt)
+                          float* __restrict__ gout, float out_scale, Vol v, int nzt, int vec2)
 {
-    extern __shared__ float win[];           // [3][cells]
-    __shared__ int bnd[6];                   // lo z,y,x ; hi z,y,x
-    const int tid = threadIdx.y * VT_X + threadIdx.x;
+    const int lane = threadIdx.x;
     const int x = blockIdx.x * VT_X + threadIdx.x;
     const int y = blockIdx.y * VT_Y + threadIdx.y;
     const int zt = blockIdx.z % nzt;
@@ -66,120 +74,76 @@ exp_square_adjoint_kernel(const float* __restrict__ src, float scale, const floa
     const float* s1 = s0 + v.V;
     const float* s2 = s1 + v.V;
     const float* g0 = gin + (size_t)b * 3 * v.V;
-    float* o0 = gout + (size_t)b * 3 * v.V;
-
-    if (tid < 3) bnd[tid] = INT_MAX;
-    else if (tid < 6) bnd[tid] = INT_MIN;
-    __syncthreads();
-
-    // 1. window bounds: every corner touched and every source voxel itself
-    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    if (xy_ok) {
-        for (int k = 0; k < VT_Z; ++k) {
-            const int z = zt * VT_Z + k;
-            if (z >= v.D) break;
-            const long long l = ((long long)z * v.H + y) * v.W + x;
+    const float* g1 = g0 + v.V;
+    const float* g2 = g1 + v.V;
+    float* o[3];
+    o[0] = gout + (size_t)b * 3 * v.V;
+    o[1] = o[0] + v.V;
+    o[2] = o[1] + v.V;
+    const int plane = v.H * v.W;
+    for (int k = 0; k < ADJ_Z; ++k) {
+        const int z = zt * ADJ_Z + k;
+        const bool active = xy_ok && z < v.D;
+        if (!DARC_ADJ_PAIR && !active) break;
+        float w[8], gs[3] = {0.f, 0.f, 0.f};
+        int cb = -4;
+        if (active) {
+            const int l = z * plane + y * v.W + x;
             const Cell c = make_cell(z, y, x, scale * __ldg(s0 + l), scale * __ldg(s1 + l),
                                      scale * __ldg(s2 + l), v);
-            lo[0] = min(lo[0], min(z, c.iz)); hi[0] = max(hi[0], max(z, c.iz + 1));
-            lo[1] = min(lo[1], min(y, c.iy)); hi[1] = max(hi[1], max(y, c.iy + 1));
-            lo[2] = min(lo[2], min(x, c.ix)); hi[2] = max(hi[2], max(x, c.ix + 1));
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[a] = min(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
-            hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
-        }
-    }
-    if ((tid & 31) == 0) {
-        for (int a = 0; a < 3; ++a) {
-            atomicMin(&bnd[a], lo[a]);
-            atomicMax(&bnd[3 + a], hi[a]);
-        }
-    }
-    __syncthreads();
-    if (bnd[0] == INT_MAX) return;           // no voxel of this tile is inside the volume
-    const int wz0 = bnd[0], wy0 = bnd[1], wx0 = bnd[2];
-    const int ey = bnd[4] - wy0 + 1, ex = bnd[5] - wx0 + 1;
-    const long long cells_ll = (long long)(bnd[3] - wz0 + 1) * ey * ex;
-    const bool staged = cells_ll <= WIN_CELLS;
-    const int cells = staged ? (int)cells_ll : 0;
-    if (staged) {
-        for (int e = tid; e < 3 * cells; e += VT_THREADS) win[e] = 0.f;
-        __syncthreads();
-    }
-
-    // 2. contributions of each source voxel
-    if (xy_ok) {
-        for (int k = 0; k < VT_Z; ++k) {
-            const int z = zt * VT_Z + k;
-            if (z >= v.D) break;
-            const long long l = ((long long)z * v.H + y) * v.W + x;
-            const Cell c = make_cell(z, y, x, scale * __ldg(s0 + l), scale * __ldg(s1 + l),
-                                     scale * __ldg(s2 + l), v);
-            const float gz = __ldg(g0 + l), gy = __ldg(g0 + v.V + l), gx = __ldg(g0 + 2 * v.V + l);
+            const float gz = __ldg(g0 + l), gy = __ldg(g1 + l), gx = __ldg(g2 + l);
             float dz0, dy0, dx0, dz1, dy1, dx1, dz2, dy2, dx2;
             tri_grad(s0, c, v, dz0, dy0, dx0);
             tri_grad(s1, c, v, dz1, dy1, dx1);
             tri_grad(s2, c, v, dz2, dy2, dx2);
             // identity + Jacobian term at the source voxel itself (scale: du_t = scale d src)
-            const float lz = gz + scale * (gz * dz0 + gy * dz1 + gx * dz2);
-            const float ly = gy + scale * (gz * dy0 + gy * dy1 + gx * dy2);
-            const float lx = gx + scale * (gz * dx0 + gy * dx1 + gx * dx2);
-            float w[8];
+            atomicAdd(o[0] + l, (gz + scale * (gz * dz0 + gy * dz1 + gx * dz2)) * out_scale);
+            atomicAdd(o[1] + l, (gy + scale * (gz * dy0 + gy * dy1 + gx * dy2)) * out_scale);
+            atomicAdd(o[2] + l, (gx + scale * (gz * dx0 + gy * dx1 + gx * dx2)) * out_scale);
             tri_weights(c, w);
-            const float gs[3] = {gz * out_scale, gy * out_scale, gx * out_scale};
-            if (staged) {
-                const int e0 = ((z - wz0) * ey + (y - wy0)) * ex + (x - wx0);
-                atomicAdd(&win[e0], lz * out_scale);
-                atomicAdd(&win[cells + e0], ly * out_scale);
-                atomicAdd(&win[2 * cells + e0], lx * out_scale);
-                const int cb = ((c.iz - wz0) * ey + (c.iy - wy0)) * ex + (c.ix - wx0);
+            gs[0] = gz * out_scale;
+            gs[1] = gy * out_scale;
+            gs[2] = gx * out_scale;
+            cb = c.base;
+        } else {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int e = cb + ((q >> 2) & 1) * ey * ex + ((q >> 1) & 1) * ex + (q & 1);
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) atomicAdd(&win[ch * cells + e], w[q] * gs[ch]);
-                }
-            } else {
-                atomicAdd(o0 + l, lz * out_scale);
-                atomicAdd(o0 + v.V + l, ly * out_scale);
-                atomicAdd(o0 + 2 * v.V + l, lx * out_scale);
-                const long long sy = v.W, sz = (long long)v.H * v.W;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const long long e = c.base + ((q >> 2) & 1) * sz + ((q >> 1) & 1) * sy + (q & 1);
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) atomicAdd(o0 + ch * v.V + e, w[q] * gs[ch]);
-                }
-            }
+            for (int q = 0; q < 8; ++q) w[q] = 0.f;
         }
-    }
-
-    // 3. flush the window
-    if (staged) {
-        __syncthreads();
-        for (int e = tid; e < cells; e += VT_THREADS) {
-            const int wz = e / (ey * ex);
-            const int rem = e - wz * ey * ex;
-            const int wy = rem / ex;
-            const int wx = rem - wy * ex;
-            const long long l = ((long long)(wz0 + wz) * v.H + (wy0 + wy)) * v.W + (wx0 + wx);
+        // transpose of the interpolation: the 8 corners, as 4 (dz, dy) pairs of x-corners
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const int a = active ? cb + ((q >> 2) & 1) * plane + ((q >> 1) & 1) * v.W : -4;
+            bool absorb = false, given = false;
+            if (DARC_ADJ_PAIR) {
+                const int pa = __shfl_up_sync(0xffffffffu, a, 1);
+                absorb = active && lane > 0 && pa >= 0 && pa + 1 == a;
+                given = __shfl_down_sync(0xffffffffu, absorb, 1) && lane < 31;
+            }
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                const float val = win[ch * cells + e];
-                if (val != 0.f) atomicAdd(o0 + ch * v.V + l, val);
+                float lo_v = w[q] * gs[ch];
+                const float hi_v = w[q + 1] * gs[ch];
+                if (DARC_ADJ_PAIR) {
+                    const float ph = __shfl_up_sync(0xffffffffu, hi_v, 1);
+                    if (absorb) lo_v += ph;
+                }
+                if (!active) continue;
+                if (given) {
+                    atomicAdd(o[ch] + a, lo_v);
+                } else if (DARC_ADJ_VEC2 && vec2 && (a & 1) == 0) {
+                    atomicAdd(reinterpret_cast<float2*>(o[ch] + a), make_float2(lo_v, hi_v));
+                } else {
+                    atomicAdd(o[ch] + a, lo_v);
+                    atomicAdd(o[ch] + a + 1, hi_v);
+                }
             }
         }
     }
 }
 
-dim3 voxel_grid(int B, const Vol& v, int& nzt)
+dim3 voxel_grid(int B, const Vol& v, int& nzt, int zt)
 {
-    nzt = div_up(v.D, VT_Z);
+    nzt = div_up(v.D, zt);
     return dim3(div_up(v.W, VT_X), div_up(v.H, VT_Y), nzt * B);
 }
 
@@ -189,7 +153,7 @@ cudaError_t exp_square(const float* src, float scale, float* dst, int B, const V
                        cudaStream_t s)
 {
     int nzt;
-    const dim3 grid = voxel_grid(B, v, nzt);
+    const dim3 grid = voxel_grid(B, v, nzt, VT_Z);
     exp_square_kernel<<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, dst, v, nzt);
     return cudaGetLastError();
 }
@@ -197,18 +161,12 @@ cudaError_t exp_square(const float* src, float scale, float* dst, int B, const V
 cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, float* gout,
                                float out_scale, int B, const Vol& v, cudaStream_t s)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(exp_square_adjoint_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)WIN_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
     int nzt;
-    const dim3 grid = voxel_grid(B, v, nzt);
-    exp_square_adjoint_kernel<<<grid, dim3(VT_X, VT_Y), WIN_BYTES, s>>>(src, scale, gin, gout,
-                                                                        out_scale, v, nzt);
+    const dim3 grid = voxel_grid(B, v, nzt, ADJ_Z);
+    // 8-byte atomics need every channel plane 8-byte aligned (V even, aligned base)
+    const int vec2 = (v.V % 2 == 0) && ((reinterpret_cast<uintptr_t>(gout) & 7) == 0);
+    exp_square_adjoint_kernel<<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, gin, gout, out_scale, v,
+                                                                nzt, vec2);
     return cudaGetLastError();
 }
 

@@ -9,12 +9,12 @@
 // self-adjoint):  dL/dJ(y) = -1/V [Box(a) + 2 J(y) Box(b) + A(y) Box(g)]
 // with a = dcc/dS_J, b = dcc/dS_JJ, g = dcc/dS_JA (mirror for A).
 //
-// One kernel template streams a 32 x 16 (x, y) column tile through z: each
-// input plane (with an r-voxel halo, zero outside) is staged in shared
-// memory, summed along x and then y, and its 2-D window sums go into a ring
-// of w planes; every output plane sums its w ring entries afresh (no
-// running sum, so no drift along z).  An `Op` supplies the per-voxel input
-// channels and consumes the window sums.
+// Every box sum is two kernels sharing an `Op` (input channels, epilogue):
+// an XY kernel, one warp per plane strip of 32 columns, stages each row with
+// its halo in warp-private shared memory, sums x windows from it and keeps a
+// running y sum (lane-private ring of the last w rows), writing the 2-D
+// window sums; a Z kernel, one thread per column, keeps a running z sum over
+// chunks of 32 planes and applies the epilogue.  Zero padding throughout.
 #include "kernels.h"
 
 #include <algorithm>
@@ -22,109 +22,129 @@
 namespace darc_impl {
 namespace {
 
-constexpr int BX = 32, BY = 16, BNT = 256, ZCHUNK = 32;
+// XY pass: a block of XW warps covers a 32-column strip, YC output rows and
+// XW consecutive planes (one plane per warp).
+constexpr int XW = 8, YC = 32;
+// Z pass: 32 x 8 columns per block, ZC output planes per thread.
+constexpr int ZX = 32, ZY = 8, ZC = 32;
 
-template <int NCH>
-size_t box_smem_bytes(int r)
+size_t xy_smem_bytes(int nch, int r)
 {
-    const int w = 2 * r + 1, LX = BX + 2 * r, LY = BY + 2 * r;
-    return sizeof(float) * ((size_t)NCH * LY * LX + (size_t)NCH * LY * BX + (size_t)w * NCH * BY * BX);
+    const int w = 2 * r + 1;
+    return sizeof(float) * (size_t)XW * ((size_t)nch * (32 + 2 * r) + (size_t)(w + 1) * nch * 32);
 }
 
+// P[b][c] = 2-D window sums (x, y) of the input channels of every plane
 template <int NCH, class Op>
-__global__ void __launch_bounds__(BNT) box_kernel(Op op, Vol v, int r, int nzc)
+__global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, float* __restrict__ P, int nzb)
 {
     extern __shared__ float sm[];
-    __shared__ double red[32];
-    const int w = 2 * r + 1, LX = BX + 2 * r, LY = BY + 2 * r;
-    float* tile = sm;                               // [NCH][LY][LX]
-    float* xs = tile + NCH * LY * LX;               // [NCH][LY][BX]
-    float* ring = xs + NCH * LY * BX;               // [w][NCH][BY][BX]
-    const int tid = threadIdx.x;
-    const int b = blockIdx.z / nzc, zc = blockIdx.z % nzc;
-    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
-    const int z0 = zc * ZCHUNK, z1 = min(v.D, z0 + ZCHUNK);
-    float acc = 0.f;
-    for (int zi = z0 - r; zi < z1 + r; ++zi) {
-        const bool zin = (zi >= 0) && (zi < v.D);
-        for (int e = tid; e < LY * LX; e += BNT) {
-            const int ly = e / LX, lx = e - ly * LX;
-            const int y = y0 - r + ly, x = x0 - r + lx;
+    const int w = 2 * r + 1, LXW = 32 + 2 * r, NR = w + 1;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int b = blockIdx.z / nzb;
+    const int z = (blockIdx.z % nzb) * XW + wp;
+    if (z >= v.D) return;                          // whole warp; no block-level barrier below
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * YC;
+    const int x = x0 + lane;
+    float* row = sm + (size_t)wp * (NCH * LXW + NR * NCH * 32);
+    float* ring = row + NCH * LXW;
+    const int yend = min(y0 + YC, v.H);
+    float ys[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) ys[c] = 0.f;
+    for (int yi = y0 - r; yi < yend + r; ++yi) {
+        const bool yin = yi >= 0 && yi < v.H;
+        for (int j = lane; j < LXW; j += 32) {
+            const int xx = x0 - r + j;
             float vals[NCH];
-            if (zin && y >= 0 && y < v.H && x >= 0 && x < v.W) {
-                op.load(b, ((long long)zi * v.H + y) * v.W + x, vals);
+            if (yin && xx >= 0 && xx < v.W) {
+                op.load(b, ((long long)z * v.H + yi) * v.W + xx, vals);
             } else {
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) vals[c] = 0.f;
             }
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) tile[(c * LY + ly) * LX + lx] = vals[c];
+            for (int c = 0; c < NCH; ++c) row[c * LXW + j] = vals[c];
         }
-        __syncthreads();
-        for (int e = tid; e < LY * BX; e += BNT) {
-            const int ly = e / BX, tx = e - ly * BX;
+        __syncwarp();
+        const int slot = (yi - (y0 - r)) % NR, old = (slot + 1) % NR;
+        const bool drop = yi - w >= y0 - r;
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                const float* row = tile + (c * LY + ly) * LX + tx;
-                float s = 0.f;
-                for (int d = 0; d < w; ++d) s += row[d];
-                xs[(c * LY + ly) * BX + tx] = s;
-            }
+        for (int c = 0; c < NCH; ++c) {
+            const float* rr = row + c * LXW + lane;
+            float xsum = 0.f;
+            for (int d = 0; d < w; ++d) xsum += rr[d];
+            ys[c] += xsum;
+            if (drop) ys[c] -= ring[(old * NCH + c) * 32 + lane];
+            ring[(slot * NCH + c) * 32 + lane] = xsum;     // lane-private
         }
-        __syncthreads();
-        const int slot = (zi - (z0 - r)) % w;
-        for (int e = tid; e < BY * BX; e += BNT) {
-            const int ty = e / BX, tx = e - ty * BX;
+        __syncwarp();
+        const int yo = yi - r;
+        if (yo >= y0 && x < v.W) {
+            const long long l = ((long long)z * v.H + yo) * v.W + x;
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) {
-                const float* col = xs + (c * LY + ty) * BX + tx;
-                float s = 0.f;
-                for (int d = 0; d < w; ++d) s += col[d * BX];
-                ring[((slot * NCH + c) * BY + ty) * BX + tx] = s;
-            }
+            for (int c = 0; c < NCH; ++c) P[((size_t)b * NCH + c) * v.V + l] = ys[c];
         }
-        __syncthreads();
-        const int zo = zi - r;
-        if (zo >= z0) {
-            for (int e = tid; e < BY * BX; e += BNT) {
-                const int ty = e / BX, tx = e - ty * BX;
-                const int y = y0 + ty, x = x0 + tx;
-                if (y < v.H && x < v.W) {
-                    float S[NCH];
+    }
+}
+
+// 3-D window sums along z from the 2-D sums, then the Op's epilogue
+template <int NCH, class Op>
+__global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc)
+{
+    __shared__ double red[32];
+    const int x = blockIdx.x * ZX + threadIdx.x;
+    const int y = blockIdx.y * ZY + threadIdx.y;
+    const int b = blockIdx.z / nzc, zc = blockIdx.z % nzc;
+    const int z0 = zc * ZC, z1 = min(v.D, z0 + ZC);
+    float acc = 0.f;
+    if (x < v.W && y < v.H) {
+        const long long col = (long long)y * v.W + x, plane = (long long)v.H * v.W;
+        const float* Pb = P + (size_t)b * NCH * v.V;
+        float S[NCH];
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        float s = 0.f;
-                        for (int k = 0; k < w; ++k) s += ring[((k * NCH + c) * BY + ty) * BX + tx];
-                        S[c] = s;
-                    }
-                    acc += op.emit(b, zo, y, x, ((long long)zo * v.H + y) * v.W + x, S);
+        for (int c = 0; c < NCH; ++c) {
+            float s = 0.f;
+            for (int q = max(z0 - r, 0); q <= min(z0 + r, v.D - 1); ++q) s += __ldg(Pb + c * v.V + q * plane + col);
+            S[c] = s;
+        }
+        for (int zo = z0; zo < z1; ++zo) {
+            if (zo > z0) {
+                const int qa = zo + r, qd = zo - r - 1;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    if (qa < v.D) S[c] += __ldg(Pb + c * v.V + qa * plane + col);
+                    if (qd >= 0) S[c] -= __ldg(Pb + c * v.V + qd * plane + col);
                 }
             }
+            acc += op.emit(b, zo, y, x, zo * plane + col, S);
         }
     }
     if (Op::kReduces) {
-        const double s = block_sum(acc, red);
-        if (tid == 0)
-            op.partial(b, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc), s);
+        const double s2 = block_sum(acc, red);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            op.partial(b, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc), s2);
     }
 }
 
 // ---------------------------------------------------------------------------
-struct AtlasStatsOp {
+// Box(f) and Box(f^2) of each image of a batch: stats[b] = {Box f_b, Box f_b^2}
+struct StatsOp {
     static constexpr bool kReduces = false;
     const float* A;
     float* stats;
     long long V;
-    __device__ void load(int, long long l, float* o) const
+    __device__ void load(int b, long long l, float* o) const
     {
-        const float a = __ldg(A + l);
+        const float a = __ldg(A + (size_t)b * V + l);
         o[0] = a;
         o[1] = a * a;
     }
-    __device__ float emit(int, int, int, int, long long l, const float* S) const
+    __device__ float emit(int b, int, int, int, long long l, const float* S) const
     {
-        stats[l] = S[0];
-        stats[V + l] = S[1];
+        float* sb = stats + (size_t)b * 2 * V;
+        sb[l] = S[0];
+        sb[V + l] = S[1];
         return 0.f;
     }
     __device__ void partial(int, int, double) const {}
@@ -281,20 +301,103 @@ struct BwdWarpRegOp {
     __device__ void partial(int b, int blk, double s) const { partials[(size_t)b * nblk + blk] = s; }
 };
 
+// Atlas SGD, forward for one mini-batch: only Box(J A) depends on the atlas;
+// Box(J), Box(J^2) come from the per-sweep cache, Box(A), Box(A^2) from the
+// atlas statistics.  Writes d cc / d(S_A, S_AA, S_JA) per subject.
+struct AtlasFwdOp {
+    static constexpr bool kReduces = true;
+    const float* J;        // warped cohort [n][V]
+    const float* jstats;   // [n][2][V]
+    const int* subj;
+    const float* A;
+    const float* astats;   // [2][V]
+    float* coef;           // [nb][3][V]
+    double* partials;
+    int nblk;
+    long long V;
+    float invN, eps, negInvV;
+    __device__ void load(int b, long long l, float* o) const
+    {
+        o[0] = __ldg(J + (size_t)subj[b] * V + l) * __ldg(A + l);
+    }
+    __device__ float emit(int b, int, int, int, long long l, const float* S) const
+    {
+        const float* js = jstats + (size_t)subj[b] * 2 * V;
+        const CCTerms t = cc_terms(__ldg(js + l), __ldg(js + V + l), S[0], __ldg(astats + l),
+                                   __ldg(astats + V + l), invN, eps, true);
+        float* cb = coef + (size_t)b * 3 * V;
+        cb[l] = t.c0;
+        cb[V + l] = t.c1;
+        cb[2 * V + l] = t.c2;
+        return t.cc * negInvV;
+    }
+    __device__ void partial(int b, int blk, double s) const { partials[(size_t)b * nblk + blk] = s; }
+};
+
+// Atlas SGD, adjoint part shared by the batch: Box is linear, so
+// sum_b [Box(a_b) + 2 A Box(b_b)] = Box(sum_b a_b) + 2 A Box(sum_b b_b).
+struct AtlasBwdSharedOp {
+    static constexpr bool kReduces = false;
+    const float* coef;     // [nb][3][V]
+    int nb;
+    const float* A;
+    float* out;            // [V]
+    long long V;
+    __device__ void load(int, long long l, float* o) const
+    {
+        float sa = 0.f, sb = 0.f;
+        for (int b = 0; b < nb; ++b) {
+            sa += __ldg(coef + (size_t)b * 3 * V + l);
+            sb += __ldg(coef + (size_t)b * 3 * V + V + l);
+        }
+        o[0] = sa;
+        o[1] = sb;
+    }
+    __device__ float emit(int, int, int, int, long long l, const float* S) const
+    {
+        out[l] = S[0] + 2.f * __ldg(A + l) * S[1];
+        return 0.f;
+    }
+    __device__ void partial(int, int, double) const {}
+};
+
+// Atlas SGD, adjoint part of each subject: J_b Box(g_b).
+struct AtlasBwdSubjOp {
+    static constexpr bool kReduces = false;
+    const float* coef;     // [nb][3][V]
+    const float* J;
+    const int* subj;
+    float* out;            // [nb][V]
+    long long V;
+    __device__ void load(int b, long long l, float* o) const
+    {
+        o[0] = __ldg(coef + (size_t)b * 3 * V + 2 * V + l);
+    }
+    __device__ float emit(int b, int, int, int, long long l, const float* S) const
+    {
+        out[(size_t)b * V + l] = __ldg(J + (size_t)subj[b] * V + l) * S[0];
+        return 0.f;
+    }
+    __device__ void partial(int, int, double) const {}
+};
+
 template <int NCH, class Op>
-cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, cudaStream_t s)
+cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, float* P, cudaStream_t s)
 {
-    const size_t smem = box_smem_bytes<NCH>(r);
     static bool attr_set = false;   // once per instantiation, sized for the largest window (r = 8)
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(box_kernel<NCH, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)box_smem_bytes<NCH>(8));
+        cudaError_t e = cudaFuncSetAttribute(box_xy_kernel<NCH, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)xy_smem_bytes(NCH, 8));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int nzc = div_up(v.D, ZCHUNK);
-    const dim3 grid(div_up(v.W, BX), div_up(v.H, BY), nzc * B);
-    box_kernel<NCH, Op><<<grid, BNT, smem, s>>>(op, v, r, nzc);
+    const int nzb = div_up(v.D, XW);
+    box_xy_kernel<NCH, Op><<<dim3(div_up(v.W, 32), div_up(v.H, YC), nzb * B), XW * 32, xy_smem_bytes(NCH, r), s>>>(
+        op, v, r, P, nzb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nzc = div_up(v.D, ZC);
+    box_z_kernel<NCH, Op><<<dim3(div_up(v.W, ZX), div_up(v.H, ZY), nzc * B), dim3(ZX, ZY), 0, s>>>(op, v, r, P, nzc);
     return cudaGetLastError();
 }
 
@@ -311,40 +414,67 @@ __global__ void sum_images_kernel(const float* __restrict__ g, int B, float* __r
 
 }  // namespace
 
-int box_blocks(const Vol& v) { return div_up(v.W, BX) * div_up(v.H, BY) * div_up(v.D, ZCHUNK); }
+int box_blocks(const Vol& v) { return div_up(v.W, ZX) * div_up(v.H, ZY) * div_up(v.D, ZC); }
 
-cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, cudaStream_t s)
+cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, float* P, cudaStream_t s)
 {
-    AtlasStatsOp op{A, stats, v.V};
-    return launch_box<2>(op, 1, v, r, s);
+    StatsOp op{A, stats, v.V};
+    return launch_box<2>(op, 1, v, r, P, s);
+}
+
+cudaError_t image_stats(const float* J, float* stats, int B, int r, const Vol& v, float* P, cudaStream_t s)
+{
+    StatsOp op{J, stats, v.V};
+    return launch_box<2>(op, B, v, r, P, s);
+}
+
+cudaError_t atlas_sgd_forward(const float* J, const float* jstats, const int* subj, const float* A,
+                              const float* astats, int r, float eps, float* coef, double* partials,
+                              int nb, const Vol& v, float* P, cudaStream_t s)
+{
+    const int w = 2 * r + 1;
+    AtlasFwdOp op{J, jstats, subj, A, astats, coef, partials, box_blocks(v), v.V,
+                  (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V)};
+    return launch_box<1>(op, nb, v, r, P, s);
+}
+
+cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, const float* coef,
+                               int r, float* gshared, float* gsubj, int nb, const Vol& v, float* P,
+                               cudaStream_t s)
+{
+    AtlasBwdSharedOp shared{coef, nb, A, gshared, v.V};
+    cudaError_t e = launch_box<2>(shared, 1, v, r, P, s);
+    if (e != cudaSuccess) return e;
+    AtlasBwdSubjOp each{coef, J, subj, gsubj, v.V};
+    return launch_box<1>(each, nb, v, r, P, s);
 }
 
 cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const float* stats,
                          int r, float eps, int wrt_atlas, float* coef, double* partials, int B,
-                         const Vol& v, cudaStream_t s)
+                         const Vol& v, float* P, cudaStream_t s)
 {
     const int w = 2 * r + 1;
     FwdOp op{J, subj, A, stats, coef, partials, box_blocks(v), v.V,
              (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V), wrt_atlas};
-    return launch_box<3>(op, B, v, r, s);
+    return launch_box<3>(op, B, v, r, P, s);
 }
 
 cudaError_t lncc_backward(const float* J, const int* subj, const float* A, const float* coef,
-                          int r, int wrt_atlas, float* g, int B, const Vol& v, cudaStream_t s)
+                          int r, int wrt_atlas, float* g, int B, const Vol& v, float* P, cudaStream_t s)
 {
     BwdOp op{J, subj, A, coef, g, v.V, (float)(-1.0 / (double)v.V), wrt_atlas};
-    return launch_box<3>(op, B, v, r, s);
+    return launch_box<3>(op, B, v, r, P, s);
 }
 
 cudaError_t lncc_backward_warp_reg(const float* J, const float* A, const float* coef, int r,
                                    const float* I, size_t I_bstride, const float* uT,
                                    float lambda, float* gT, double* partials, int B, const Vol& v,
-                                   cudaStream_t s)
+                                   float* P, cudaStream_t s)
 {
     auto w = [&](int n) { return (float)(1.0 / (3.0 * (double)v.V * (double)(n - 1) / (double)n)); };
     BwdWarpRegOp op{J, A, coef, I, I_bstride, uT, gT, partials, box_blocks(v), v,
                     (float)(-1.0 / (double)v.V), lambda, RegW{w(v.D), w(v.H), w(v.W)}};
-    return launch_box<3>(op, B, v, r, s);
+    return launch_box<3>(op, B, v, r, P, s);
 }
 
 cudaError_t sum_images(const float* g, int B, float* out, const Vol& v, cudaStream_t s)

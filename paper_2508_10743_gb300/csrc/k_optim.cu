@@ -237,15 +237,14 @@ finalize_mean_kernel(const double* __restrict__ acc, double inv_n, float* __rest
 
 __global__ void __launch_bounds__(RT)
 atlas_adam_kernel(float* __restrict__ A, float* __restrict__ m, float* __restrict__ s,
-                  const float* __restrict__ g, int B, float lr_c1, float isc2, float b1, float b2,
-                  float eps, long long V)
+                  const float* __restrict__ gsh, const float* __restrict__ g, int B, float scale,
+                  float lr_c1, float isc2, float b1, float b2, float eps, long long V)
 {
-    const float invB = 1.f / (float)B;
     for (long long l = blockIdx.x * (long long)RT + threadIdx.x; l < V; l += (long long)gridDim.x * RT) {
-        float gs = 0.f;
+        float gs = gsh ? __ldg(gsh + l) : 0.f;
         for (int b = 0; b < B; ++b) gs += __ldg(g + (size_t)b * V + l);
         float a = A[l], mm = m[l], ss = s[l];
-        adam1(a, mm, ss, gs * invB, b1, b2, lr_c1, isc2, eps);
+        adam1(a, mm, ss, gs * scale, b1, b2, lr_c1, isc2, eps);
         A[l] = a;
         m[l] = mm;
         s[l] = ss;
@@ -326,12 +325,12 @@ cudaError_t finalize_mean(const double* acc, double inv_n, float* A, const Vol& 
     return cudaGetLastError();
 }
 
-cudaError_t atlas_adam(float* A, float* m, float* s_, const float* g, int B, float lr_c1,
-                       float inv_sqrt_c2, float beta1, float beta2, float eps, const Vol& v,
-                       cudaStream_t st)
+cudaError_t atlas_adam(float* A, float* m, float* s_, const float* gshared, const float* gsubj,
+                       int B, float scale, float lr_c1, float inv_sqrt_c2, float beta1, float beta2,
+                       float eps, const Vol& v, cudaStream_t st)
 {
-    atlas_adam_kernel<<<grid_for(v.V), RT, 0, st>>>(A, m, s_, g, B, lr_c1, inv_sqrt_c2, beta1, beta2,
-                                                    eps, v.V);
+    atlas_adam_kernel<<<grid_for(v.V), RT, 0, st>>>(A, m, s_, gshared, gsubj, B, scale, lr_c1, inv_sqrt_c2,
+                                                    beta1, beta2, eps, v.V);
     return cudaGetLastError();
 }
 

@@ -68,31 +68,44 @@ cudaError_t warp_accumulate(const float* I, const int* subj, const float* u, dou
 cudaError_t image_mean_accumulate(const float* I, int n, double* acc, const Vol& v,
                                   cudaStream_t s);
 cudaError_t finalize_mean(const double* acc, double inv_n, float* A, const Vol& v, cudaStream_t s);
-// A -= Adam(mean_b g[b]) for the atlas SGD; g [B][V]
-cudaError_t atlas_adam(float* A, float* m, float* s_, const float* g, int B, float lr_c1,
-                       float inv_sqrt_c2, float beta1, float beta2, float eps, const Vol& v,
-                       cudaStream_t st);
+// Adam step of the atlas SGD with the mini-batch mean gradient
+// g = scale * (gshared + sum_b gsubj[b]) (gshared may be null)
+cudaError_t atlas_adam(float* A, float* m, float* s_, const float* gshared, const float* gsubj,
+                       int B, float scale, float lr_c1, float inv_sqrt_c2, float beta1, float beta2,
+                       float eps, const Vol& v, cudaStream_t st);
 
 // ---- local NCC (k_lncc.cu) ----
+// Box sums need scratch P of B x (channels <= 3) x V floats for the 2-D sums.
 int box_blocks(const Vol& v);
 // window statistics of the atlas: stats[0] = Box(A), stats[1] = Box(A^2)
-cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, cudaStream_t s);
+cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, float* P, cudaStream_t s);
 // forward: box sums of J, J^2, J*A; cc; loss partials [B][nblk]; per-voxel
 // coefficients coef [B][3][V]: wrt_atlas = 0 -> dcc/d(S_J, S_JJ, S_JA),
 // 1 -> dcc/d(S_A, S_AA, S_JA).  J rows are J + subj[b]*V when subj != null.
 cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const float* stats,
                          int r, float eps, int wrt_atlas, float* coef, double* partials, int B,
-                         const Vol& v, cudaStream_t s);
+                         const Vol& v, float* P, cudaStream_t s);
 // backward: g = -1/V [Box(c0) + 2 X Box(c1) + Y Box(c2)], X = J (Y = A) or,
 // for wrt_atlas, X = A (Y = J); writes g [B][V]
 cudaError_t lncc_backward(const float* J, const int* subj, const float* A, const float* coef,
-                          int r, int wrt_atlas, float* g, int B, const Vol& v, cudaStream_t s);
+                          int r, int wrt_atlas, float* g, int B, const Vol& v, float* P, cudaStream_t s);
 // backward fused with the warp adjoint and the regulariser:
 // gT = gJ * dS(I, x + uT)/dp + lambda dR/du_T; reg partials [B][nblk]
 cudaError_t lncc_backward_warp_reg(const float* J, const float* A, const float* coef, int r,
                                    const float* I, size_t I_bstride, const float* uT,
                                    float lambda, float* gT, double* partials, int B, const Vol& v,
-                                   cudaStream_t s);
+                                   float* P, cudaStream_t s);
 cudaError_t sum_images(const float* g, int B, float* out, const Vol& v, cudaStream_t s);
+// Box(J_b), Box(J_b^2) of B images: stats [B][2][V]
+cudaError_t image_stats(const float* J, float* stats, int B, int r, const Vol& v, float* P, cudaStream_t s);
+// atlas SGD for a mini-batch (rows subj[0..nb)): coefficients wrt the atlas,
+// loss partials [nb][nblk]
+cudaError_t atlas_sgd_forward(const float* J, const float* jstats, const int* subj, const float* A,
+                              const float* astats, int r, float eps, float* coef, double* partials,
+                              int nb, const Vol& v, float* P, cudaStream_t s);
+// gshared [V] = Box(sum a) + 2 A Box(sum b); gsubj [nb][V] = J_b Box(g_b)
+cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, const float* coef,
+                               int r, float* gshared, float* gsubj, int nb, const Vol& v, float* P,
+                               cudaStream_t s);
 
 }  // namespace darc_impl

@@ -1,0 +1,68 @@
+"""One kernel family on a small seeded case, for focused profiler captures.
+
+    python -m paper_2508_10743_gb300.kernel_case --kernel exp_adjoint --batch 1
+
+runs `--warmup` untimed launches then `--reps` launches of the chosen
+operator on one or a few brain-shaped subjects (160x192x224 by default) and
+prints the mean CUDA-event time.  Inputs are seeded synthetic fields and
+images; the velocities reach the workload's 6-voxel displacement scale.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import configs, darc, synth
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", required=True,
+                    choices=["exp_square", "exp_adjoint", "lncc", "subject_grad", "warp"])
+    ap.add_argument("--shape", type=int, nargs=3, default=[160, 192, 224])
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--window", type=int, default=9)
+    ap.add_argument("--T", type=int, default=7)
+    ap.add_argument("--max-disp", type=float, default=6.0)
+    ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    dev = torch.device("cuda:0")
+    shape = tuple(a.shape)
+    B = a.batch
+    v = torch.stack([synth.random_field(shape, 8.0, a.max_disp, 10 + b, device=dev) for b in range(B)]).contiguous()
+    I = torch.stack([synth.random_image(shape, 20 + b, n_ell=12, radii=(4.0, 20.0), device=dev)
+                     for b in range(B)]).contiguous()
+    A = synth.random_image(shape, 30, n_ell=12, radii=(4.0, 20.0), device=dev).contiguous()
+    u = darc.exp_forward(v, a.T)
+    g = torch.randn_like(v) * 1e-3
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=a.window, n_squarings=a.T, lam=1.0)
+
+    def run():
+        if a.kernel == "exp_square":
+            darc.exp_forward(v, 1)
+        elif a.kernel == "exp_adjoint":
+            darc.exp_backward(v, u[:1], g)
+        elif a.kernel == "lncc":
+            darc.lncc(I, A, a.window, grad_J=True)
+        elif a.kernel == "warp":
+            darc.warp(I, u[-1])
+        else:
+            darc.subject_grad(cfg, I, A, v)
+
+    for _ in range(a.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": a.kernel, "shape": shape, "batch": B, "ms": e0.elapsed_time(e1) / a.reps}))
+
+
+if __name__ == "__main__":
+    main()

@@ -351,7 +351,7 @@ def random_field(shape, sigma, max_disp, seed, device="cpu") -> torch.Tensor:
     f = random_spline_fields(1, shape, sigma, rng)[0]
     wg = f.on_grid(shape, device)
     peak = float(torch.linalg.vector_norm(wg, dim=0).max())
-    return (wg * (max_disp / peak)).float()
+    return (wg * (max_disp / peak)).float().contiguous()
 
 
 def random_image(shape, seed, n_ell=6, radii=(2.0, 6.0), noise=0.02, device="cpu") -> torch.Tensor:
@@ -360,4 +360,4 @@ def random_image(shape, seed, n_ell=6, radii=(2.0, 6.0), noise=0.02, device="cpu
     ph = ellipsoid_phantom(shape, n_ell, radii, rng)
     img = eval_template(ph, _grid_points(tuple(shape), device))
     eps = torch.as_tensor(rng.standard_normal(tuple(shape)), device=device)
-    return (img + noise * eps).float()
+    return (img + noise * eps).float().contiguous()

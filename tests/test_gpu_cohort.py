@@ -28,7 +28,7 @@ def _lib():
 
 
 def np64(t):
-    return t.detach().double().cpu().numpy()
+    return np.ascontiguousarray(t.detach().double().cpu().numpy())
 
 
 def cohort_images(n, shape, seed, phantom="ellipsoids"):
@@ -111,7 +111,7 @@ def test_ncc_atlas_update_matches_oracle_sgd():
         c.set_velocity(i, v[i].to(DEV).contiguous())
     A0 = np64(c.atlas())
     stats = c.update_atlas()
-    vv = np.stack([np64(x) for x in v])
+    vv = np.ascontiguousarray(np.stack([np64(x) for x in v]))
     oracle.centrality(vv)
     A_ref, loss_ref = oracle.atlas_sgd(np64(co.images), vv, A0, _ocfg(cfg), sweep=0)
     A = np64(c.atlas())

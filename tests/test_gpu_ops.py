@@ -46,7 +46,7 @@ def image(shape, seed, B=1):
 
 
 def np64(t):
-    return t.detach().double().cpu().numpy()
+    return np.ascontiguousarray(t.detach().double().cpu().numpy())
 
 
 @pytest.mark.parametrize("shape", SHAPES)
