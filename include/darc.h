@@ -289,6 +289,35 @@ int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* ou
 int darc_jacobian_det(const float* u_dev, float* det_dev, unsigned long long* count_dev, int B,
                       int D, int H, int W, void* stream);
 
+/* ===================================================================== */
+/* Allocation-free adjoint (the paper has no counterpart)                 */
+/* ===================================================================== */
+
+/* For callers that cannot allocate device memory -- a plug-in handed its
+ * device buffers by a host application that owns the allocator, or a
+ * process whose device memory is committed to a fixed budget -- and so
+ * cannot supply the workspace darc_exp_backward needs.  Same arguments and
+ * result as darc_exp_backward without the workspace: the scratch lives in a
+ * file-scope device array of DARC_NOALLOC_SCRATCH_BYTES (64 MiB) that every
+ * GPU which loads the library holds until the process exits.
+ *  - Limit: B*D*H*W <= DARC_NOALLOC_MAX_VOXELS (the adjoint alternates
+ *    between two gradient buffers of B*3*D*H*W floats); a larger call
+ *    returns DARC_ERR_ARG and a message naming the limit.
+ *  - The first call on a device looks up the array's device address (one
+ *    cudaGetSymbolAddress with that device current); make that first call
+ *    before any stream capture on the device.
+ *  - All calls share the one array, which keeps the last call's contents;
+ *    each call clears what it accumulates into before using it.  Calls
+ *    whose work overlaps on the GPU (other streams, unordered threads) race
+ *    on the array: order them on one stream.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * Errors: ARG, SHAPE, CUDA. */
+#define DARC_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define DARC_NOALLOC_MAX_VOXELS 2796202
+int darc_exp_backward_noalloc(const float* v_dev, const float* u_dev, const float* gT_dev,
+                              float* gv_dev, int B, int D, int H, int W, int T, float sign,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

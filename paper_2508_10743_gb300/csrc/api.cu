@@ -526,6 +526,10 @@ int fill_atlas_stats(darc_cohort* c, darc_sweep_stats* stats)
 
 }  // namespace
 
+namespace darc_impl {
+int report_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace darc_impl
+
 extern "C" {
 
 void darc_default_config(darc_config* c)

@@ -5,9 +5,14 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace darc_impl {
+
+// records `msg` as the thread's darc_last_error() and returns `code`
+int report_error(int code, const std::string& msg);
 
 // ---- scaling and squaring (k_exp.cu) ----
 // dst[b] = u + S(u, x + u(x)) with u = scale * src[b]; B fields of [3][V].

@@ -101,6 +101,7 @@ _SIGS = {
     "darc_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                ctypes.POINTER(ctypes.c_double)]),
     "darc_launch_count": (ctypes.c_longlong, [_vp]),
+    "darc_exp_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
 }
 
 KERNEL_IDS = {"exp_square": 0, "exp_adjoint": 1, "warp": 2, "lncc_fwd": 3, "lncc_bwd_warp_reg": 4,
@@ -323,6 +324,22 @@ def exp_backward(v: torch.Tensor, u: torch.Tensor, gT: torch.Tensor, sign: float
     work = _work(lib().darc_exp_backward_workspace(B, D, H, W), v.device)
     _check(lib().darc_exp_backward(_ptr(v), _ptr(u), _ptr(gT), _ptr(gv), _ptr(work), B, D, H, W, T,
                                    sign, _stream()))
+    return gv
+
+
+def exp_backward_noalloc(v: torch.Tensor, u: torch.Tensor, gT: torch.Tensor, sign: float = 1.0,
+                         out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """darc_exp_backward without a workspace: for callers that cannot allocate
+    device memory (the library keeps a fixed 64 MiB device array instead).
+    `out` lets such a caller pass a preallocated result buffer."""
+    for t, nm in ((v, "v"), (u, "u"), (gT, "gT")):
+        _need(t, nm)
+    B = v.shape[0]
+    D, H, W = _dims(v)
+    gv = torch.empty_like(v) if out is None else out
+    _need(gv, "out")
+    _check(lib().darc_exp_backward_noalloc(_ptr(v), _ptr(u), _ptr(gT), _ptr(gv), B, D, H, W, u.shape[0],
+                                           sign, _stream()))
     return gv
 
 
