@@ -183,6 +183,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2508_10743_gb300 import darc, synth
+    from paper_2508_10743_gb300.distributed import ShardedSweep
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
@@ -197,9 +198,22 @@ def main():
     for i in range(wl.n):
         c.set_velocity(i, (-co.w[i]).contiguous())
     del co
+    # one GPU: the cohort's own sweep (graph replay, fused atlas update);
+    # several: subjects sharded, one sum all-reduce at the centrality
+    # activation and per atlas step (NCCL), nothing else crosses GPUs
+    drv = ShardedSweep([c], cfg, shard_offset=rank) if world > 1 else None
+    sweep_no = [0]
+
+    def step(stats=False):
+        if drv is None:
+            return c.sweep(stats=stats)
+        drv.sweep(sweep_no[0])
+        sweep_no[0] += 1
+        return None
+
     torch.cuda.synchronize()
     for _ in range(args.warmup):
-        c.sweep(stats=False)
+        step()
     torch.cuda.synchronize()
 
     # ---- timed region: device time, CUDA events on the launching stream ----
@@ -215,7 +229,7 @@ def main():
     torch.cuda.nvtx.range_push("timed")
     ev0.record()
     for _ in range(args.steps):
-        c.sweep(stats=False)
+        step()
     ev1.record()
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
@@ -244,7 +258,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             images.copy_(host_imgs, non_blocking=True)
-            st = c.sweep(stats=True)                 # waits; reads the step's loss
+            st = step(stats=True)                    # waits; reads the step's loss
             host_atlas.copy_(c.atlas(), non_blocking=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -291,7 +305,9 @@ def main():
         "config": {"workload": wl.name, "subjects_per_gpu": wl.n, "shape": list(wl.shape),
                    "dissimilarity": "local NCC %d^3" % cfg.ncc_window, "squarings": cfg.n_squarings,
                    "inner_steps": cfg.inner_steps, "atlas_epochs": cfg.atlas_epochs,
-                   "atlas_batch": cfg.atlas_batch, "parallelism": f"subjects sharded over {world} GPU(s)",
+                   "atlas_batch": cfg.atlas_batch,
+                   "parallelism": (f"{wl.n * world} subjects sharded over {world} GPUs, all-reduce at centrality and "
+                                   f"per atlas step" if world > 1 else "one GPU"),
                    "l2": "inputs larger than L2 (state %.1f GB per GPU)" % (wl.n * wl.voxels * 4 * 10 / 1e9),
                    "step": "one sweep: K2 subject updates of every subject + centrality + atlas"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

@@ -150,6 +150,43 @@ int darc_load(darc_cohort** out, const char* path, const float* images_dev, void
 void darc_destroy(darc_cohort* c);
 
 /* ===================================================================== */
+/* Sharded cohorts: hooks around the exchange steps of Eq. 3              */
+/* ===================================================================== */
+/* When the subjects of one cohort are split over several GPUs (each rank a
+ * darc_cohort of its own subjects, same atlas), the subject updates stay
+ * local (Eq. 3: uncoupled given A) and only the centrality activation and
+ * the atlas re-estimate need the whole cohort.  These calls split them so a
+ * caller can put a sum all-reduce (e.g. NCCL) between the halves; on one
+ * rank, with an identity in between, they compute what darc_update_atlas
+ * computes (up to summation order).  All are stream-ordered like the rest. */
+
+/* sum_dev [3][V] <- sum of this rank's velocities (fixed order). */
+int darc_velocity_sum(darc_cohort* c, float* sum_dev);
+/* v_i <- v_i - sum_dev / n_total for every subject of this rank (sum_dev
+ * [3][V] = the all-reduced darc_velocity_sum, n_total = subjects of all
+ * ranks).  Errors: ARG, CUDA. */
+int darc_centrality_apply(darc_cohort* c, const float* sum_dev, long long n_total);
+/* MSE atlas: acc_dev double [V] <- sum over this rank's subjects of
+ * I_i o Exp(v_i) (after the centrality activation). */
+int darc_atlas_partial(darc_cohort* c, double* acc_dev);
+/* A <- acc_dev / n_total (acc_dev = the all-reduced partial sums). */
+int darc_atlas_set_sum(darc_cohort* c, const double* acc_dev, long long n_total);
+/* NCC atlas SGD (Algorithm 1 SGD_for_atlas) split per mini-batch: begin
+ * warps this rank's subjects and resets the atlas optimiser; grad writes
+ * g_dev [V] = sum over this rank's mini-batch `batch` of epoch `epoch` of
+ * dL_i/dA and loss_dev float [1] = the sum of their losses (the order of the
+ * rank's subjects is its own shuffle, seeded with cfg.seed + rank_seed);
+ * apply takes one Adam step with the all-reduced sum divided by the global
+ * batch size; end refreshes the atlas window statistics.
+ * Returns DARC_ERR_ARG for an epoch/batch outside the schedule. */
+int darc_atlas_sgd_begin(darc_cohort* c, int sweep, unsigned long long rank_seed);
+int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, float* loss_dev);
+int darc_atlas_sgd_apply(darc_cohort* c, const float* g_dev, int global_batch);
+int darc_atlas_sgd_end(darc_cohort* c);
+/* number of mini-batches per epoch of this rank: ceil(n / atlas_batch) */
+int darc_atlas_batches(darc_cohort* c);
+
+/* ===================================================================== */
 /* Measurement                                                             */
 /* ===================================================================== */
 

@@ -211,6 +211,10 @@ struct darc_cohort {
     int* perm_host = nullptr;    // pinned [K3][n]
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::map<std::pair<int, int>, int> seen;
+    // sharded atlas SGD state
+    int sgd_k = 0;
+    bool sgd_open = false;
+    float* gcomb = nullptr;                    // [V] combined mini-batch gradient
     // measurement
     bool profiling = false;
     long long launches = 0;
@@ -619,6 +623,7 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
         ALLOC(c->As, v.V);
         ALLOC(c->gA, (size_t)v.V * cfg->atlas_batch);
         ALLOC(c->gsh, (size_t)v.V);
+        ALLOC(c->gcomb, (size_t)v.V);
         ALLOC(c->jstats, 2 * (size_t)v.V * n);
         ALLOC(c->aloss, (size_t)std::max(cfg->atlas_epochs, 1) * n);
         ALLOC(c->perm_dev, (size_t)std::max(cfg->atlas_epochs, 1) * n);
@@ -901,6 +906,138 @@ void darc_destroy(darc_cohort* c)
     if (!c) return;
     cudaStreamSynchronize(c->st);
     cohort_free(c);
+}
+
+// ---- sharded cohorts: halves of the exchange steps ----
+
+int darc_velocity_sum(darc_cohort* c, float* sum_dev)
+{
+    if (!c || !sum_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    CK(field_sum(c->v, c->n, sum_dev, c->vol, c->st));
+    c->launches += 1;
+    return end(c);
+}
+
+int darc_centrality_apply(darc_cohort* c, const float* sum_dev, long long n_total)
+{
+    if (!c || !sum_dev || n_total < 1) return fail(DARC_ERR_ARG, "bad argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    CK(field_subtract(c->v, c->n, sum_dev, (float)(1.0 / (double)n_total), c->vol, c->st));
+    c->launches += 1;
+    return end(c);
+}
+
+int darc_atlas_partial(darc_cohort* c, double* acc_dev)
+{
+    if (!c || !acc_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    const Vol& vol = c->vol;
+    CK(cudaMemsetAsync(acc_dev, 0, sizeof(double) * vol.V, c->st));
+    for (int f = 0; f < c->n; f += c->bmax) {
+        const int cnt = std::min(c->bmax, c->n - f);
+        float* uT = nullptr;
+        CK(exp_forward_pingpong(c->v + (size_t)f * 3 * vol.V, c->u_all, cnt, vol, c->cfg.n_squarings, 1.f, c->st, &uT));
+        CK(warp_accumulate(c->images, c->iota_dev + f, uT, acc_dev, cnt, vol, c->st));
+        c->launches += c->cfg.n_squarings + 1;
+    }
+    return end(c);
+}
+
+int darc_atlas_set_sum(darc_cohort* c, const double* acc_dev, long long n_total)
+{
+    if (!c || !acc_dev || n_total < 1) return fail(DARC_ERR_ARG, "bad argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    CK(finalize_mean(acc_dev, 1.0 / (double)n_total, c->A, c->vol, c->st));
+    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
+    return end(c);
+}
+
+int darc_atlas_batches(darc_cohort* c)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    return (c->n + c->cfg.atlas_batch - 1) / c->cfg.atlas_batch;
+}
+
+int darc_atlas_sgd_begin(darc_cohort* c, int sweep, unsigned long long rank_seed)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    if (c->cfg.dissim != DARC_LNCC) return fail(DARC_ERR_ARG, "atlas SGD is the local-NCC atlas update");
+    int rc = begin(c);
+    if (rc) return rc;
+    const Vol& vol = c->vol;
+    const int n = c->n, K3 = std::max(c->cfg.atlas_epochs, 1), r = c->cfg.ncc_window / 2;
+    cudaStream_t s = c->st;
+    for (int f = 0; f < n; f += c->bmax) {
+        const int cnt = std::min(c->bmax, n - f);
+        float* uT = nullptr;
+        CK(exp_forward_pingpong(c->v + (size_t)f * 3 * vol.V, c->u_all, cnt, vol, c->cfg.n_squarings, 1.f, s, &uT));
+        CK(warp(c->images + (size_t)f * vol.V, vol.V, uT, c->Wcache + (size_t)f * vol.V, cnt, vol, s));
+        CK(image_stats(c->Wcache + (size_t)f * vol.V, c->jstats + (size_t)f * 2 * vol.V, cnt, r, vol, c->boxbuf, s));
+        c->launches += c->cfg.n_squarings + 3;
+    }
+    CK(cudaEventSynchronize(c->ev_perm));
+    for (int ep = 0; ep < K3; ++ep)
+        minibatch_order(c->cfg.seed + rank_seed, sweep, ep, n, c->perm_host + (size_t)ep * n);
+    CK(cudaMemcpyAsync(c->perm_dev, c->perm_host, sizeof(int) * (size_t)K3 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->ev_perm, s));
+    CK(cudaMemsetAsync(c->Am, 0, sizeof(float) * vol.V, s));
+    CK(cudaMemsetAsync(c->As, 0, sizeof(float) * vol.V, s));
+    c->sgd_k = 0;
+    c->sgd_open = true;
+    return end(c);
+}
+
+int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, float* loss_dev)
+{
+    if (!c || !g_dev || !loss_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (!c->sgd_open) return fail(DARC_ERR_ARG, "darc_atlas_sgd_begin was not called");
+    const int B = c->cfg.atlas_batch, nbatch = (c->n + B - 1) / B;
+    if (epoch < 0 || epoch >= std::max(c->cfg.atlas_epochs, 1) || batch < 0 || batch >= nbatch)
+        return fail(DARC_ERR_ARG, "epoch or mini-batch outside the schedule");
+    int rc = begin(c);
+    if (rc) return rc;
+    const Vol& vol = c->vol;
+    const int r = c->cfg.ncc_window / 2, b0 = batch * B, nb = std::min(B, c->n - b0);
+    const int* subj = c->perm_dev + (size_t)epoch * c->n + b0;
+    cudaStream_t s = c->st;
+    CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));
+    CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps, c->coef, c->pL, nb, vol,
+                         c->boxbuf, s));
+    CK(reduce_partials(c->pL, nb * box_blocks(vol), 1, 1.0, loss_dev, 1, 1, s));
+    CK(atlas_sgd_backward(c->Wcache, subj, c->A, c->coef, r, c->gsh, c->gA, nb, vol, c->boxbuf, s));
+    CK(combine_grad(c->gsh, c->gA, nb, (float)(-1.0 / (double)vol.V), g_dev, vol, s));
+    c->launches += 10;
+    return end(c);
+}
+
+int darc_atlas_sgd_apply(darc_cohort* c, const float* g_dev, int global_batch)
+{
+    if (!c || !g_dev || global_batch < 1) return fail(DARC_ERR_ARG, "bad argument");
+    if (!c->sgd_open) return fail(DARC_ERR_ARG, "darc_atlas_sgd_begin was not called");
+    int rc = begin(c);
+    if (rc) return rc;
+    c->sgd_k += 1;
+    const double c1 = 1.0 - std::pow((double)c->cfg.beta1, c->sgd_k);
+    const double c2 = 1.0 - std::pow((double)c->cfg.beta2, c->sgd_k);
+    CK(atlas_adam(c->A, c->Am, c->As, g_dev, nullptr, 0, (float)(1.0 / global_batch), (float)(c->cfg.lr / c1),
+                  (float)(1.0 / std::sqrt(c2)), c->cfg.beta1, c->cfg.beta2, c->cfg.adam_eps, c->vol, c->st));
+    c->launches += 1;
+    return end(c);
+}
+
+int darc_atlas_sgd_end(darc_cohort* c)
+{
+    if (!c) return fail(DARC_ERR_ARG, "null cohort");
+    int rc = begin(c);
+    if (rc) return rc;
+    c->sgd_open = false;
+    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
+    return end(c);
 }
 
 int darc_set_profiling(darc_cohort* c, int on)

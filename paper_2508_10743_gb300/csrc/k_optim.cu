@@ -251,9 +251,58 @@ atlas_adam_kernel(float* __restrict__ A, float* __restrict__ m, float* __restric
     }
 }
 
+__global__ void __launch_bounds__(RT)
+field_sum_kernel(const float* __restrict__ v, int B, float* __restrict__ out, long long N)
+{
+    for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+        double s = 0.0;
+        for (int b = 0; b < B; ++b) s += (double)__ldg(v + (size_t)b * N + e);
+        out[e] = (float)s;
+    }
+}
+
+__global__ void __launch_bounds__(RT)
+field_subtract_kernel(float* __restrict__ v, int B, const float* __restrict__ sum, float scale, long long N)
+{
+    for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < N; e += (long long)gridDim.x * RT) {
+        const float mu = __ldg(sum + e) * scale;
+        for (int b = 0; b < B; ++b) v[(size_t)b * N + e] -= mu;
+    }
+}
+
+__global__ void __launch_bounds__(RT)
+combine_grad_kernel(const float* __restrict__ gsh, const float* __restrict__ g, int B, float scale,
+                    float* __restrict__ out, long long V)
+{
+    for (long long l = blockIdx.x * (long long)RT + threadIdx.x; l < V; l += (long long)gridDim.x * RT) {
+        float s = gsh ? __ldg(gsh + l) : 0.f;
+        for (int b = 0; b < B; ++b) s += __ldg(g + (size_t)b * V + l);
+        out[l] = s * scale;
+    }
+}
+
 int grid_for(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + RT - 1) / RT, 152LL * 32)); }
 
 }  // namespace
+
+cudaError_t field_sum(const float* v, int B, float* out, const Vol& vol, cudaStream_t s)
+{
+    field_sum_kernel<<<grid_for(3 * vol.V), RT, 0, s>>>(v, B, out, 3 * vol.V);
+    return cudaGetLastError();
+}
+
+cudaError_t field_subtract(float* v, int B, const float* sum, float scale, const Vol& vol, cudaStream_t s)
+{
+    field_subtract_kernel<<<grid_for(3 * vol.V), RT, 0, s>>>(v, B, sum, scale, 3 * vol.V);
+    return cudaGetLastError();
+}
+
+cudaError_t combine_grad(const float* gshared, const float* gsubj, int B, float scale, float* out,
+                         const Vol& v, cudaStream_t s)
+{
+    combine_grad_kernel<<<grid_for(v.V), RT, 0, s>>>(gshared, gsubj, B, scale, out, v.V);
+    return cudaGetLastError();
+}
 
 cudaError_t reduce_partials(const double* partials, int nblk, int nval, double scale, float* out,
                             int out_stride, int B, cudaStream_t s)

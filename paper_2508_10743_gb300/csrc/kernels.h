@@ -79,6 +79,14 @@ cudaError_t atlas_adam(float* A, float* m, float* s_, const float* gshared, cons
                        int B, float scale, float lr_c1, float inv_sqrt_c2, float beta1, float beta2,
                        float eps, const Vol& v, cudaStream_t st);
 
+// out[l] = scale * sum over B fields of v[b] [3][V] (fixed order, double sums)
+cudaError_t field_sum(const float* v, int B, float* out, const Vol& vol, cudaStream_t s);
+// v[b] -= scale * sum for B fields
+cudaError_t field_subtract(float* v, int B, const float* sum, float scale, const Vol& vol, cudaStream_t s);
+// out[l] = scale * (gshared[l] + sum_b gsubj[b][l])
+cudaError_t combine_grad(const float* gshared, const float* gsubj, int B, float scale, float* out,
+                         const Vol& v, cudaStream_t s);
+
 // ---- local NCC (k_lncc.cu) ----
 // Box sums need scratch P of B x (channels <= 3) x V floats for the 2-D sums.
 int box_blocks(const Vol& v);

@@ -102,6 +102,15 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_double)]),
     "darc_launch_count": (ctypes.c_longlong, [_vp]),
     "darc_exp_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
+    "darc_velocity_sum": (_i, [_vp, _vp]),
+    "darc_centrality_apply": (_i, [_vp, _vp, ctypes.c_longlong]),
+    "darc_atlas_partial": (_i, [_vp, _vp]),
+    "darc_atlas_set_sum": (_i, [_vp, _vp, ctypes.c_longlong]),
+    "darc_atlas_batches": (_i, [_vp]),
+    "darc_atlas_sgd_begin": (_i, [_vp, _i, ctypes.c_ulonglong]),
+    "darc_atlas_sgd_grad": (_i, [_vp, _i, _i, _vp, _vp]),
+    "darc_atlas_sgd_apply": (_i, [_vp, _vp, _i]),
+    "darc_atlas_sgd_end": (_i, [_vp]),
 }
 
 KERNEL_IDS = {"exp_square": 0, "exp_adjoint": 1, "warp": 2, "lncc_fwd": 3, "lncc_bwd_warp_reg": 4,
@@ -264,6 +273,48 @@ class Cohort:
         k = ctypes.c_int(0)
         _check(lib().darc_get_adam_state(self._h, i, _ptr(m), _ptr(s), ctypes.byref(k)))
         return m, s, k.value
+
+    # ---- halves of the exchange steps, for sharded cohorts ----
+
+    def velocity_sum(self) -> torch.Tensor:
+        out = torch.empty((3, *self.shape), dtype=torch.float32, device=self.device)
+        _check(lib().darc_velocity_sum(self._h, _ptr(out)))
+        return out
+
+    def centrality_apply(self, vsum: torch.Tensor, n_total: int):
+        _need(vsum, "sum")
+        _check(lib().darc_centrality_apply(self._h, _ptr(vsum), int(n_total)))
+
+    def atlas_partial(self) -> torch.Tensor:
+        acc = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        _check(lib().darc_atlas_partial(self._h, _ptr(acc)))
+        return acc
+
+    def atlas_set_sum(self, acc: torch.Tensor, n_total: int):
+        _need(acc, "acc", torch.float64)
+        _check(lib().darc_atlas_set_sum(self._h, _ptr(acc), int(n_total)))
+
+    def atlas_batches(self) -> int:
+        nb = lib().darc_atlas_batches(self._h)
+        if nb < 0:
+            _check(nb)
+        return nb
+
+    def atlas_sgd_begin(self, sweep: int, rank_seed: int = 0):
+        _check(lib().darc_atlas_sgd_begin(self._h, int(sweep), int(rank_seed)))
+
+    def atlas_sgd_grad(self, epoch: int, batch: int):
+        g = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        _check(lib().darc_atlas_sgd_grad(self._h, int(epoch), int(batch), _ptr(g), _ptr(loss)))
+        return g, loss
+
+    def atlas_sgd_apply(self, g: torch.Tensor, global_batch: int):
+        _need(g, "g")
+        _check(lib().darc_atlas_sgd_apply(self._h, _ptr(g), int(global_batch)))
+
+    def atlas_sgd_end(self):
+        _check(lib().darc_atlas_sgd_end(self._h))
 
     def set_profiling(self, on: bool):
         _check(lib().darc_set_profiling(self._h, int(on)))

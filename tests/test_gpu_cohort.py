@@ -194,3 +194,40 @@ def test_subject_batches_give_the_same_result():
     # float atomics in the adjoint make bitwise equality too strict; Adam may
     # flip the rare step of a near-zero gradient
     assert float(((out[0] - out[1]).abs() <= 1e-4).float().mean()) > 0.99
+
+
+def test_sharded_hooks_reproduce_the_fused_updates():
+    """The exchange hooks of a sharded cohort, run on one GPU: MSE with two
+    shards equals one cohort of all subjects; NCC with one shard equals the
+    cohort's fused atlas update (same mini-batches)."""
+    from paper_2508_10743_gb300.distributed import ShardedSweep
+    shape, n = (12, 16, 34), 4
+    co = cohort_images(n, shape, 9)
+    imgs = co.images.to(DEV).contiguous()
+    v = [synth.random_field(shape, 3.0, 1.5, 400 + i).to(DEV).contiguous() for i in range(n)]
+    cfg = configs.DarcConfig(dissim=configs.MSE, n_squarings=6, lam=0.1, inner_steps=2)
+    whole = darc.Cohort(imgs, cfg)
+    halves = [darc.Cohort(imgs[:2].contiguous(), cfg), darc.Cohort(imgs[2:].contiguous(), cfg)]
+    for i in range(n):
+        whole.set_velocity(i, v[i])
+        halves[i // 2].set_velocity(i % 2, v[i])
+    for h in halves:
+        h.set_atlas(whole.atlas())
+    whole.update_atlas()
+    ShardedSweep(halves, cfg).update_atlas(0)
+    A = np64(whole.atlas())
+    for h in halves:
+        assert np.abs(np64(h.atlas()) - A).max() <= 1e-5 * np.abs(A).max()
+    for i in range(n):
+        assert float((whole.velocity(i) - halves[i // 2].velocity(i % 2)).abs().max()) <= 1e-5
+
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=6, atlas_epochs=3, atlas_batch=2, seed=4)
+    fused, split = darc.Cohort(imgs, cfg), darc.Cohort(imgs, cfg)
+    for i in range(n):
+        fused.set_velocity(i, v[i])
+        split.set_velocity(i, v[i])
+    A0 = np64(fused.atlas())
+    fused.update_atlas()
+    ShardedSweep([split], cfg).update_atlas(0)
+    step_f, step_s = np64(fused.atlas()) - A0, np64(split.atlas()) - A0
+    assert np.mean(np.abs(step_f - step_s) <= 1e-3 * np.abs(step_f).max()) > 0.99

@@ -1,0 +1,110 @@
+"""Parity at the full brain-MRI size (160x192x224), in the kernels' full-size
+launch shapes, on sampled outputs.
+
+A voxel's result depends only on a bounded neighbourhood: u_T(x) on the
+squaring fields within sum_t (max|u_t| + 1) <= 2 max|u_T| + T voxels, the NCC
+gradient additionally on the w^3 windows of the windows (2r) and on the
+adjoint's reach back through the squarings.  The oracle therefore runs on a
+crop around each sample whose margin exceeds that cone; the crop's centre
+then equals the full-volume result.  With lambda = 0 the energy is the NCC
+term alone, whose gradient scales exactly as 1/V, so crop and full volume
+compare after the ratio of their voxel counts.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2508_10743_gb300 import configs, darc, synth
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+SHAPE = (160, 192, 224)
+FWD_TOL, GRAD_TOL = 1e-4, 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2508_10743_gb300 import build
+    build.build()
+    oracle.build()
+    darc.lib()
+
+
+@pytest.fixture(scope="module")
+def brain():
+    co = synth.make_cohort(2, SHAPE, 2000, device=DEV, keep_disp=False,
+                           **configs.WORKLOADS["brain"].gen)
+    v = (-co.w).contiguous()                       # the bench's converged-like state (6-voxel scale)
+    return co.images.contiguous(), co.template.contiguous(), v
+
+
+def np64(t):
+    return np.ascontiguousarray(t.detach().double().cpu().numpy())
+
+
+def crop(a, c, m):
+    sl = tuple(slice(ci - m, ci + m + 1) for ci in c)
+    return a[(Ellipsis,) + sl]
+
+
+SAMPLES = [(80, 96, 112), (60, 120, 70)]
+
+
+def test_full_size_exp_and_warp_on_sampled_voxels(brain):
+    images, template, v = brain
+    u = darc.exp_forward(v, 7)
+    uT = u[-1]
+    W = darc.warp(images, uT.contiguous())
+    max_u = float(torch.linalg.vector_norm(uT, dim=1).max())
+    k = 4                                           # compare the central (2k+1)^3 block
+    m = int(np.ceil(2 * max_u + 7)) + k + 2
+    for b in range(2):
+        for c in SAMPLES:
+            vc = crop(np64(v[b]), c, m)
+            ref = oracle.exp(vc, 7)[-1]
+            got = crop(np64(uT[b]), c, m)
+            inner = (slice(None),) + tuple(slice(m - k, m + k + 1) for _ in range(3))
+            assert np.abs(got[inner] - ref[inner]).max() <= FWD_TOL * np.abs(ref[inner]).max()
+            Ic = crop(np64(images[b]), c, m)
+            Wref = oracle.warp(Ic, ref)
+            Wgot = crop(np64(W[b]), c, m)
+            assert np.abs(Wgot[inner[1:]] - Wref[inner[1:]]).max() <= FWD_TOL * max(np.abs(Wref).max(), 1e-6)
+
+
+def test_full_size_ncc_gradient_on_sampled_blocks(brain):
+    images, template, v = brain
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=9, n_squarings=7, lam=0.0)
+    energy, gv = darc.subject_grad(cfg, images, template, v)
+    torch.cuda.synchronize()
+    Vfull = float(np.prod(SHAPE))
+    max_u = float(torch.linalg.vector_norm(darc.exp_forward(v, 7)[-1], dim=1).max())
+    cone = int(np.ceil(2 * max_u + 7))
+    k = 6
+    m = 2 * cone + 8 + k + 3                        # adjoint reach back + windows + forward cone
+    ocfg = oracle.make_cfg(dissim=1, window=9, T=7, lam=0.0)
+    for b in range(2):
+        c = SAMPLES[b]
+        Ic, Ac, vc = crop(np64(images[b]), c, m), crop(np64(template), c, m), crop(np64(v[b]), c, m)
+        _, _, g = oracle.subject_energy(Ic, Ac, vc, ocfg)
+        g *= Ic.size / Vfull
+        inner = (slice(None),) + tuple(slice(m - k, m + k + 1) for _ in range(3))
+        got = crop(np64(gv[b]), c, m)[inner]
+        ref = g[inner]
+        assert np.linalg.norm(got - ref) <= GRAD_TOL * np.linalg.norm(ref)
+
+
+def test_full_size_centrality_and_subject_steps_in_the_bench_configuration(brain):
+    """The cohort at the bench's size: a subject step keeps every loss finite
+    and the centrality activation leaves a zero-mean velocity set."""
+    images, template, v = brain
+    cfg = configs.WORKLOADS["brain"].config
+    c = darc.Cohort(images, cfg)
+    for i in range(2):
+        c.set_velocity(i, v[i].contiguous())
+    losses = c.subject_step(0, 2, 2, want_loss=True)
+    assert all(np.isfinite(losses))
+    stats = c.update_atlas()
+    assert stats["centrality_after"] < 1e-6 * max(stats["centrality_before"], 1e-3)
+    vs = torch.stack([c.velocity(i) for i in range(2)])
+    assert float(vs.sum(0).abs().max()) <= 1e-5 * float(vs.abs().max())
