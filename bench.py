@@ -60,9 +60,12 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+PROFILE_FILES = {"exp_adjoint": "exp_square_adjoint", "exp_square": "exp_square_kernel"}
+
+
 def read_traffic(kernel: str, workload: str):
     """dram bytes per launch from a committed ncu summary (profiles/), or None."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    path = os.path.join(ROOT, "profiles", f"{PROFILE_FILES.get(kernel, kernel)}_{workload}.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
