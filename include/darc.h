@@ -327,6 +327,99 @@ int darc_jacobian_det(const float* u_dev, float* det_dev, unsigned long long* co
                       int D, int H, int W, void* stream);
 
 /* ===================================================================== */
+/* Learned warm start: BF16 tensor-core kernels (an addition to the       */
+/* method; the paper has no counterpart)                                  */
+/* ===================================================================== */
+
+/* C = A B^T on the 5th-generation tensor cores: A_dev bf16 [M][K], B_dev
+ * bf16 [N][K] (K contiguous in both), C_dev fp32 [M][N]; fp32 accumulation
+ * in tensor memory.  M % 128 == 0, N % 16 == 0 with 16 <= N <= 256,
+ * K % 16 == 0.  Errors: ARG, CUDA. */
+int darc_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, int M, int N, int K, void* stream);
+
+/* 3x3x3 'same' convolution (zero padding) as an implicit GEMM on the tensor
+ * cores, BF16 operands, FP32 accumulation:
+ *   z[v][co] = bias[co] + sum_{tap, ci} in[v + off(tap)][ci] * wt[co][tap*cin + ci]
+ *   off(tap) = (tap/9 - 1, (tap/3)%3 - 1, tap%3 - 1) in (z, y, x).
+ * in_dev: bf16 channels-last [batch][D][H][W][in_stride], channels [0, cin)
+ * read; wt_dev: bf16 [np][kp], zero past 27*cin and past cout; bias_dev:
+ * fp32 [cout] or null.  Epilogue: act = 1 applies a leaky ReLU of slope
+ * `slope`; gate_dev (bf16 channels-last, stride gate_stride, or null)
+ * multiplies each result by 1 where gate > 0 and by `slope` elsewhere (the
+ * data gradient through a leaky ReLU whose output is the gate).  Output:
+ * out_dev bf16 channels-last [..][out_stride], channels [0, cout) -- or,
+ * when out_f32_dev is non-null, fp32 planar [batch][cout][D*H*W].
+ * Requirements: cin % 8 == 0, in_stride % 8 == 0, kp % 16 == 0,
+ * kp >= 27 cin, np % 16 == 0 with 16 <= np <= 256, cout <= np, 16-byte
+ * aligned in_dev and wt_dev.  Errors: ARG, SHAPE, CUDA. */
+int darc_conv3d(const void* in_dev, int in_stride, int cin, const void* wt_dev, const float* bias_dev, void* out_dev,
+                int out_stride, int cout, float* out_f32_dev, const void* gate_dev, int gate_stride, int act,
+                float slope, int batch, int D, int H, int W, int kp, int np, void* stream);
+
+/* Weight and bias gradients of darc_conv3d:
+ *   dw[co][k] = sum_v gz[v][co] * im2col(in)[v][k]   (fp32 [np][kp])
+ *   db[co]    = sum_v gz[v][co]                      (fp32 [cout], db_dev may be null)
+ * gz_dev: bf16 channels-last gradient wrt the pre-activation, stride
+ * gz_stride, cout % 8 == 0 channels read (zero-padded), cout / 8 dividing
+ * 256 when db_dev is given; np % 16 == 0 with cout <= np <= 128.  Split-K
+ * partial sums go to work_dev (fp32, work_bytes) and are added in a fixed
+ * order, so the result is deterministic.  Errors: ARG (also: workspace
+ * smaller than one split), SHAPE, CUDA. */
+int darc_conv3d_wgrad(const void* in_dev, int in_stride, int cin, const void* gz_dev, int gz_stride, int cout,
+                      float* dw_dev, float* db_dev, int batch, int D, int H, int W, int kp, int np, void* work_dev,
+                      size_t work_bytes, void* stream);
+
+/* Half-resolution image (mean of each 2x2x2 block): I_dev fp32 [B][D][H][W]
+ * with even D, H, W -> out_dev [B][D/2][H/2][W/2].  Errors: ARG, CUDA. */
+int darc_resample_half(const float* I_dev, int B, int D, int H, int W, float* out_dev, void* stream);
+
+/* Full-resolution velocity from a half-resolution one: trilinear
+ * interpolation at ((x + 1/2)/2 - 1/2) of the half grid (clamped), values
+ * doubled because the voxel unit halves.  vh_dev fp32 [B][3][Dh][Hh][Wh] ->
+ * v_dev [B][3][2Dh][2Hh][2Wh].  Errors: ARG, CUDA. */
+int darc_upsample_velocity(const float* vh_dev, int B, int Dh, int Hh, int Wh, float* v_dev, void* stream);
+
+/* The warm-start network: a 3-D U-Net with 4 levels of 16, 32, 64, 128
+ * channels (two 3x3x3 conv + leaky ReLU 0.2 per level, 2x average pooling
+ * down, nearest 2x up, skip connections by channel concatenation, a 3x3x3
+ * head to 3 channels).  Input: (subject, atlas) at the network's
+ * resolution D x H x W (each a multiple of 8, >= 16); output: a velocity
+ * field fp32 [B][3][D][H][W] in voxel units of that grid.  BF16 weights
+ * and activations, FP32 accumulation and FP32 master weights (Adam with
+ * PyTorch's defaults beta = (0.9, 0.999), eps = 1e-8).  Weights are
+ * He-normal from `seed` (SplitMix64 + Box-Muller).  The handle owns every
+ * buffer for batches up to max_batch; calls on one handle must be ordered.
+ * Errors: ARG, SHAPE, OOM, CUDA. */
+typedef struct darc_unet darc_unet;
+int darc_unet_create(darc_unet** out, int D, int H, int W, int max_batch, unsigned long long seed);
+void darc_unet_destroy(darc_unet* u);
+/* subj_dev fp32 [B][D][H][W], atlas_dev fp32 [D][H][W] (shared by the
+ * batch) -> v_dev fp32 [B][3][D][H][W]. */
+int darc_unet_forward(darc_unet* u, const float* subj_dev, const float* atlas_dev, int B, float* v_dev, void* stream);
+/* One Adam step on loss = mean over B*3*D*H*W of (net(subj, atlas) -
+ * target)^2, target_dev fp32 [B][3][D][H][W].  loss_host (may be null)
+ * receives the loss of the forward pass before the update (the call then
+ * synchronises the stream). */
+int darc_unet_train_step(darc_unet* u, const float* subj_dev, const float* atlas_dev, const float* target_dev, int B,
+                         float lr, float* loss_host, void* stream);
+/* The same loss and its gradients without an update (read them with
+ * darc_unet_layer_params). */
+int darc_unet_gradients(darc_unet* u, const float* subj_dev, const float* atlas_dev, const float* target_dev, int B,
+                        float* loss_host, void* stream);
+/* Layer l in 0..14 (encoder 0-7, decoder 8-13, head 14): padded input
+ * channels cin (multiple of 8), cout, and the weight matrix shape [np][kp]
+ * with k = tap*cin + ci. */
+int darc_unet_layer_info(darc_unet* u, int layer, int* cin, int* cout, int* kp, int* np);
+/* set = 0: copy the fp32 master weights [np][kp], bias [cout] and the last
+ * gradients out (null pointers skip); set = 1: load w and b (refreshing the
+ * bf16 copies).  Synchronises the device. */
+int darc_unet_layer_params(darc_unet* u, int layer, float* w_dev, float* b_dev, float* dw_dev, float* db_dev, int set);
+/* Weights and Adam state to / from a file (little-endian, magic
+ * "DARCUNT1").  Errors: ARG, IO, CUDA. */
+int darc_unet_save(darc_unet* u, const char* path);
+int darc_unet_load(darc_unet* u, const char* path);
+
+/* ===================================================================== */
 /* Allocation-free adjoint (the paper has no counterpart)                 */
 /* ===================================================================== */
 

@@ -107,6 +107,9 @@ def _load():
             "ora_propagate_labels": (_int, [_U8, _D, _int, _int, _int, _int, _U8]),
             "ora_jacobian_det": (_int, [_D, _int, _int, _int, _D]),
             "ora_dice": (None, [_U8, _U8, _long, _int, _D]),
+            "ora_conv3d": (_int, [_D, _int, _int, _int, _int, _int, _D, _D, _int, _D]),
+            "ora_conv3d_adjoint_input": (_int, [_D, _int, _int, _int, _int, _int, _D, _int, _D]),
+            "ora_conv3d_wgrad": (_int, [_D, _D, _int, _int, _int, _int, _int, _int, _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -362,3 +365,42 @@ def dice(a, b, nlab):
     out = np.empty(nlab - 1)
     _load().ora_dice(_pu8(a), _pu8(b), a.size, int(nlab), _p(out))
     return out
+
+
+# ---- learned warm start: 3x3x3 'same' convolution (no counterpart in the paper) ----
+
+def conv3d(x, w, b=None):
+    """out[b, co] = bias[co] + sum_{ci, tap} w[co, ci, tap] x[b, ci, p + tap - 1]
+    (zero padding).  x [B, cin, D, H, W], w [cout, cin, 3, 3, 3]."""
+    x, w = _d(x), _d(w)
+    B, cin = x.shape[:2]
+    cout = w.shape[0]
+    assert w.shape == (cout, cin, 3, 3, 3)
+    D, H, W = _dims(x.shape)
+    out = np.empty((B, cout, D, H, W))
+    bb = _d(b) if b is not None else None
+    _load().ora_conv3d(_p(x), B, cin, D, H, W, _p(w), _p(bb) if bb is not None else None, cout, _p(out))
+    return out
+
+
+def conv3d_adjoint_input(gz, w):
+    """Transpose of ``conv3d`` in x: gz [B, cout, D, H, W] -> gx [B, cin, D, H, W]."""
+    gz, w = _d(gz), _d(w)
+    B, cout = gz.shape[:2]
+    cin = w.shape[1]
+    D, H, W = _dims(gz.shape)
+    gx = np.empty((B, cin, D, H, W))
+    _load().ora_conv3d_adjoint_input(_p(gz), B, cout, D, H, W, _p(w), cin, _p(gx))
+    return gx
+
+
+def conv3d_wgrad(x, gz):
+    """(dw [cout, cin, 3, 3, 3], db [cout]) of sum(gz * conv3d(x, w, b))."""
+    x, gz = _d(x), _d(gz)
+    B, cin = x.shape[:2]
+    cout = gz.shape[1]
+    D, H, W = _dims(x.shape)
+    dw = np.empty((cout, cin, 3, 3, 3))
+    db = np.empty(cout)
+    _load().ora_conv3d_wgrad(_p(x), _p(gz), B, cin, cout, D, H, W, _p(dw), _p(db))
+    return dw, db

@@ -836,3 +836,126 @@ void ora_dice(const uint8_t *a, const uint8_t *b, long V, int nlab, double *per_
         per_label[lab - 1] = (na + nb) ? 2.0 * (double)both / (double)(na + nb) : -1.0;
     }
 }
+
+/* ===================================================================== */
+/* Learned warm start (an addition to the method; the paper has none).   */
+/* Plain definitions of the 3-D U-Net's convolution, in fp64.            */
+/* Layout: x [B][C][D][H][W]; weights [cout][cin][3][3][3] with tap       */
+/* (a, b, c) reading the input at (z + a - 1, y + b - 1, x + c - 1);      */
+/* zero outside the volume (a 'same' cross-correlation).                 */
+/* ===================================================================== */
+
+/* out[b][co][p] = bias[co] + sum_{ci, tap} w[co][ci][tap] x[b][ci][p + off(tap)] */
+int ora_conv3d(const double *x, int B, int cin, int D, int H, int W, const double *w, const double *bias,
+               int cout, double *out)
+{
+    const long V = (long)D * H * W;
+#pragma omp parallel for schedule(dynamic) collapse(2)
+    for (int bb = 0; bb < B; ++bb)
+        for (int co = 0; co < cout; ++co) {
+            double *o = out + ((long)bb * cout + co) * V;
+            for (long l = 0; l < V; ++l) o[l] = bias ? bias[co] : 0.0;
+            for (int ci = 0; ci < cin; ++ci) {
+                const double *xi = x + ((long)bb * cin + ci) * V;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        for (int c = 0; c < 3; ++c) {
+                            const double wt = w[(((long)co * cin + ci) * 3 + a) * 9 + b * 3 + c];
+                            for (int z = 0; z < D; ++z) {
+                                const int zz = z + a - 1;
+                                if (zz < 0 || zz >= D) continue;
+                                for (int y = 0; y < H; ++y) {
+                                    const int yy = y + b - 1;
+                                    if (yy < 0 || yy >= H) continue;
+                                    for (int xq = 0; xq < W; ++xq) {
+                                        const int xx = xq + c - 1;
+                                        if (xx < 0 || xx >= W) continue;
+                                        o[((long)z * H + y) * W + xq] += wt * xi[((long)zz * H + yy) * W + xx];
+                                    }
+                                }
+                            }
+                        }
+            }
+        }
+    return 0;
+}
+
+/* Adjoint of ora_conv3d in its input: every product w * x[p + off] of the
+ * forward sum sends gz[b][co][p] * w back to the input voxel p + off it read
+ * (a scatter, written as the transpose of the forward map). */
+int ora_conv3d_adjoint_input(const double *gz, int B, int cout, int D, int H, int W, const double *w, int cin,
+                             double *gx)
+{
+    const long V = (long)D * H * W;
+#pragma omp parallel for schedule(dynamic) collapse(2)
+    for (int bb = 0; bb < B; ++bb)
+        for (int ci = 0; ci < cin; ++ci) {
+            double *g = gx + ((long)bb * cin + ci) * V;
+            for (long l = 0; l < V; ++l) g[l] = 0.0;
+            for (int co = 0; co < cout; ++co) {
+                const double *gzo = gz + ((long)bb * cout + co) * V;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        for (int c = 0; c < 3; ++c) {
+                            const double wt = w[(((long)co * cin + ci) * 3 + a) * 9 + b * 3 + c];
+                            for (int z = 0; z < D; ++z) {
+                                const int zz = z + a - 1;
+                                if (zz < 0 || zz >= D) continue;
+                                for (int y = 0; y < H; ++y) {
+                                    const int yy = y + b - 1;
+                                    if (yy < 0 || yy >= H) continue;
+                                    for (int xq = 0; xq < W; ++xq) {
+                                        const int xx = xq + c - 1;
+                                        if (xx < 0 || xx >= W) continue;
+                                        g[((long)zz * H + yy) * W + xx] += wt * gzo[((long)z * H + y) * W + xq];
+                                    }
+                                }
+                            }
+                        }
+            }
+        }
+    return 0;
+}
+
+/* Gradients of sum_{b,co,p} gz[b][co][p] out[b][co][p] in the weights and
+ * biases: dw[co][ci][tap] = sum_{b,p} gz[b][co][p] x[b][ci][p + off(tap)],
+ * db[co] = sum_{b,p} gz[b][co][p] (db may be NULL). */
+int ora_conv3d_wgrad(const double *x, const double *gz, int B, int cin, int cout, int D, int H, int W, double *dw,
+                     double *db)
+{
+    const long V = (long)D * H * W;
+#pragma omp parallel for schedule(dynamic) collapse(2)
+    for (int co = 0; co < cout; ++co)
+        for (int ci = 0; ci < cin; ++ci)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    for (int c = 0; c < 3; ++c) {
+                        double s = 0.0;
+                        for (int bb = 0; bb < B; ++bb) {
+                            const double *xi = x + ((long)bb * cin + ci) * V;
+                            const double *gzo = gz + ((long)bb * cout + co) * V;
+                            for (int z = 0; z < D; ++z) {
+                                const int zz = z + a - 1;
+                                if (zz < 0 || zz >= D) continue;
+                                for (int y = 0; y < H; ++y) {
+                                    const int yy = y + b - 1;
+                                    if (yy < 0 || yy >= H) continue;
+                                    for (int xq = 0; xq < W; ++xq) {
+                                        const int xx = xq + c - 1;
+                                        if (xx < 0 || xx >= W) continue;
+                                        s += gzo[((long)z * H + y) * W + xq] * xi[((long)zz * H + yy) * W + xx];
+                                    }
+                                }
+                            }
+                        }
+                        dw[(((long)co * cin + ci) * 3 + a) * 9 + b * 3 + c] = s;
+                    }
+    if (db)
+        for (int co = 0; co < cout; ++co) {
+            double s = 0.0;
+            for (int bb = 0; bb < B; ++bb)
+                for (long l = 0; l < V; ++l) s += gz[((long)bb * cout + co) * V + l];
+            db[co] = s;
+        }
+    return 0;
+}

@@ -1040,6 +1040,16 @@ int darc_atlas_sgd_end(darc_cohort* c)
     return end(c);
 }
 
+int darc_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, int M, int N, int K, void* stream)
+{
+    if (!A_dev || !B_dev || !C_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (M < 128 || M % 128 || N < 16 || N > 256 || N % 16 || K < 16 || K % 16)
+        return fail(DARC_ERR_SHAPE, "gemm needs M % 128 == 0, N % 16 == 0 in [16, 256], K % 16 == 0");
+    if (((uintptr_t)A_dev & 15) || ((uintptr_t)B_dev & 15)) return fail(DARC_ERR_ARG, "operands must be 16-byte aligned");
+    CK(gemm_bf16(A_dev, B_dev, C_dev, M, N, K, (cudaStream_t)stream));
+    return DARC_OK;
+}
+
 int darc_set_profiling(darc_cohort* c, int on)
 {
     if (!c) return fail(DARC_ERR_ARG, "null cohort");

@@ -87,6 +87,48 @@ cudaError_t field_subtract(float* v, int B, const float* sum, float scale, const
 cudaError_t combine_grad(const float* gshared, const float* gsubj, int B, float scale, float* out,
                          const Vol& v, cudaStream_t s);
 
+// ---- tensor-core kernels (k_unet.cu) ----
+cudaError_t gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, cudaStream_t s);
+// one 3x3x3 'same' convolution (see darc_conv3d in darc.h for the fields)
+struct ConvDesc {
+    const void* in;               // bf16 channels-last [batch][D][H][W][in_stride]
+    int in_stride, cin;
+    const void* wt;               // bf16 [np][kp]
+    const float* bias;
+    void* out;                    // bf16 channels-last, channels [out_off, out_off + cout)
+    int out_stride, out_off, cout;
+    float* out_f32;               // planar fp32 [batch][cout][D * H * W] (replaces out)
+    const void* gate;             // bf16 channels-last: multiply by the leaky-ReLU slope where gate <= 0
+    int gate_stride;
+    int act;
+    float slope;
+    int batch, D, H, W, kp, np;
+};
+cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s);
+// dw [np][kp] fp32 = sum_v gz[v][co] im2col(in)[v][k]; partial: splits x kp x np floats
+cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout, float* partial,
+                        int splits, float* dw, int batch, int D, int H, int W, int kp, int np, cudaStream_t s);
+// db[c] = sum over voxels of gz[v][c]; (cout + 7) / 8 must divide 256; work:
+// bias_grad_work_floats(cout) floats
+int bias_grad_work_floats(int cout);
+cudaError_t bias_grad(const void* gz, int stride, long long nvox, int cout, float* db, float* work, cudaStream_t s);
+cudaError_t pool2(const void* x, int xs, void* y, int ys, int C, int B, int D, int H, int W, cudaStream_t s);
+cudaError_t pool2_adjoint(const void* gy, int gys, const void* x, int xs, void* gx, int gxs, int C, float slope, int B,
+                          int D, int H, int W, cudaStream_t s);
+cudaError_t up2(const void* x, int xs, void* y, int ys, int yoff, int C, int B, int D, int H, int W, cudaStream_t s);
+cudaError_t up2_adjoint(const void* gy, int gys, int gyoff, void* gx, int gxs, int C, int B, int D, int H, int W,
+                        cudaStream_t s);
+cudaError_t pack_input(const float* subj, const float* atlas, void* x, int xs, long long V, int B, cudaStream_t s);
+int velocity_loss_blocks(long long n);
+// pred, target planar [batch][3][V], n = batch * V
+cudaError_t velocity_loss(const float* pred, const float* target, long long n, long long V, void* g, int gs,
+                          double* partials, cudaStream_t s);
+cudaError_t weight_prep(const float* w, int kp, int np, int cin, int cin_real, int cout, int coutp, void* wb, void* wd,
+                        int kpd, int npd, cudaStream_t s);
+cudaError_t upsample_velocity(const float* vh, int Dh, int Hh, int Wh, float* v, int D, int H, int W, int B,
+                              cudaStream_t s);
+cudaError_t downsample_image(const float* I, int D, int H, int W, float* Ih, int B, cudaStream_t s);
+
 // ---- local NCC (k_lncc.cu) ----
 // Box sums need scratch P of B x (channels <= 3) x V floats for the 2-D sums.
 int box_blocks(const Vol& v);

@@ -102,6 +102,22 @@ _SIGS = {
                                ctypes.POINTER(ctypes.c_double)]),
     "darc_launch_count": (ctypes.c_longlong, [_vp]),
     "darc_exp_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
+    "darc_gemm_bf16": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "darc_conv3d": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _i, _vp, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _i,
+                         _vp]),
+    "darc_conv3d_wgrad": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp]),
+    "darc_resample_half": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "darc_upsample_velocity": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "darc_unet_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, ctypes.c_ulonglong]),
+    "darc_unet_destroy": (None, [_vp]),
+    "darc_unet_forward": (_i, [_vp, _vp, _vp, _i, _vp, _vp]),
+    "darc_unet_train_step": (_i, [_vp, _vp, _vp, _vp, _i, _f, ctypes.POINTER(_f), _vp]),
+    "darc_unet_gradients": (_i, [_vp, _vp, _vp, _vp, _i, ctypes.POINTER(_f), _vp]),
+    "darc_unet_layer_info": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                  ctypes.POINTER(_i)]),
+    "darc_unet_layer_params": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _i]),
+    "darc_unet_save": (_i, [_vp, ctypes.c_char_p]),
+    "darc_unet_load": (_i, [_vp, ctypes.c_char_p]),
     "darc_velocity_sum": (_i, [_vp, _vp]),
     "darc_centrality_apply": (_i, [_vp, _vp, ctypes.c_longlong]),
     "darc_atlas_partial": (_i, [_vp, _vp]),
@@ -392,6 +408,170 @@ def exp_backward_noalloc(v: torch.Tensor, u: torch.Tensor, gT: torch.Tensor, sig
     _check(lib().darc_exp_backward_noalloc(_ptr(v), _ptr(u), _ptr(gT), _ptr(gv), B, D, H, W, u.shape[0],
                                            sign, _stream()))
     return gv
+
+
+def gemm_bf16(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
+    """C = A B^T on the tensor cores (bf16 in, fp32 out)."""
+    _need(A, "A", torch.bfloat16)
+    _need(B, "B", torch.bfloat16)
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().darc_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), M, N, K, _stream()))
+    return C
+
+
+def conv3d(x: torch.Tensor, cin: int, wt: torch.Tensor, cout: int, bias: Optional[torch.Tensor] = None,
+           act: bool = False, slope: float = 0.2, gate: Optional[torch.Tensor] = None,
+           f32_out: bool = False) -> torch.Tensor:
+    """3x3x3 'same' convolution on the tensor cores (darc_conv3d).
+
+    x: bf16 channels-last [B, D, H, W, S] (channels [0, cin) read); wt: bf16
+    [np, kp], k = tap * cin + ci.  Returns bf16 [B, D, H, W, cout] or, with
+    f32_out, fp32 planar [B, cout, D, H, W]."""
+    _need(x, "x", torch.bfloat16)
+    _need(wt, "wt", torch.bfloat16)
+    B, D, H, W, S = (int(d) for d in x.shape)
+    np_, kp = (int(d) for d in wt.shape)
+    if bias is not None:
+        _need(bias, "bias")
+    gs = 0
+    if gate is not None:
+        _need(gate, "gate", torch.bfloat16)
+        gs = int(gate.shape[-1])
+    if f32_out:
+        out = torch.empty((B, cout, D, H, W), dtype=torch.float32, device=x.device)
+        _check(lib().darc_conv3d(_ptr(x), S, cin, _ptr(wt), _ptr(bias), None, cout, cout, _ptr(out), _ptr(gate),
+                                 gs, int(act), slope, B, D, H, W, kp, np_, _stream()))
+    else:
+        out = torch.empty((B, D, H, W, cout), dtype=torch.bfloat16, device=x.device)
+        _check(lib().darc_conv3d(_ptr(x), S, cin, _ptr(wt), _ptr(bias), _ptr(out), cout, cout, None, _ptr(gate),
+                                 gs, int(act), slope, B, D, H, W, kp, np_, _stream()))
+    return out
+
+
+def conv3d_wgrad(x: torch.Tensor, cin: int, gz: torch.Tensor, cout: int, kp: int, np_: int):
+    """(dw fp32 [np, kp], db fp32 [cout]) of darc_conv3d (darc_conv3d_wgrad);
+    gz: bf16 channels-last [B, D, H, W, S] gradient wrt the pre-activation."""
+    _need(x, "x", torch.bfloat16)
+    _need(gz, "gz", torch.bfloat16)
+    B, D, H, W, S = (int(d) for d in x.shape)
+    dw = torch.empty((np_, kp), dtype=torch.float32, device=x.device)
+    db = torch.empty(cout, dtype=torch.float32, device=x.device)
+    nbytes = 64 * kp * np_ * 4
+    work = _work(nbytes, x.device)
+    _check(lib().darc_conv3d_wgrad(_ptr(x), S, cin, _ptr(gz), int(gz.shape[-1]), cout, _ptr(dw), _ptr(db), B, D, H,
+                                   W, kp, np_, _ptr(work), nbytes, _stream()))
+    return dw, db
+
+
+def resample_half(I: torch.Tensor) -> torch.Tensor:
+    """Mean of each 2x2x2 block: [B, D, H, W] -> [B, D/2, H/2, W/2]."""
+    _need(I, "I")
+    B, D, H, W = (int(d) for d in I.shape)
+    out = torch.empty((B, D // 2, H // 2, W // 2), dtype=torch.float32, device=I.device)
+    _check(lib().darc_resample_half(_ptr(I), B, D, H, W, _ptr(out), _stream()))
+    return out
+
+
+def upsample_velocity(vh: torch.Tensor) -> torch.Tensor:
+    """Half-resolution velocity [B, 3, Dh, Hh, Wh] -> [B, 3, 2Dh, 2Hh, 2Wh]
+    (trilinear at cell centres, values doubled)."""
+    _need(vh, "vh")
+    B, _, Dh, Hh, Wh = (int(d) for d in vh.shape)
+    out = torch.empty((B, 3, 2 * Dh, 2 * Hh, 2 * Wh), dtype=torch.float32, device=vh.device)
+    _check(lib().darc_upsample_velocity(_ptr(vh), B, Dh, Hh, Wh, _ptr(out), _stream()))
+    return out
+
+
+class UNet:
+    """The warm-start 3-D U-Net on the tensor cores (darc_unet_*): 4 levels of
+    16-32-64-128 channels at the resolution (D, H, W), BF16 weights and
+    activations, FP32 master weights and accumulation."""
+
+    N_LAYERS = 15
+
+    def __init__(self, shape, max_batch: int = 4, seed: int = 0, device="cuda:0"):
+        self.shape = tuple(int(s) for s in shape)
+        self.max_batch = int(max_batch)
+        self.device = torch.device(device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().darc_unet_create(ctypes.byref(h), *self.shape, self.max_batch, int(seed)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().darc_unet_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _inputs(self, subj, atlas):
+        _need(subj, "subj")
+        _need(atlas, "atlas")
+        if tuple(subj.shape[1:]) != self.shape or tuple(atlas.shape) != self.shape:
+            raise ValueError(f"inputs must be [B, {self.shape}] and {self.shape}")
+        return int(subj.shape[0])
+
+    def forward(self, subj: torch.Tensor, atlas: torch.Tensor) -> torch.Tensor:
+        """Velocity [B, 3, D, H, W] (voxel units of this grid)."""
+        B = self._inputs(subj, atlas)
+        v = torch.empty((B, 3, *self.shape), dtype=torch.float32, device=subj.device)
+        _check(lib().darc_unet_forward(self._h, _ptr(subj), _ptr(atlas), B, _ptr(v), _stream()))
+        return v
+
+    def train_step(self, subj, atlas, target, lr: float = 1e-3, want_loss: bool = True):
+        """One Adam step on the mean squared error to target; returns the loss
+        before the step (or None without want_loss, which avoids a sync)."""
+        B = self._inputs(subj, atlas)
+        _need(target, "target")
+        out = ctypes.c_float(0.0)
+        _check(lib().darc_unet_train_step(self._h, _ptr(subj), _ptr(atlas), _ptr(target), B, float(lr),
+                                          ctypes.byref(out) if want_loss else None, _stream()))
+        return out.value if want_loss else None
+
+    def gradients(self, subj, atlas, target) -> float:
+        B = self._inputs(subj, atlas)
+        _need(target, "target")
+        out = ctypes.c_float(0.0)
+        _check(lib().darc_unet_gradients(self._h, _ptr(subj), _ptr(atlas), _ptr(target), B, ctypes.byref(out),
+                                         _stream()))
+        return out.value
+
+    def layer_info(self, layer: int):
+        """(padded cin, cout, kp, np) of layer 0..14."""
+        vals = [ctypes.c_int() for _ in range(4)]
+        _check(lib().darc_unet_layer_info(self._h, layer, *[ctypes.byref(v) for v in vals]))
+        return tuple(v.value for v in vals)
+
+    def params(self, layer: int):
+        """(w [np, kp], b [cout], dw [np, kp], db [cout]) fp32 copies."""
+        cin, cout, kp, np_ = self.layer_info(layer)
+        w = torch.empty((np_, kp), dtype=torch.float32, device=self.device)
+        dw = torch.empty_like(w)
+        b = torch.empty(cout, dtype=torch.float32, device=self.device)
+        db = torch.empty_like(b)
+        _check(lib().darc_unet_layer_params(self._h, layer, _ptr(w), _ptr(b), _ptr(dw), _ptr(db), 0))
+        return w, b, dw, db
+
+    def set_params(self, layer: int, w: torch.Tensor, b: torch.Tensor):
+        _need(w, "w")
+        _need(b, "b")
+        cin, cout, kp, np_ = self.layer_info(layer)
+        if tuple(w.shape) != (np_, kp) or tuple(b.shape) != (cout,):
+            raise ValueError(f"layer {layer}: w [{np_}, {kp}], b [{cout}]")
+        _check(lib().darc_unet_layer_params(self._h, layer, _ptr(w), _ptr(b), None, None, 1))
+
+    def save(self, path: str):
+        _check(lib().darc_unet_save(self._h, path.encode()))
+
+    def load(self, path: str):
+        _check(lib().darc_unet_load(self._h, path.encode()))
 
 
 def warp(I: torch.Tensor, u: torch.Tensor) -> torch.Tensor:

@@ -1,0 +1,272 @@
+"""Tensor-core (tcgen05) kernels of the learned warm start against FP64
+products of the same BF16 values (numpy on the host)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2508_10743_gb300 import darc
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2508_10743_gb300 import build
+    build.build()
+    darc.lib()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 16), (256, 32, 64), (384, 48, 144), (128, 128, 432), (256, 256, 96)])
+def test_gemm_bf16_matches_fp64_product(M, N, K):
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16)
+    C = darc.gemm_bf16(A.to(DEV), B.to(DEV)).cpu().double().numpy()
+    ref = A.double().numpy() @ B.double().numpy().T
+    assert np.abs(C - ref).max() <= 1e-5 * np.abs(ref).max() + 1e-6
+
+
+# ---------------------------------------------------------------------------
+# implicit-GEMM convolutions against the FP64 oracle on the same BF16 values
+# ---------------------------------------------------------------------------
+import oracle                                     # noqa: E402
+from oracle import unet as ounet                  # noqa: E402
+
+U = 2.0 ** -24                                    # unit roundoff of fp32
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _oracle():
+    oracle.build()
+
+
+def rup(x, m):
+    return (x + m - 1) // m * m
+
+
+def to_oracle_x(x, cin):
+    """bf16 channels-last [B, D, H, W, S] -> fp64 [B, cin, D, H, W]."""
+    return np.ascontiguousarray(x[..., :cin].permute(0, 4, 1, 2, 3).double().cpu().numpy())
+
+
+def to_oracle_w(wt, cin, cout):
+    """[np, kp] with k = tap * cin + ci -> [cout, cin, 3, 3, 3]."""
+    a = wt.double().cpu().numpy()[:cout, :27 * cin].reshape(cout, 27, cin)
+    return np.ascontiguousarray(a.transpose(0, 2, 1).reshape(cout, cin, 3, 3, 3))
+
+
+def to_gpu_w(w_or, cinp, kp, np_):
+    cout, cin = w_or.shape[:2]
+    blk = np.zeros((cout, 27, cinp))
+    blk[:, :, :cin] = w_or.reshape(cout, cin, 27).transpose(0, 2, 1)
+    t = np.zeros((np_, kp))
+    t[:cout, :27 * cinp] = blk.reshape(cout, 27 * cinp)
+    return torch.from_numpy(t).float()
+
+
+def rand_w(g, cin, cout, kp, np_, scale=0.2):
+    w = torch.zeros(np_, kp)
+    w[:cout, :27 * cin] = torch.randn(cout, 27 * cin, generator=g) * scale
+    return w.to(torch.bfloat16)
+
+
+CONV_CASES = [
+    # B, (D, H, W), cin, stride, cout, np     (voxel counts not multiples of 128: ragged last tile)
+    (2, (6, 7, 9), 16, 16, 16, 16),
+    (1, (5, 8, 12), 8, 8, 3, 16),
+    (2, (4, 6, 10), 48, 64, 32, 32),
+    (1, (4, 4, 8), 16, 16, 192, 192),
+    (1, (4, 5, 6), 128, 128, 128, 128),
+]
+
+
+@pytest.mark.parametrize("B,shape,cin,S,cout,np_", CONV_CASES)
+def test_conv3d_fp32_output_matches_oracle(B, shape, cin, S, cout, np_):
+    g = torch.Generator().manual_seed(B * 1000 + cin + cout)
+    kp = rup(27 * cin, 16)
+    x = torch.randn(B, *shape, S, generator=g).to(torch.bfloat16)
+    wt = rand_w(g, cin, cout, kp, np_)
+    bias = torch.randn(cout, generator=g) * 0.1
+    got = darc.conv3d(x.to(DEV), cin, wt.to(DEV), cout, bias=bias.to(DEV), f32_out=True).cpu().double().numpy()
+    xo, wo, bo = to_oracle_x(x, cin), to_oracle_w(wt, cin, cout), bias.double().numpy()
+    ref = oracle.conv3d(xo, wo, bo)
+    # bf16 x bf16 products are exact in fp32; K + 1 fp32 additions in any order
+    bound = 2 * (27 * cin + 1) * U * oracle.conv3d(np.abs(xo), np.abs(wo), np.abs(bo))
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("B,shape,cin,S,cout,np_", CONV_CASES[:3])
+def test_conv3d_bf16_output_with_activation_and_gate(B, shape, cin, S, cout, np_):
+    g = torch.Generator().manual_seed(7 + cin)
+    kp = rup(27 * cin, 16)
+    x = torch.randn(B, *shape, S, generator=g).to(torch.bfloat16)
+    wt = rand_w(g, cin, cout, kp, np_)
+    bias = torch.randn(cout, generator=g) * 0.1
+    gate = torch.randn(B, *shape, cout, generator=g).to(torch.bfloat16)
+    got = darc.conv3d(x.to(DEV), cin, wt.to(DEV), cout, bias=bias.to(DEV), act=True, gate=gate.to(DEV))
+    got = got.permute(0, 4, 1, 2, 3).double().cpu().numpy()
+    xo, wo, bo = to_oracle_x(x, cin), to_oracle_w(wt, cin, cout), bias.double().numpy()
+    gf = np.where(to_oracle_x(gate, cout) > 0, 1.0, 0.2)
+    ref = ounet.lrelu(oracle.conv3d(xo, wo, bo)) * gf
+    bound = 2 * (27 * cin + 1) * U * oracle.conv3d(np.abs(xo), np.abs(wo), np.abs(bo))
+    # one rounding to bf16 (half an ulp of 2^-8 relative) on top of the fp32 sum
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + bound)
+
+
+@pytest.mark.parametrize("B,shape,cin,cout", [(2, (6, 7, 9), 16, 16), (1, (4, 6, 8), 192, 64), (1, (5, 6, 7), 16, 3)])
+def test_conv3d_as_data_gradient_matches_oracle_adjoint(B, shape, cin, cout):
+    """The data gradient is the forward kernel run on gz with the flipped,
+    transposed weights wd[ci][tap' * coutp + co] = w[co][ci][26 - tap']."""
+    g = torch.Generator().manual_seed(cin * 31 + cout)
+    coutp = rup(cout, 8)
+    w_or = (torch.randn(cout, cin, 3, 3, 3, generator=g) * 0.2).to(torch.bfloat16).double().numpy()
+    gz = torch.zeros(B, *shape, coutp)
+    gz[..., :cout] = torch.randn(B, *shape, cout, generator=g)
+    gz = gz.to(torch.bfloat16)
+    kpd, npd = rup(27 * coutp, 16), rup(cin, 16)
+    wd = np.zeros((npd, kpd))
+    flat = w_or.reshape(cout, cin, 27)
+    for tp in range(27):
+        wd[:cin, tp * coutp:tp * coutp + cout] = flat[:, :, 26 - tp].T
+    wd = torch.from_numpy(wd).to(torch.bfloat16)
+    gate = torch.randn(B, *shape, cin, generator=g).to(torch.bfloat16)
+    got = darc.conv3d(gz.to(DEV), coutp, wd.to(DEV), cin, gate=gate.to(DEV), f32_out=True).cpu().double().numpy()
+    gzo = to_oracle_x(gz, cout)
+    gf = np.where(to_oracle_x(gate, cin) > 0, 1.0, 0.2)
+    ref = oracle.conv3d_adjoint_input(gzo, w_or) * gf
+    bound = 2 * (27 * coutp + 1) * U * oracle.conv3d_adjoint_input(np.abs(gzo), np.abs(w_or))
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+@pytest.mark.parametrize("B,shape,cin,S,cout", [(2, (6, 7, 9), 16, 16, 16), (2, (16, 16, 20), 8, 8, 8),
+                                                 (1, (8, 8, 12), 48, 48, 16), (1, (4, 4, 8), 128, 128, 128)])
+def test_conv3d_weight_gradient_matches_oracle(B, shape, cin, S, cout):
+    g = torch.Generator().manual_seed(cin * 7 + cout + B)
+    kp, np_ = rup(27 * cin, 16), rup(cout, 16)
+    x = torch.randn(B, *shape, S, generator=g).to(torch.bfloat16)
+    gz = torch.randn(B, *shape, cout, generator=g).to(torch.bfloat16)
+    dw, db = darc.conv3d_wgrad(x.to(DEV), cin, gz.to(DEV), cout, kp, np_)
+    xo, gzo = to_oracle_x(x, cin), to_oracle_x(gz, cout)
+    ref_dw, ref_db = oracle.conv3d_wgrad(xo, gzo)
+    abs_dw, abs_db = oracle.conv3d_wgrad(np.abs(xo), np.abs(gzo))
+    nvox = B * int(np.prod(shape))
+    got_dw = to_oracle_w(dw, cin, cout)
+    # every partial and the fixed-order split reduction are fp32 sums of at most nvox + 1 terms
+    assert np.all(np.abs(got_dw - ref_dw) <= 2 * (nvox + 1) * U * abs_dw)
+    assert np.linalg.norm(got_dw - ref_dw) <= 1e-5 * np.linalg.norm(ref_dw)
+    assert not dw[cout:].any() and not dw[:, 27 * cin:].any()
+    assert np.all(np.abs(db.cpu().double().numpy() - ref_db) <= 2 * (nvox + 1) * U * abs_db)
+
+
+# ---------------------------------------------------------------------------
+# the whole network
+# ---------------------------------------------------------------------------
+
+def make_net(shape, B, seed):
+    net = darc.UNet(shape, max_batch=B, seed=99, device=DEV)
+    params = ounet.init_params(seed)
+    p32 = []
+    for i, (w, b) in enumerate(params):
+        cinp, cout, kp, np_ = net.layer_info(i)
+        w32, b32 = w.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64)
+        net.set_params(i, to_gpu_w(w32, cinp, kp, np_).to(DEV), torch.from_numpy(b32).float().to(DEV))
+        p32.append((w32, b32))
+    return net, p32
+
+
+def net_inputs(shape, B, seed):
+    r = np.random.Generator(np.random.PCG64(seed))
+    subj = r.uniform(size=(B,) + shape).astype(np.float32)
+    atlas = r.uniform(size=shape).astype(np.float32)
+    target = r.normal(scale=0.5, size=(B, 3) + shape).astype(np.float32)
+    return subj, atlas, target
+
+
+def test_unet_forward_and_gradients_match_oracle():
+    shape, B = (16, 16, 24), 2
+    net, p32 = make_net(shape, B, 11)
+    subj, atlas, target = net_inputs(shape, B, 12)
+    ts, ta, tt = (torch.from_numpy(a).to(DEV) for a in (subj, atlas, target))
+    pred = net.forward(ts, ta).cpu().double().numpy()
+    loss = net.gradients(ts, ta, tt)
+    L, ref_pred, grads = ounet.loss_and_grad(p32, subj.astype(np.float64), atlas.astype(np.float64),
+                                             target.astype(np.float64), bf16=True)
+    # Same bf16 storage on both sides; what separates them is the fp32 (GPU)
+    # against fp64 (oracle) summation deciding some bf16 roundings the other
+    # way.  Perturbing every oracle sum by a relative 1e-7 (less than one
+    # fp32 rounding) moves this prediction by 2.8e-3 and the per-layer weight
+    # and bias gradients by up to 1.5e-2 and 1.1e-2 (relative norms): the
+    # floor of any bf16 implementation.  The bounds are ~3x those floors; a
+    # wrong index, term or sign gives errors of order one.
+    assert np.linalg.norm(pred - ref_pred) <= 1e-2 * np.linalg.norm(ref_pred)
+    assert abs(loss - L) <= 1e-3 * L
+    for i in range(15):
+        cinp, cout, kp, np_ = net.layer_info(i)
+        _, _, dw, db = net.params(i)
+        got = to_oracle_w(dw, cinp, cout)[:, :ounet.LAYERS[i][0]]
+        ref = grads[i][0]
+        assert np.linalg.norm(got - ref) <= 5e-2 * np.linalg.norm(ref), i
+        assert np.linalg.norm(db.cpu().double().numpy() - grads[i][1]) <= 5e-2 * np.linalg.norm(grads[i][1]), i
+        assert not dw[cout:].any()
+
+
+def test_unet_training_reduces_the_loss_and_save_load_round_trips(tmp_path):
+    shape, B = (16, 16, 16), 2
+    net = darc.UNet(shape, max_batch=B, seed=5, device=DEV)
+    subj, atlas, target = net_inputs(shape, B, 13)
+    ts, ta = torch.from_numpy(subj).to(DEV), torch.from_numpy(atlas).to(DEV)
+    # a learnable target: a smooth function of the input
+    tt = torch.stack([ts * 0.5, -ts * 0.25 + 0.1, ts * ta], dim=1).contiguous()
+    # (at lr 2e-3 this 15-layer net without normalisation diverges in fp64 too)
+    losses = [net.train_step(ts, ta, tt, lr=3e-4) for _ in range(60)]
+    assert all(np.isfinite(losses))
+    assert losses[-1] < 0.5 * losses[0]
+    path = str(tmp_path / "net.bin")
+    net.save(path)
+    other = darc.UNet(shape, max_batch=B, seed=6, device=DEV)
+    assert not torch.equal(other.forward(ts, ta), net.forward(ts, ta))
+    other.load(path)
+    assert torch.equal(other.forward(ts, ta), net.forward(ts, ta))
+    # both continue identically (Adam state restored too)
+    assert other.train_step(ts, ta, tt, lr=1e-3) == net.train_step(ts, ta, tt, lr=1e-3)
+    assert torch.equal(other.forward(ts, ta), net.forward(ts, ta))
+
+
+def test_unet_rejects_bad_shapes():
+    with pytest.raises(darc.DarcError):
+        darc.UNet((20, 16, 16), max_batch=1, device=DEV)
+    net = darc.UNet((16, 16, 16), max_batch=1, device=DEV)
+    x = torch.zeros(2, 16, 16, 16, device=DEV)
+    with pytest.raises(darc.DarcError):
+        net.forward(x, x[0].contiguous())
+
+
+def test_resample_half_and_upsample_velocity_match_oracle():
+    g = torch.Generator().manual_seed(3)
+    I = torch.rand(2, 10, 12, 14, generator=g)
+    got = darc.resample_half(I.to(DEV)).cpu().double().numpy()
+    ref = ounet.downsample(I.double().numpy())
+    assert np.abs(got - ref).max() <= 1e-6
+    vh = torch.randn(2, 3, 5, 6, 7, generator=g)
+    got = darc.upsample_velocity(vh.to(DEV)).cpu().double().numpy()
+    ref = ounet.upsample_velocity(vh.double().numpy())
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_warm_start_writes_upsampled_network_velocities_into_the_cohort():
+    from paper_2508_10743_gb300 import configs, synth, warmstart
+    co = synth.make_cohort(4, (32, 32, 32), 77, device=DEV, keep_w=False, keep_disp=False,
+                           **configs.WORKLOADS["mse32"].gen)
+    images = co.images.contiguous()
+    c = darc.Cohort(images, configs.WORKLOADS["mse32"].config)
+    net = darc.UNet((16, 16, 16), max_batch=4, seed=3, device=DEV)
+    A = c.atlas()
+    warmstart.warm_start(c, net, batch=3)
+    Ih, Ah = warmstart.half_inputs(images, A)
+    v = darc.upsample_velocity(net.forward(Ih, Ah))
+    for i in range(4):
+        assert torch.equal(c.velocity(i), v[i])
+    # the oracle's definitions of the two resamplings around the network
+    assert np.abs(Ih.cpu().double().numpy() - ounet.downsample(images.cpu().double().numpy())).max() <= 1e-6
+    c.sweep()
