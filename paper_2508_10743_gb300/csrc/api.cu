@@ -67,7 +67,7 @@ int check_config(const darc_config* c, int D, int H, int W)
     if (c->inner_steps < 1 || c->atlas_epochs < 0 || c->atlas_batch < 1 || c->subject_batch < 0)
         return fail(DARC_ERR_ARG, "bad step / batch count");
     if (c->center_mode != 0) return fail(DARC_ERR_ARG, "only center_mode 0 (velocities) is built");
-    if (c->checkpoint_stride != 0) return fail(DARC_ERR_ARG, "checkpoint_stride > 0 is not built in this library");
+    if (c->checkpoint_stride < 0) return fail(DARC_ERR_ARG, "checkpoint_stride must be >= 0");
     return DARC_OK;
 }
 
@@ -114,6 +114,74 @@ void minibatch_order(uint64_t seed, int sweep, int epoch, int n, int* perm)
 }
 
 // Exp forward of `cnt` fields into u (T slots of cnt*3V); returns u_T
+// Which squaring fields the adjoint keeps.  Stride s (2 <= s < T): u_t is
+// stored for (t + 1) % s == 0 and for the last step; every other field sits
+// in one of s - 1 scratch slots (slot t % s) and is recomputed, one segment
+// of s steps at a time, from the checkpoint below it.  Stride 0, 1 or >= T
+// keeps all T.  Fields are t = 0..T-1 = the outputs of the T squarings.
+struct CkPlan {
+    int T, s, nck;
+    CkPlan(int T_, int stride) : T(T_), s((stride <= 1 || stride >= T_) ? 0 : stride)
+    {
+        nck = s ? T / s + (T % s != 0) : T;
+    }
+    int fields() const { return s ? nck + s - 1 : T; }
+    bool kept(int t) const { return !s || (t + 1) % s == 0 || t == T - 1; }
+    int slot(int t) const
+    {
+        if (!s) return t;
+        if ((t + 1) % s == 0) return (t + 1) / s - 1;
+        if (t == T - 1) return nck - 1;
+        return nck + t % s;
+    }
+    // segment of the last field the forward leaves in scratch (-1: none)
+    int scratch_segment() const
+    {
+        if (!s) return -1;
+        for (int t = T - 1; t >= 0; --t)
+            if (!kept(t)) return t / s;
+        return -1;
+    }
+};
+
+// Forward squarings into the plan's slots; sq(src, scale, dst) launches one.
+template <typename Sq>
+cudaError_t exp_forward_plan(const CkPlan& pl, const float* v, float* u, size_t fb, float s0, Sq sq)
+{
+    for (int t = 0; t < pl.T; ++t) {
+        const float* src = t ? u + (size_t)pl.slot(t - 1) * fb : v;
+        cudaError_t e = sq(src, t ? 1.f : s0, u + (size_t)pl.slot(t) * fb);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Adjoint steps t = T-1 .. 0 in segment order, recomputing a segment's
+// scratch fields when they are not the ones the forward left there;
+// adj(t, src, scale) runs the adjoint of step t.
+template <typename Sq, typename Adj>
+cudaError_t exp_backward_plan(const CkPlan& pl, const float* v, float* u, size_t fb, float s0, Sq sq, Adj adj)
+{
+    const int s = pl.s ? pl.s : pl.T;
+    int have = pl.scratch_segment();
+    for (int j = (pl.T - 1) / s; j >= 0; --j) {
+        const int a = j * s, e = std::min(a + s, pl.T) - 1;
+        if (pl.s && e > a && j != have) {
+            for (int t = a; t < e; ++t) {
+                const float* src = t ? u + (size_t)pl.slot(t - 1) * fb : v;
+                cudaError_t err = sq(src, t ? 1.f : s0, u + (size_t)pl.slot(t) * fb);
+                if (err != cudaSuccess) return err;
+            }
+            have = j;
+        }
+        for (int t = e; t >= a; --t) {
+            cudaError_t err = adj(t, t ? u + (size_t)pl.slot(t - 1) * fb : v, t ? 1.f : s0);
+            if (err != cudaSuccess) return err;
+        }
+    }
+    return cudaSuccess;
+}
+
 cudaError_t exp_forward_all(const float* v, float* u, int cnt, const Vol& vol, int T, float sign,
                             cudaStream_t s)
 {
@@ -210,6 +278,7 @@ struct darc_cohort {
     int *perm_dev = nullptr, *iota_dev = nullptr;
     int* perm_host = nullptr;    // pinned [K3][n]
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    std::map<std::pair<int, int>, long long> graph_kernels;     // kernels per replay of each graph
     std::map<std::pair<int, int>, int> seen;
     // sharded atlas SGD state
     int sgd_k = 0;
@@ -319,19 +388,15 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     const float* Ib = c->images + (size_t)f * vol.V;
     cudaError_t e = cudaSuccess;
     const float s0 = std::ldexp(1.0f, -T);
-    {
-        const float* src = vb;
-        float scale = s0;
-        for (int t = 0; t < T && e == cudaSuccess; ++t) {
-            float* dst = c->u_all + (size_t)t * fb;
-            Prof p(c, s, DARC_K_EXP_SQUARE, 24.0 * nv);
-            e = exp_square(src, scale, dst, cnt, vol, s);
-            src = dst;
-            scale = 1.f;
-        }
-    }
+    const CkPlan plan(T, c->cfg.checkpoint_stride);
+    auto sq = [&](const float* src, float scale, float* dst) {
+        Prof p(c, s, DARC_K_EXP_SQUARE, 24.0 * nv);
+        c->launches += 1;
+        return exp_square(src, scale, dst, cnt, vol, s);
+    };
+    e = exp_forward_plan(plan, vb, c->u_all, fb, s0, sq);
     if (e != cudaSuccess) return e;
-    const float* uT = c->u_all + (size_t)(T - 1) * fb;
+    const float* uT = c->u_all + (size_t)plan.slot(T - 1) * fb;
     const double *pLp, *pRp;
     int nL, nR, sL, sR;
     if (c->cfg.dissim == DARC_MSE) {
@@ -365,19 +430,21 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     float* gv = (T >= 2) ? c->gT : c->gbuf;
     {
         const float* gin = c->gT;
-        for (int t = T - 1; t >= 0 && e == cudaSuccess; --t) {
-            const float* src = (t == 0) ? vb : c->u_all + (size_t)(t - 1) * fb;
+        auto adj = [&](int t, const float* src, float scale) {
             float* gout = (t == 0) ? gv : c->gbuf + (size_t)((T - 1 - t) % 2) * fb;
-            e = cudaMemsetAsync(gout, 0, fb * sizeof(float), s);
-            if (e != cudaSuccess) break;
+            cudaError_t err = cudaMemsetAsync(gout, 0, fb * sizeof(float), s);
+            if (err != cudaSuccess) return err;
             Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
-            e = exp_square_adjoint(src, (t == 0) ? s0 : 1.f, gin, gout, (t == 0) ? s0 : 1.f, cnt, vol, s);
+            c->launches += 1;
+            err = exp_square_adjoint(src, scale, gin, gout, scale, cnt, vol, s);
             gin = gout;
-        }
+            return err;
+        };
+        e = exp_backward_plan(plan, vb, c->u_all, fb, s0, sq, adj);
     }
     if (e != cudaSuccess) return e;
     Prof p(c, s, DARC_K_ADAM, 84.0 * nv);
-    c->launches += 2 * T + 2;
+    c->launches += 2;
     return adam_fields(c->v + (size_t)f * 3 * vol.V, c->m + (size_t)f * 3 * vol.V,
                        c->s + (size_t)f * 3 * vol.V, gv, 1.f, c->bias + f, c->flags + f, c->cfg.beta1,
                        c->cfg.beta2, c->cfg.adam_eps, cnt, 3 * vol.V, s);
@@ -407,7 +474,8 @@ int run_steps(darc_cohort* c, int first, int count, int steps)
             CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
             const long long before = c->launches;
             cudaError_t e = enqueue_step(c, f, cnt, c->st);
-            c->launches = before;   // recording launches nothing
+            c->graph_kernels[key] = c->launches - before;   // kernels one replay launches
+            c->launches = before;                           // recording launches nothing
             cudaError_t e2 = cudaStreamEndCapture(c->st, &g);
             if (e != cudaSuccess || e2 != cudaSuccess) {
                 if (g) cudaGraphDestroy(g);
@@ -420,7 +488,7 @@ int run_steps(darc_cohort* c, int first, int count, int steps)
             CK(e);
             it = c->graphs.emplace(key, ex).first;
         }
-        const long long per_step = (c->cfg.dissim == DARC_MSE ? 1 : 3) + 2LL * c->cfg.n_squarings + 2;
+        const long long per_step = c->graph_kernels[key];
         for (int s = done; s < steps; ++s) {
             CK(cudaGraphLaunch(it->second, c->st));
             c->launches += per_step;
@@ -604,7 +672,7 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     ALLOC(c->nonfinite, 1);
     ALLOC(c->loss, 2 * (size_t)n);
     ALLOC(c->A, v.V);
-    ALLOC(c->u_all, F * c->bmax * std::max(T, 2));
+    ALLOC(c->u_all, F * c->bmax * std::max(CkPlan(T, cfg->checkpoint_stride).fields(), 2));
     ALLOC(c->gT, F * c->bmax);
     ALLOC(c->gbuf, 2 * F * c->bmax);
     ALLOC(c->pL, 2 * (size_t)nb * bsub);
@@ -1218,7 +1286,8 @@ size_t darc_subject_grad_workspace(const darc_config* cfg, int B, int D, int H, 
     if (!cfg) return 0;
     const size_t V = (size_t)D * H * W, F = 3 * V * B;
     const int T = std::max(cfg->n_squarings, 1);
-    return align256(sizeof(float) * F * T) + align256(sizeof(float) * F) + 2 * align256(sizeof(float) * F) +
+    const size_t fields = (size_t)CkPlan(T, cfg->checkpoint_stride).fields();
+    return align256(sizeof(float) * F * fields) + align256(sizeof(float) * F) + 2 * align256(sizeof(float) * F) +
            align256(sizeof(float) * V * B) + align256(sizeof(float) * 3 * V * B) + align256(sizeof(float) * 2 * V) +
            2 * darc_loss_workspace(B, D, H, W) + align256(sizeof(float) * 3 * V * B);
 }
@@ -1236,7 +1305,8 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     const int T = cfg->n_squarings;
     const size_t F = 3 * (size_t)v.V * B;
     Carve cv(work_dev);
-    float* u_all = cv.take<float>(F * T);
+    const CkPlan plan(T, cfg->checkpoint_stride);
+    float* u_all = cv.take<float>(F * plan.fields());
     float* gT = cv.take<float>(F);
     float* gbuf = cv.take<float>(2 * F);
     float* Wimg = cv.take<float>((size_t)v.V * B);
@@ -1245,8 +1315,10 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     double* pL = cv.take<double>(2 * (size_t)B * nblk_max(v));
     double* pR = cv.take<double>(2 * (size_t)B * nblk_max(v));
     float* P = cv.take<float>(3 * (size_t)B * v.V);
-    CK(exp_forward_all(v_dev, u_all, B, v, T, 1.f, s));
-    const float* uT = u_all + (size_t)(T - 1) * F;
+    const float s0 = std::ldexp(1.0f, -T);
+    auto sq = [&](const float* src, float scale, float* dst) { return exp_square(src, scale, dst, B, v, s); };
+    CK(exp_forward_plan(plan, v_dev, u_all, F, s0, sq));
+    const float* uT = u_all + (size_t)plan.slot(T - 1) * F;
     if (cfg->dissim == DARC_MSE) {
         CK(mse_warp_reg(I_dev, v.V, A_dev, uT, cfg->lambda, gT, pL, B, v, s));
         CK(reduce_partials(pL, voxel_blocks(v), 2, 1.0, energy_dev, 2, B, s));
@@ -1259,7 +1331,16 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
         CK(reduce_partials(pL, box_blocks(v), 1, 1.0, energy_dev, 2, B, s));
         CK(reduce_partials(pR, box_blocks(v), 1, 1.0, energy_dev + 1, 2, B, s));
     }
-    CK(exp_backward_all(v_dev, u_all, gT, gv_dev, gbuf, B, v, T, 1.f, s));
+    const float* gin = gT;
+    auto adj = [&](int t, const float* src, float scale) {
+        float* gout = (t == 0) ? gv_dev : gbuf + (size_t)((T - 1 - t) % 2) * F;
+        cudaError_t e = cudaMemsetAsync(gout, 0, F * sizeof(float), s);
+        if (e != cudaSuccess) return e;
+        e = exp_square_adjoint(src, scale, gin, gout, scale, B, v, s);
+        gin = gout;
+        return e;
+    };
+    CK(exp_backward_plan(plan, v_dev, u_all, F, s0, sq, adj));
     return DARC_OK;
 }
 

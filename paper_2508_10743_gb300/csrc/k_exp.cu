@@ -13,6 +13,8 @@
 // lanes usually share an x-corner, so a lane hands its upper x-corner
 // contribution to the next lane when the cells coincide, and sends the two
 // x-corners of a (z, y) pair as one 8-byte atomic when they are aligned.
+// Along z, each thread walks consecutive planes and merges the upper-z
+// corners of one source with the lower-z corners of the next in registers.
 #include "kernels.h"
 
 #include <climits>
@@ -48,9 +50,12 @@ exp_square_kernel(const float* __restrict__ src, float scale, float* __restrict_
 
 // Adjoint tiles: 32 x 8 x ADJ_Z sources per block (each thread walks ADJ_Z
 // planes).  PAIR: lanes hand coinciding x-corners to their neighbour;
-// VEC2: a lane's two x-corners go out as one 8-byte atomic when aligned.
+// VEC2: a lane's two x-corners go out as one 8-byte atomic when aligned;
+// CARRY: a thread keeps its upper-z corners in registers and adds them to
+// the lower-z corners of its next plane when the two cells coincide (the
+// usual case for a smooth field), so most corners are sent once, not twice.
 #ifndef DARC_ADJ_Z
-#define DARC_ADJ_Z 4
+#define DARC_ADJ_Z 8
 #endif
 #ifndef DARC_ADJ_PAIR
 #define DARC_ADJ_PAIR 1
@@ -58,7 +63,56 @@ exp_square_kernel(const float* __restrict__ src, float scale, float* __restrict_
 #ifndef DARC_ADJ_VEC2
 #define DARC_ADJ_VEC2 1
 #endif
+#ifndef DARC_ADJ_CARRY
+#define DARC_ADJ_CARRY 1
+#endif
 constexpr int ADJ_Z = DARC_ADJ_Z;
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// The two x-corners (a, a + 1) of one (z, y) corner pair, three channels.
+// Every lane of the warp calls it (shuffles); inactive lanes pass act = false.
+__device__ __forceinline__ void emit_xpair(float* const o[3], int a, bool act, const float lo[3],
+                                           const float hi[3], int lane, int vec2)
+{
+    bool absorb = false, given = false;
+    if (DARC_ADJ_PAIR) {
+        const int pa = __shfl_up_sync(FULL_MASK, act ? a : -4, 1);
+        absorb = act && lane > 0 && pa >= 0 && pa + 1 == a;
+        given = __shfl_down_sync(FULL_MASK, absorb, 1) && lane < 31;
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        float lo_v = lo[ch];
+        if (DARC_ADJ_PAIR) {
+            const float ph = __shfl_up_sync(FULL_MASK, hi[ch], 1);
+            if (absorb) lo_v += ph;
+        }
+        if (!act) continue;
+        if (given) {
+            atomicAdd(o[ch] + a, lo_v);
+        } else if (DARC_ADJ_VEC2 && vec2 && (a & 1) == 0) {
+            atomicAdd(reinterpret_cast<float2*>(o[ch] + a), make_float2(lo_v, hi[ch]));
+        } else {
+            atomicAdd(o[ch] + a, lo_v);
+            atomicAdd(o[ch] + a + 1, hi[ch]);
+        }
+    }
+}
+
+// Same without the lane exchange (divergent callers).
+__device__ __forceinline__ void emit_plain(float* const o[3], int a, const float lo[3], const float hi[3],
+                                           int vec2)
+{
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        if (DARC_ADJ_VEC2 && vec2 && (a & 1) == 0) {
+            atomicAdd(reinterpret_cast<float2*>(o[ch] + a), make_float2(lo[ch], hi[ch]));
+        } else {
+            atomicAdd(o[ch] + a, lo[ch]);
+            atomicAdd(o[ch] + a + 1, hi[ch]);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(VT_THREADS)
 exp_square_adjoint_kernel(const float* __restrict__ src, float scale, const float* __restrict__ gin,
@@ -81,10 +135,12 @@ exp_square_adjoint_kernel(const float* __restrict__ src, float scale, const floa
     o[1] = o[0] + v.V;
     o[2] = o[1] + v.V;
     const int plane = v.H * v.W;
+    float cl[2][3], cu[2][3];        // carried upper-z pairs: [dy][channel] lower / upper x-corner
+    int ca = -1;                     // base index of the carried pairs (-1: none)
     for (int k = 0; k < ADJ_Z; ++k) {
         const int z = zt * ADJ_Z + k;
         const bool active = xy_ok && z < v.D;
-        if (!DARC_ADJ_PAIR && !active) break;
+        if (!DARC_ADJ_PAIR && !DARC_ADJ_CARRY && !active) break;
         float w[8], gs[3] = {0.f, 0.f, 0.f};
         int cb = -4;
         if (active) {
@@ -109,35 +165,47 @@ exp_square_adjoint_kernel(const float* __restrict__ src, float scale, const floa
 #pragma unroll
             for (int q = 0; q < 8; ++q) w[q] = 0.f;
         }
-        // transpose of the interpolation: the 8 corners, as 4 (dz, dy) pairs of x-corners
-#pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            const int a = active ? cb + ((q >> 2) & 1) * plane + ((q >> 1) & 1) * v.W : -4;
-            bool absorb = false, given = false;
-            if (DARC_ADJ_PAIR) {
-                const int pa = __shfl_up_sync(0xffffffffu, a, 1);
-                absorb = active && lane > 0 && pa >= 0 && pa + 1 == a;
-                given = __shfl_down_sync(0xffffffffu, absorb, 1) && lane < 31;
+        // transpose of the interpolation: the 8 corners as 4 (dz, dy) pairs of x-corners
+        if (DARC_ADJ_CARRY) {
+            const bool merge = active && ca == cb;
+            if (ca >= 0 && !merge) {                 // the carried corners are not this cell's: send them
+                emit_plain(o, ca, cl[0], cu[0], vec2);
+                emit_plain(o, ca + v.W, cl[1], cu[1], vec2);
             }
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float lo_v = w[q] * gs[ch];
-                const float hi_v = w[q + 1] * gs[ch];
-                if (DARC_ADJ_PAIR) {
-                    const float ph = __shfl_up_sync(0xffffffffu, hi_v, 1);
-                    if (absorb) lo_v += ph;
+            for (int dy = 0; dy < 2; ++dy) {
+                float lo[3], hi[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    lo[ch] = w[2 * dy] * gs[ch] + (merge ? cl[dy][ch] : 0.f);
+                    hi[ch] = w[2 * dy + 1] * gs[ch] + (merge ? cu[dy][ch] : 0.f);
                 }
-                if (!active) continue;
-                if (given) {
-                    atomicAdd(o[ch] + a, lo_v);
-                } else if (DARC_ADJ_VEC2 && vec2 && (a & 1) == 0) {
-                    atomicAdd(reinterpret_cast<float2*>(o[ch] + a), make_float2(lo_v, hi_v));
-                } else {
-                    atomicAdd(o[ch] + a, lo_v);
-                    atomicAdd(o[ch] + a + 1, hi_v);
+                emit_xpair(o, cb + dy * v.W, active, lo, hi, lane, vec2);
+            }
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    cl[dy][ch] = w[4 + 2 * dy] * gs[ch];
+                    cu[dy][ch] = w[5 + 2 * dy] * gs[ch];
                 }
+            ca = active ? cb + plane : -1;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                float lo[3], hi[3];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    lo[ch] = w[q] * gs[ch];
+                    hi[ch] = w[q + 1] * gs[ch];
+                }
+                emit_xpair(o, cb + ((q >> 2) & 1) * plane + ((q >> 1) & 1) * v.W, active, lo, hi, lane, vec2);
             }
         }
+    }
+    if (DARC_ADJ_CARRY) {
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) emit_xpair(o, ca + dy * v.W, ca >= 0, cl[dy], cu[dy], lane, vec2);
     }
 }
 

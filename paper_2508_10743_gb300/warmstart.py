@@ -36,19 +36,25 @@ def half_inputs(images: torch.Tensor, atlas: torch.Tensor):
     return darc.resample_half(images), darc.resample_half(atlas[None].contiguous())[0].contiguous()
 
 
-def make_pairs(workload: str, seeds: List[int], sweeps: int, device="cuda:0", log=None) -> Dict:
-    """Register each seeded cohort of `workload` for `sweeps` sweeps from v = 0.
+def make_pairs(seeds: List[int], sweeps: int, gen_workload: str = "brain", run_workload: str = "unet_half",
+               device="cuda:0", log=None) -> Dict:
+    """Training pairs from the plain method at half resolution.
 
-    Returns subj [N, D, H, W], atlas [C, D, H, W] (A^0 of each cohort),
-    cohort [N] (index into atlas) and target [N, 3, D, H, W] (the final
-    centred velocities), all on `device`."""
-    wl = configs.WORKLOADS[workload]
+    Each seeded cohort of `gen_workload` (full resolution) is reduced by
+    2x2x2 block means and registered from v = 0 for `sweeps` sweeps with the
+    settings of `run_workload`.  Returns subj [N, D, H, W], atlas [C, D, H, W]
+    (A^0 of each cohort), cohort [N] (index into atlas) and target
+    [N, 3, D, H, W] (the final centred velocities), all on `device`."""
+    gw, rw = configs.WORKLOADS[gen_workload], configs.WORKLOADS[run_workload]
     subj, atlas, cohort, target = [], [], [], []
     for c, seed in enumerate(seeds):
         t0 = time.perf_counter()
-        co = synth.make_cohort(wl.n, wl.shape, seed, device=device, keep_w=False, keep_disp=False, **wl.gen)
-        images = co.images.contiguous()
-        run = darc.Cohort(images, wl.config)
+        co = synth.make_cohort(gw.n, gw.shape, seed, device=device, keep_w=False, keep_disp=False, **gw.gen)
+        images = darc.resample_half(co.images.contiguous())
+        del co
+        if tuple(images.shape[1:]) != rw.shape:
+            raise ValueError(f"{gen_workload} halves to {tuple(images.shape[1:])}, not {rw.shape}")
+        run = darc.Cohort(images, rw.config)
         atlas.append(run.atlas())
         t1 = time.perf_counter()
         for _ in range(sweeps):
@@ -174,12 +180,16 @@ def main(argv=None):
     log = lambda m: print(m, flush=True)               # noqa: E731
     dev = args.device
     wl = configs.WORKLOADS["unet_half"]
+    gw = configs.WORKLOADS[args.eval_workload]
     t0 = time.perf_counter()
-    data = make_pairs("unet_half", [wl.seed + k for k in range(args.train_cohorts)], args.pair_sweeps, dev, log)
-    val = make_pairs("unet_half", [wl.seed + 500 + k for k in range(args.val_cohorts)], args.pair_sweeps, dev, log)
+    data = make_pairs([gw.seed + 100 + k for k in range(args.train_cohorts)], args.pair_sweeps,
+                      args.eval_workload, "unet_half", dev, log)
+    val = make_pairs([gw.seed + 700 + k for k in range(args.val_cohorts)], args.pair_sweeps,
+                     args.eval_workload, "unet_half", dev, log)
     t_pairs = time.perf_counter() - t0
     net = darc.UNet(wl.shape, max_batch=args.batch, seed=1, device=dev)
     val0 = evaluate(net, val, args.batch)
+    val_zero = float((val["target"] ** 2).mean())          # the plain method's start, v = 0
     tr = train(net, data, args.epochs, args.batch, args.lr, seed=1, val=val, log=log)
     if args.save:
         net.save(args.save)
@@ -203,7 +213,7 @@ def main(argv=None):
         log(json.dumps({k2: v for k2, v in evals[-1].items() if not k2.endswith("_ncc") or "final" in k2}))
     out = {"train_cohorts": args.train_cohorts, "samples": args.train_cohorts * wl.n, "pair_sweeps": args.pair_sweeps,
            "pairs_seconds": t_pairs, "epochs": args.epochs, "batch": args.batch, "lr": args.lr,
-           "val_loss_before": val0, "train": tr, "eval_workload": args.eval_workload, "eval": evals}
+           "val_loss_before": val0, "val_loss_of_zero_velocity": val_zero, "train": tr, "eval_workload": args.eval_workload, "eval": evals}
     print(json.dumps(out))
     return out
 

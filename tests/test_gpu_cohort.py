@@ -196,6 +196,25 @@ def test_subject_batches_give_the_same_result():
     assert float(((out[0] - out[1]).abs() <= 1e-4).float().mean()) > 0.99
 
 
+def test_checkpoint_stride_gives_the_same_sweep():
+    shape, n = (10, 12, 14), 4
+    co = cohort_images(n, shape, 9)
+    imgs = co.images.to(DEV).contiguous()
+    out, launches = [], []
+    for stride in (0, 3):
+        cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=3, n_squarings=7, checkpoint_stride=stride,
+                                 inner_steps=3, atlas_epochs=2, atlas_batch=2)
+        c = darc.Cohort(imgs, cfg)
+        before = c.launch_count()
+        c.subject_step(0, n, 3)
+        launches.append(c.launch_count() - before)
+        c.update_atlas()
+        out.append(torch.stack([c.velocity(i) for i in range(n)]))
+    assert float(((out[0] - out[1]).abs() <= 1e-4).float().mean()) > 0.99
+    # T = 7, stride 3: u_3 and u_6 recomputed once per step (2 more squarings)
+    assert launches[1] - launches[0] == 3 * 2
+
+
 def test_sharded_hooks_reproduce_the_fused_updates():
     """The exchange hooks of a sharded cohort, run on one GPU: MSE with two
     shards equals one cohort of all subjects; NCC with one shard equals the

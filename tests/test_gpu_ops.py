@@ -160,6 +160,23 @@ def test_subject_gradient(dissim, w, T):
         assert rel_l2(np64(gv[b]), g) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("stride", [2, 3, 4])
+def test_subject_gradient_with_checkpointed_squarings(stride):
+    """Keeping every stride-th squaring field and recomputing the rest gives
+    the oracle's gradient (the recomputed fields are bit-identical: the
+    forward squaring is a pure gather)."""
+    shape = (18, 21, 35)
+    I, A = image(shape, 91, B=2), image(shape, 92)[0].contiguous()
+    v = field(shape, 93, max_disp=2.5, B=2)
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=7, lam=0.8, checkpoint_stride=stride)
+    energy, gv = darc.subject_grad(cfg, I.to(DEV), A.to(DEV), v.to(DEV))
+    ocfg = oracle.make_cfg(dissim=configs.LNCC, window=5, T=7, lam=0.8)
+    for b in range(2):
+        E, parts, g = oracle.subject_energy(np64(I[b]), np64(A), np64(v[b]), ocfg)
+        assert abs(float(energy[b, 0]) - parts[0]) <= FWD_TOL * abs(parts[0])
+        assert rel_l2(np64(gv[b]), g) <= GRAD_TOL
+
+
 def test_adam_step():
     rng = np.random.default_rng(0)
     th, m, s, g = (rng.standard_normal(10001).astype(np.float32) for _ in range(4))
