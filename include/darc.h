@@ -337,36 +337,54 @@ int darc_jacobian_det(const float* u_dev, float* det_dev, unsigned long long* co
  * K % 16 == 0.  Errors: ARG, CUDA. */
 int darc_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, int M, int N, int K, void* stream);
 
-/* 3x3x3 'same' convolution (zero padding) as an implicit GEMM on the tensor
- * cores, BF16 operands, FP32 accumulation:
- *   z[v][co] = bias[co] + sum_{tap, ci} in[v + off(tap)][ci] * wt[co][tap*cin + ci]
+/* 3x3x3 'same' convolution (zero padding) on the tensor cores, BF16
+ * operands, FP32 accumulation:
+ *   z[v][co] = bias[co] + sum_{tap, ci} in[v + off(tap)][ci] * W[co][tap][ci]
  *   off(tap) = (tap/9 - 1, (tap/3)%3 - 1, tap%3 - 1) in (z, y, x).
- * in_dev: bf16 channels-last [batch][D][H][W][in_stride], channels [0, cin)
- * read; wt_dev: bf16 [np][kp], zero past 27*cin and past cout; bias_dev:
- * fp32 [cout] or null.  Epilogue: act = 1 applies a leaky ReLU of slope
- * `slope`; gate_dev (bf16 channels-last, stride gate_stride, or null)
+ * Volumes are bf16 channels-last with a one-voxel zero border:
+ * [batch][D+2][H+2][W+2][stride]; the border of the input must be zero and
+ * the border of the output is not written.  in_dev: channels [0, cin)
+ * read; wt_dev: weights packed by darc_conv3d_pack_weights (flip 0);
+ * bias_dev: fp32 [cout] or null.  Epilogue: act = 1 applies a leaky ReLU of
+ * slope `slope`; gate_dev (same geometry, stride gate_stride, or null)
  * multiplies each result by 1 where gate > 0 and by `slope` elsewhere (the
  * data gradient through a leaky ReLU whose output is the gate).  Output:
- * out_dev bf16 channels-last [..][out_stride], channels [0, cout) -- or,
- * when out_f32_dev is non-null, fp32 planar [batch][cout][D*H*W].
- * Requirements: cin % 8 == 0, in_stride % 8 == 0, kp % 16 == 0,
- * kp >= 27 cin, np % 16 == 0 with 16 <= np <= 256, cout <= np, 16-byte
- * aligned in_dev and wt_dev.  Errors: ARG, SHAPE, CUDA. */
+ * out_dev, channels [0, cout) -- or, when out_f32_dev is non-null, fp32
+ * planar without border [batch][cout][D*H*W].  np: cout rounded up to 16.
+ * The data gradient of a layer is this call on dL/dz (cin = its cout
+ * rounded up to 16) with weights packed with flip 1 and np = its cin.
+ * Requirements: cin % 16 == 0, in_stride % 8 == 0, np % 16 == 0 with
+ * 16 <= np <= 256, cout <= np, W small enough for two shared-memory stages
+ * (W <= 581 at np = 256), 16-byte aligned in_dev and wt_dev.
+ * Errors: ARG, SHAPE, CUDA. */
 int darc_conv3d(const void* in_dev, int in_stride, int cin, const void* wt_dev, const float* bias_dev, void* out_dev,
                 int out_stride, int cout, float* out_f32_dev, const void* gate_dev, int gate_stride, int act,
-                float slope, int batch, int D, int H, int W, int kp, int np, void* stream);
+                float slope, int batch, int D, int H, int W, int np, void* stream);
 
-/* Weight and bias gradients of darc_conv3d:
- *   dw[co][k] = sum_v gz[v][co] * im2col(in)[v][k]   (fp32 [np][kp])
- *   db[co]    = sum_v gz[v][co]                      (fp32 [cout], db_dev may be null)
- * gz_dev: bf16 channels-last gradient wrt the pre-activation, stride
- * gz_stride, cout % 8 == 0 channels read (zero-padded), cout / 8 dividing
- * 256 when db_dev is given; np % 16 == 0 with cout <= np <= 128.  Split-K
- * partial sums go to work_dev (fp32, work_bytes) and are added in a fixed
- * order, so the result is deterministic.  Errors: ARG (also: workspace
- * smaller than one split), SHAPE, CUDA. */
+/* Bytes of packed bf16 weights for a convolution with conv_cin input
+ * channels and nrows output rows (both multiples of 16; 0 otherwise). */
+size_t darc_conv3d_packed_bytes(int conv_cin, int nrows);
+
+/* Packs fp32 weights w_dev [>= cout][kp] (k = tap * cin + ci, zero past
+ * 27 cin) for darc_conv3d: flip = 0 the layer itself (conv_cin = cin,
+ * nrows = cout rounded up to 16); flip = 1 its data gradient, the
+ * transposed, mirrored kernel W'[ci][tap][co] = W[co][26 - tap][ci]
+ * (conv_cin = cout rounded up to 16, nrows = cin).  packed_dev: 16-byte
+ * aligned, darc_conv3d_packed_bytes(conv_cin, nrows) bytes.
+ * Errors: ARG, SHAPE, CUDA. */
+int darc_conv3d_pack_weights(const float* w_dev, int kp, int cin, int cout, int flip, void* packed_dev, void* stream);
+
+/* Weight and bias gradients of darc_conv3d (same padded geometry):
+ *   dw[co][k] = sum_v gz[v][co] * in[v + off(tap)][ci], k = tap*cin + ci  (fp32 [np][27 cin])
+ *   db[co]    = sum_v gz[v][co]                                         (fp32 [cout], db_dev may be null)
+ * gz_dev: gradient wrt the pre-activation (zero border), stride gz_stride,
+ * cout % 8 == 0 channels read, cout / 8 dividing 256 when db_dev is given;
+ * cin % 16 == 0; np % 16 == 0 with cout <= np <= 128.  Split-K partial sums
+ * go to work_dev (fp32, work_bytes) and are added in a fixed order, so the
+ * result is deterministic.  Errors: ARG (also: workspace smaller than one
+ * split), SHAPE, CUDA. */
 int darc_conv3d_wgrad(const void* in_dev, int in_stride, int cin, const void* gz_dev, int gz_stride, int cout,
-                      float* dw_dev, float* db_dev, int batch, int D, int H, int W, int kp, int np, void* work_dev,
+                      float* dw_dev, float* db_dev, int batch, int D, int H, int W, int np, void* work_dev,
                       size_t work_bytes, void* stream);
 
 /* Half-resolution image (mean of each 2x2x2 block): I_dev fp32 [B][D][H][W]
@@ -408,7 +426,7 @@ int darc_unet_gradients(darc_unet* u, const float* subj_dev, const float* atlas_
                         float* loss_host, void* stream);
 /* Layer l in 0..14 (encoder 0-7, decoder 8-13, head 14): padded input
  * channels cin (multiple of 8), cout, and the weight matrix shape [np][kp]
- * with k = tap*cin + ci. */
+ * with k = tap*cin + ci (cin rounded up to 16). */
 int darc_unet_layer_info(darc_unet* u, int layer, int* cin, int* cout, int* kp, int* np);
 /* set = 0: copy the fp32 master weights [np][kp], bias [cout] and the last
  * gradients out (null pointers skip); set = 1: load w and b (refreshing the

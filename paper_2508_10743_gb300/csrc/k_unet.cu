@@ -1,6 +1,17 @@
 // k_unet.cu -- BF16 tensor-core (tcgen05, TMEM) kernels for the learned
-// warm start: a dense GEMM core and the implicit-GEMM 3-D convolutions of the
-// U-Net (forward, data gradient, weight gradient).
+// warm start: a dense GEMM core and the 3-D convolutions of the U-Net
+// (forward and data gradient by one kernel, weight gradient by another).
+//
+// Activations are channels-last bf16 volumes stored with a one-voxel zero
+// border ([batch][D+2][H+2][W+2][stride]).  In the flattened padded index a
+// 3x3x3 tap is a constant row shift, (dz-1) P + (dy-1) (W+2) + (dx-1) with
+// P = (H+2)(W+2), so the convolution of 128 consecutive padded rows reads,
+// for each dz, one contiguous window of 128 + 2 (W+2) + 2 rows, and the nine
+// (dy, dx) taps are the same window seen from nine start rows.  In the
+// no-swizzle K-major layout the rows of a window are 16 bytes apart, so a
+// tap is a shared-memory descriptor whose start address moves by 16 bytes a
+// row: one staged window feeds nine MMAs.  Border rows of the output are
+// computed and discarded; the borders of every buffer stay zero.
 #include "kernels.h"
 #include "umma.cuh"
 
@@ -15,6 +26,24 @@ using bf16 = __nv_bfloat16;
 constexpr int TC_M = 128;            // rows of a CTA tile (TMEM lanes)
 constexpr int TC_KC = 64;            // K elements staged per round (4 MMAs of K = 16)
 constexpr long long TC_WAIT = 1LL << 26;
+constexpr int CONV_SMEM_MAX = 225 * 1024;      // dynamic; the static mbarriers and TMEM slot take the rest of 227 KB
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(umma::smem_u32(dst_smem)), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// padded row of interior voxel (z, y, x)
+__device__ __forceinline__ long long pad_row(const PadVol& g, int z, int y, int x)
+{
+    return ((long long)(z + 1) * g.Hp + (y + 1)) * g.Wp + (x + 1);
+}
 
 // C[M x N] (fp32, row-major) = A[M x K] (bf16, K contiguous) * B[N x K]^T
 // (bf16, K contiguous).  Grid: M / 128 CTAs of 128 threads; N <= 256.
@@ -86,52 +115,54 @@ gemm_bf16_kernel(const bf16* __restrict__ A, const bf16* __restrict__ B, float* 
 }
 
 
+
 // ---------------------------------------------------------------------------
-// 3x3x3 'same' convolution as an implicit GEMM on the tensor cores.
-//   out[v][co] = act( sum_{tap, ci} in[v + off(tap)][ci] * W[co][tap*cin + ci] + bias[co] )
-// Activations are channels-last bf16 with a per-voxel stride (multiple of 8)
-// so a layer can read or write a channel slice of a wider buffer (skip
-// concatenation costs nothing).  Rows of the GEMM are 128 consecutive voxels
-// of the batch; K runs over (tap, channel) in groups of 8 channels (16 bytes,
-// one gather); N is the padded output channel count (<= 128).  Two shared
-// stages alternate so the gathers of one overlap the MMAs of the other.
-struct ConvArgs {
+// 3x3x3 'same' convolution on the tensor cores (forward, and the data
+// gradient when run on dL/dz with flipped weights):
+//   out[q][co] = act( bias[co] + sum_{tap, ci} in[q + off(tap)][ci] W[co][tap][ci] )
+// A CTA owns 128 consecutive padded rows q (TMEM lanes) x np output channels
+// (TMEM columns).  Stage (c, dz), c = 16-channel chunk: the dz window of the
+// chunk (2 x R rows of 16 bytes) and the chunk's nine (dy, dx) weight tiles
+// are copied with cp.async; one elected thread issues nine M128 x N x K16
+// MMAs whose A descriptors start (dy (W+2) + dx) rows into the window.  ns
+// stages rotate; a stage's slot is refilled once the commit of the MMAs
+// that read it has arrived on the slot's mbarrier (bounded waits; a timeout
+// poisons the output with NaN instead of hanging).
+struct WinArgs {
     const bf16* in;
-    int in_stride, cin;           // channels used: [0, cin), cin % 8 == 0
-    const bf16* wt;               // [np][kp] bf16, k = tap * cin + ci, zero padded
+    int in_stride, nchunk;        // channels [0, 16 nchunk) read
+    const bf16* wt;               // packed [nchunk][3][9][2][np][8]
     const float* bias;            // [cout] or null
     bf16* out;
-    int out_stride, out_off, cout;
-    float* out_f32;               // optional planar fp32 output [batch][cout][D*H*W] (instead of out)
-    const bf16* gate;             // optional: result *= (gate > 0 ? 1 : slope), gate channels-last
+    int out_stride, cout, out_vec;
+    float* out_f32;               // planar [batch][cout][D H W] (replaces out)
+    const bf16* gate;             // x slope where gate <= 0 (same geometry), or null
     int gate_stride;
     int act;                      // 1: leaky ReLU
     float slope;
-    int D, H, W;
-    long long nvox;               // batch * D * H * W
-    int kp, np;
+    int B;
+    PadVol g;
+    int np, R, ns, slot_bytes;
+    long long tiles_per_batch;
 };
 
-constexpr int CONV_SMEM_STAGE_A = TC_M * TC_KC * 2;     // 16 KB
-
 __global__ void __launch_bounds__(128)
-conv3_fwd_kernel(ConvArgs a)
+conv3_win_kernel(WinArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t mbar[3];
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long m0 = (long long)blockIdx.x * TC_M;
-    const int stageB = a.np * TC_KC * 2;
-    uint8_t* sA[2] = {smem, smem + CONV_SMEM_STAGE_A + stageB};
-    uint8_t* sB[2] = {smem + CONV_SMEM_STAGE_A, smem + 2 * CONV_SMEM_STAGE_A + stageB};
-    const uint32_t lboA = (TC_M / 8) * 128, lboB = (uint32_t)(a.np / 8) * 128;
+    const PadVol g = a.g;
+    const int b = (int)(blockIdx.x / a.tiles_per_batch);
+    const long long q0 = g.P + (long long)(blockIdx.x % a.tiles_per_batch) * TC_M;
+    const long long base_b = (long long)b * g.Vp;
+    const long long rows_total = (long long)a.B * g.Vp;
     uint32_t ncols = 32;
     while ((int)ncols < a.np) ncols <<= 1;
     if (warp == 0) umma::tmem_alloc(&tslot, ncols);
     if (tid == 0) {
-        umma::mbar_init(&mbar[0], 1);
-        umma::mbar_init(&mbar[1], 1);
+        for (int k = 0; k < a.ns; ++k) umma::mbar_init(&mbar[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     umma::fence_before_sync();
@@ -139,73 +170,99 @@ conv3_fwd_kernel(ConvArgs a)
     umma::fence_after_sync();
     const uint32_t tmem = tslot;
     const uint32_t idesc = umma::idesc_bf16_f32(TC_M, a.np);
-    const long long plane = (long long)a.H * a.W, vol = (long long)a.D * plane;
+    const uint32_t lboA = (uint32_t)a.R * 16u, lboB = (uint32_t)a.np * 16u;
+    const int nst = 3 * a.nchunk;
+
+    auto load = [&](int st, int slot) {
+        const int c = st / 3, dz = st - 3 * c;
+        uint8_t* As = smem + (size_t)slot * a.slot_bytes;
+        uint8_t* Bs = As + 2 * lboA;
+        const long long r0 = base_b + q0 + (long long)(dz - 1) * g.P - g.Wp - 1;
+        for (int e = tid; e < 2 * a.R; e += 128) {
+            const int r = e >> 1, grp = e & 1;
+            const long long qg = r0 + r;
+            const bool in_buf = qg >= 0 && qg < rows_total;
+            const bf16* src = in_buf ? a.in + qg * a.in_stride + 16 * c + 8 * grp : a.in;
+            cp_async16(As + grp * lboA + r * 16, src, in_buf ? 16 : 0);
+        }
+        const bf16* w = a.wt + (size_t)(c * 3 + dz) * 18 * a.np * 8;
+        for (int e = tid; e < 18 * a.np; e += 128) cp_async16(Bs + (size_t)e * 16, w + (size_t)e * 8, 16);
+    };
+
+    for (int p = 0; p < a.ns - 1; ++p) {
+        if (p < nst) load(p, p);
+        cp_async_commit();
+    }
     bool ok = true;
-    const int steps = (a.kp + TC_KC - 1) / TC_KC;
-    for (int i = 0; i < steps; ++i) {
-        const int st = i & 1;
-        if (i >= 2) ok = umma::mbar_wait(&mbar[st], ((i - 2) >> 1) & 1, TC_WAIT) && ok;
-        const int k0 = i * TC_KC, kc = min(TC_KC, a.kp - k0);
-        const int ng = kc / 8;
-        // A: implicit im2col gather, one 16-byte group of 8 channels per load
-        for (int e = tid; e < TC_M * ng; e += 128) {
-            const int r = e / ng, g = e - r * ng;
-            const int k = k0 + 8 * g;
-            const int tap = k / a.cin, ci = k - tap * a.cin;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            const long long v = m0 + r;
-            if (tap < 27 && v < a.nvox) {
-                const long long bb = v / vol, rem = v - bb * vol;
-                const int z = (int)(rem / plane), y = (int)((rem / a.W) % a.H), x = (int)(rem % a.W);
-                const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-                if (zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
-                    const long long nv = bb * vol + ((long long)zz * a.H + yy) * a.W + xx;
-                    val = *reinterpret_cast<const uint4*>(a.in + nv * a.in_stride + ci);
-                }
-            }
-            *reinterpret_cast<uint4*>(sA[st] + umma::kmajor_offset(r, 8 * g, lboA)) = val;
+    for (int i = 0; i < nst; ++i) {
+        const int j = i + a.ns - 1;
+        if (j < nst) {
+            const int sj = j % a.ns;
+            if (j >= a.ns) ok = umma::mbar_wait(&mbar[sj], (uint32_t)(((j - a.ns) / a.ns) & 1), TC_WAIT) && ok;
+            load(j, sj);
         }
-        for (int e = tid; e < a.np * ng; e += 128) {
-            const int r = e / ng, g = e - r * ng;
-            const uint4 val = *reinterpret_cast<const uint4*>(a.wt + (size_t)r * a.kp + k0 + 8 * g);
-            *reinterpret_cast<uint4*>(sB[st] + umma::kmajor_offset(r, 8 * g, lboB)) = val;
-        }
+        cp_async_commit();
+        if (a.ns == 3) cp_async_wait<2>();
+        else cp_async_wait<1>();
         umma::fence_smem_async();
         __syncthreads();
         if (tid == 0) {
             umma::fence_after_sync();
-            for (int j = 0; j < kc / 16; ++j) {
-                const uint64_t da = umma::smem_desc(umma::smem_u32(sA[st]) + 2 * j * lboA, lboA, 128);
-                const uint64_t db = umma::smem_desc(umma::smem_u32(sB[st]) + 2 * j * lboB, lboB, 128);
-                umma::mma_bf16(tmem, da, db, idesc, (k0 + 16 * j) > 0);
+            const uint32_t As = umma::smem_u32(smem + (size_t)(i % a.ns) * a.slot_bytes);
+            const uint32_t Bs = As + 2 * lboA;
+            for (int t9 = 0; t9 < 9; ++t9) {
+                const int dy = t9 / 3, dx = t9 - 3 * dy;
+                const uint64_t da = umma::smem_desc(As + (uint32_t)(dy * g.Wp + dx) * 16u, lboA, 128);
+                const uint64_t db = umma::smem_desc(Bs + (uint32_t)t9 * 2u * lboB, lboB, 128);
+                umma::mma_bf16(tmem, da, db, idesc, (i > 0) || (t9 > 0));
             }
-            umma::commit(&mbar[st]);
+            umma::commit(&mbar[i % a.ns]);
         }
     }
-    // the last two commits (one per stage) retire in order: wait for both
-    for (int i = max(steps - 2, 0); i < steps; ++i) ok = umma::mbar_wait(&mbar[i & 1], (i >> 1) & 1, TC_WAIT) && ok;
+    ok = umma::mbar_wait(&mbar[(nst - 1) % a.ns], (uint32_t)(((nst - 1) / a.ns) & 1), TC_WAIT) && ok;
     umma::fence_after_sync();
-    // epilogue: warp w holds voxels m0 + 32w .. m0 + 32w + 31 (TMEM lanes)
-    const long long v = m0 + 32 * warp + lane;
-    const bool in_range = v < a.nvox;
-    const long long vb = v / vol, vl = v - vb * vol;        // planar fp32 output is [batch][cout][vol]
+
+    // epilogue: warp w holds rows q0 + 32 w + lane
+    const long long q = q0 + 32 * warp + lane;
+    const int xp = (int)(q % g.Wp), yp = (int)((q / g.Wp) % g.Hp);
+    const long long zp = q / g.P;
+    const bool valid = zp <= g.D && yp >= 1 && yp <= g.H && xp >= 1 && xp <= g.W;
+    const long long orow = base_b + q;
+    const long long V = (long long)g.D * g.H * g.W;
+    const long long l = ((zp - 1) * g.H + (yp - 1)) * (long long)g.W + (xp - 1);
     for (int c = 0; c < a.np; c += 8) {
         float r8[8];
         umma::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, r8);
-        if (!in_range || c >= a.cout) continue;
+        if (!valid || c >= a.cout) continue;
+        float y8[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int co = c + j;
-            if (co >= a.cout) break;
             float y = ok ? r8[j] : __int_as_float(0x7fc00000);
-            if (a.bias) y += __ldg(a.bias + co);
-            if (a.act == 1) y = y > 0.f ? y : a.slope * y;
-            if (a.gate) {
-                const float gt = __bfloat162float(a.gate[v * a.gate_stride + co]);
-                y = gt > 0.f ? y : a.slope * y;
+            if (co < a.cout) {
+                if (a.bias) y += __ldg(a.bias + co);
+                if (a.act == 1) y = y > 0.f ? y : a.slope * y;
+                if (a.gate) {
+                    const float gt = __bfloat162float(a.gate[orow * a.gate_stride + co]);
+                    y = gt > 0.f ? y : a.slope * y;
+                }
             }
-            if (a.out_f32) a.out_f32[((size_t)vb * a.cout + co) * vol + vl] = y;
-            else a.out[v * a.out_stride + a.out_off + co] = __float2bfloat16(y);
+            y8[j] = y;
+        }
+        if (a.out_f32) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (c + j < a.cout) a.out_f32[((size_t)b * a.cout + c + j) * V + l] = y8[j];
+        } else if (a.out_vec && c + 8 <= a.cout) {
+            uint4 pk;
+            __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(y8[2 * j], y8[2 * j + 1]);
+            *reinterpret_cast<uint4*>(a.out + orow * a.out_stride + c) = pk;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (c + j < a.cout) a.out[orow * a.out_stride + c + j] = __float2bfloat16(y8[j]);
         }
     }
     umma::fence_before_sync();
@@ -213,22 +270,57 @@ conv3_fwd_kernel(ConvArgs a)
     if (warp == 0) umma::tmem_dealloc(tmem, ncols);
 }
 
+// packed[(((c 3 + dz) 9 + t9) 2 + grp) nrows + row] [e], tap = 9 dz + t9,
+// channel ch = 16 c + 8 grp + e of the convolution's input:
+//   forward (flip 0): row = output channel, W[row][tap][ch]
+//   data gradient (flip 1): row = input channel of the layer, ch = its output
+//   channel, W[ch][26 - tap][row]  (the transpose of the mirrored kernel)
+// from fp32 masters w[co][k], k = tap cin + ci; zero outside cout / cin.
+__global__ void pack_weights_kernel(const float* __restrict__ w, int kp, int cin, int cout, int nchunk, int nrows,
+                                    int flip, bf16* __restrict__ out)
+{
+    const long long n = (long long)nchunk * 54 * nrows * 8;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int e8 = (int)(e % 8);
+        long long rest = e / 8;
+        const int row = (int)(rest % nrows);
+        rest /= nrows;
+        const int grp = (int)(rest % 2);
+        rest /= 2;
+        const int t9 = (int)(rest % 9);
+        rest /= 9;
+        const int dz = (int)(rest % 3);
+        const int c = (int)(rest / 3);
+        const int tap = 9 * dz + t9, ch = 16 * c + 8 * grp + e8;
+        float val = 0.f;
+        if (!flip) {
+            if (row < cout && ch < cin) val = w[(size_t)row * kp + tap * cin + ch];
+        } else {
+            if (ch < cout && row < cin) val = w[(size_t)ch * kp + (26 - tap) * cin + row];
+        }
+        out[e] = __float2bfloat16(val);
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Weight gradient of a conv layer as a GEMM over voxels on the tensor cores:
-//   dW[co][k] = sum_v gz[v][co] * im2col(in)[v][k],  k = tap * cin + ci.
+// Weight gradient as a GEMM over the padded rows of the interior planes:
+//   dW[co][k] = sum_q gz[q][co] in[q + off(tap)][ci],  k = tap cin + ci.
 // Rows (TMEM lanes) are k in tiles of 128, columns co (np <= 128), K runs
-// over a CTA's range of voxels.  Both operands are stored voxel-major (8
-// channels per 16 bytes), so they are transposed while staging: one 16-byte
-// load gives 8 rows of one K column.  Each CTA writes its partial sums;
-// conv3_wgrad_reduce adds them in a fixed order.
+// over a CTA's range of rows.  Border rows contribute zero (gz is zero
+// there); their shifted reads can leave the buffer (the first border rows
+// of batch 0, the last of the last batch), so those are not made.
+// Operands are stored row-major by voxel, so they are transposed while
+// staging (one 16-byte load gives 8 k-rows of one K column).  Each CTA
+// writes its partial sums; conv3_wgrad_reduce adds them in a fixed order.
 struct WgradArgs {
     const bf16* in;
     int in_stride, cin;
-    const bf16* gz;             // channels-last gradient wrt the pre-activation
-    int gz_stride, cout;        // cout % 8 == 0 (padded storage)
+    const bf16* gz;             // gradient wrt the pre-activation, same geometry
+    int gz_stride, cout;        // cout % 8 == 0 channels read
     float* partial;             // [splits][kp][np]
-    int D, H, W;
-    long long nvox, chunk;      // voxels per split (multiple of 64)
+    PadVol g;
+    long long nrows, chunk;     // K extent (batch x D x P) and rows per split (multiple of 64)
+    long long rows_total;       // batch x Vp: rows of the buffers
     int kp, np;
 };
 
@@ -239,12 +331,13 @@ conv3_wgrad_kernel(WgradArgs a)
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const PadVol g = a.g;
     const int r0 = blockIdx.x * TC_M;                       // first k row of this tile
     const long long v0 = (long long)blockIdx.y * a.chunk;
-    const long long v1 = min(a.nvox, v0 + a.chunk);
-    const int stageB = a.np * TC_KC * 2;
-    uint8_t* sA[2] = {smem, smem + CONV_SMEM_STAGE_A + stageB};
-    uint8_t* sB[2] = {smem + CONV_SMEM_STAGE_A, smem + 2 * CONV_SMEM_STAGE_A + stageB};
+    const long long v1 = min(a.nrows, v0 + a.chunk);
+    const int stageA = TC_M * TC_KC * 2, stageB = a.np * TC_KC * 2;
+    uint8_t* sA[2] = {smem, smem + stageA + stageB};
+    uint8_t* sB[2] = {smem + stageA, smem + 2 * stageA + stageB};
     const uint32_t lboA = (TC_M / 8) * 128, lboB = (uint32_t)(a.np / 8) * 128;
     uint32_t ncols = 32;
     while ((int)ncols < a.np) ncols <<= 1;
@@ -259,7 +352,7 @@ conv3_wgrad_kernel(WgradArgs a)
     umma::fence_after_sync();
     const uint32_t tmem = tslot;
     const uint32_t idesc = umma::idesc_bf16_f32(TC_M, a.np);
-    const long long plane = (long long)a.H * a.W, vol = (long long)a.D * plane;
+    const long long DP = (long long)g.D * g.P;
     bool ok = true;
     const int steps = (int)((v1 - v0 + TC_KC - 1) / TC_KC);
     for (int i = 0; i < steps; ++i) {
@@ -268,7 +361,7 @@ conv3_wgrad_kernel(WgradArgs a)
         const long long vb = v0 + (long long)i * TC_KC;
         bf16* A16 = reinterpret_cast<bf16*>(sA[st]);
         bf16* B16 = reinterpret_cast<bf16*>(sB[st]);
-        // A: 64 voxels x 16 groups of 8 rows (k), transposed into K-major
+        // A: 64 rows x 16 groups of 8 k-rows, transposed into K-major
         for (int e = tid; e < TC_KC * (TC_M / 8); e += 128) {
             const int j = e % TC_KC, mg = e / TC_KC;
             const int k = r0 + 8 * mg;
@@ -276,22 +369,24 @@ conv3_wgrad_kernel(WgradArgs a)
             uint4 val = make_uint4(0u, 0u, 0u, 0u);
             const long long v = vb + j;
             if (tap < 27 && k < a.kp && v < v1) {
-                const long long bb = v / vol, rem = v - bb * vol;
-                const int z = (int)(rem / plane), y = (int)((rem / a.W) % a.H), x = (int)(rem % a.W);
-                const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-                if (zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
-                    val = *reinterpret_cast<const uint4*>(a.in + (bb * vol + ((long long)zz * a.H + yy) * a.W + xx) * a.in_stride + ci);
+                const long long row = (v / DP) * g.Vp + g.P + v % DP;
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                const long long src = row + (long long)(dz - 1) * g.P + (long long)(dy - 1) * g.Wp + (dx - 1);
+                if (src >= 0 && src < a.rows_total) val = *reinterpret_cast<const uint4*>(a.in + src * a.in_stride + ci);
             }
             const bf16* pv = reinterpret_cast<const bf16*>(&val);
 #pragma unroll
             for (int q = 0; q < 8; ++q) A16[umma::kmajor_offset(8 * mg + q, j, lboA) >> 1] = pv[q];
         }
-        // B: 64 voxels x (np / 8) groups of 8 output channels
+        // B: 64 rows x (np / 8) groups of 8 output channels
         for (int e = tid; e < TC_KC * (a.np / 8); e += 128) {
             const int j = e % TC_KC, cg = e / TC_KC;
             uint4 val = make_uint4(0u, 0u, 0u, 0u);
             const long long v = vb + j;
-            if (v < v1 && 8 * cg < a.cout) val = *reinterpret_cast<const uint4*>(a.gz + v * a.gz_stride + 8 * cg);
+            if (v < v1 && 8 * cg < a.cout) {
+                const long long row = (v / DP) * g.Vp + g.P + v % DP;
+                val = *reinterpret_cast<const uint4*>(a.gz + row * a.gz_stride + 8 * cg);
+            }
             const bf16* pv = reinterpret_cast<const bf16*>(&val);
 #pragma unroll
             for (int q = 0; q < 8; ++q) B16[umma::kmajor_offset(8 * cg + q, j, lboB) >> 1] = pv[q];
@@ -378,131 +473,117 @@ __global__ void bias_grad_reduce_kernel(const float* __restrict__ partial, int n
 }
 
 // ---------------------------------------------------------------------------
-// 2x average pooling of channels-last bf16 volumes and its adjoint.
-// The adjoint adds (g / 8) * lrelu'(x) into gx at each of the 8 children
-// (x = the pooled activation, whose pre-activation gradient this is).
-__global__ void pool2_kernel(const bf16* __restrict__ x, int xs, bf16* __restrict__ y, int ys, int C, int B, int D,
-                             int H, int W)
+// 2x average pooling of padded channels-last volumes and its adjoint (fine
+// grid gf, coarse grid gc = gf / 2).  The adjoint adds (g / 8) lrelu'(x) into
+// gx at each of the 8 children (x = the pooled activation, whose
+// pre-activation gradient this is).
+__global__ void pool2_kernel(const bf16* __restrict__ x, int xs, bf16* __restrict__ y, int ys, int C, int B,
+                             PadVol gf, PadVol gc)
 {
-    const int Do = D / 2, Ho = H / 2, Wo = W / 2;
-    const long long n = (long long)B * Do * Ho * Wo * C;
+    const long long n = (long long)B * gc.D * gc.H * gc.W * C;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(e % C);
-        long long v = e / C;
-        const int xo = (int)(v % Wo), yo = (int)((v / Wo) % Ho), zo = (int)((v / ((long long)Wo * Ho)) % Do);
-        const long long b = v / ((long long)Wo * Ho * Do);
+        const long long v = e / C;
+        const int xo = (int)(v % gc.W), yo = (int)((v / gc.W) % gc.H), zo = (int)((v / ((long long)gc.W * gc.H)) % gc.D);
+        const long long b = v / ((long long)gc.W * gc.H * gc.D);
         float s = 0.f;
         for (int q = 0; q < 8; ++q) {
-            const long long iv = ((b * D + 2 * zo + (q >> 2)) * H + 2 * yo + ((q >> 1) & 1)) * W + 2 * xo + (q & 1);
+            const long long iv = b * gf.Vp + pad_row(gf, 2 * zo + (q >> 2), 2 * yo + ((q >> 1) & 1), 2 * xo + (q & 1));
             s += __bfloat162float(x[iv * xs + c]);
         }
-        y[v * ys + c] = __float2bfloat16(0.125f * s);
+        y[(b * gc.Vp + pad_row(gc, zo, yo, xo)) * ys + c] = __float2bfloat16(0.125f * s);
     }
 }
 
 __global__ void pool2_adjoint_kernel(const bf16* __restrict__ gy, int gys, const bf16* __restrict__ x, int xs,
-                                     bf16* __restrict__ gx, int gxs, int C, float slope, int B, int D, int H, int W)
+                                     bf16* __restrict__ gx, int gxs, int C, float slope, int B, PadVol gf, PadVol gc)
 {
-    const long long n = (long long)B * D * H * W * C;
-    const int Ho = H / 2, Wo = W / 2, Do = D / 2;
+    const long long n = (long long)B * gf.D * gf.H * gf.W * C;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(e % C);
         const long long v = e / C;
-        const int xx = (int)(v % W), yy = (int)((v / W) % H), zz = (int)((v / ((long long)W * H)) % D);
-        const long long b = v / ((long long)W * H * D);
-        const long long ov = ((b * Do + zz / 2) * Ho + yy / 2) * Wo + xx / 2;
-        const float g = 0.125f * __bfloat162float(gy[ov * gys + c]);
-        const float act = __bfloat162float(x[v * xs + c]);
-        const float add = act > 0.f ? g : slope * g;
-        gx[v * gxs + c] = __float2bfloat16(__bfloat162float(gx[v * gxs + c]) + add);
+        const int xx = (int)(v % gf.W), yy = (int)((v / gf.W) % gf.H), zz = (int)((v / ((long long)gf.W * gf.H)) % gf.D);
+        const long long b = v / ((long long)gf.W * gf.H * gf.D);
+        const long long ov = b * gc.Vp + pad_row(gc, zz / 2, yy / 2, xx / 2);
+        const long long iv = b * gf.Vp + pad_row(gf, zz, yy, xx);
+        const float gv = 0.125f * __bfloat162float(gy[ov * gys + c]);
+        const float act = __bfloat162float(x[iv * xs + c]);
+        const float add = act > 0.f ? gv : slope * gv;
+        gx[iv * gxs + c] = __float2bfloat16(__bfloat162float(gx[iv * gxs + c]) + add);
     }
 }
 
 // nearest 2x upsampling into a channel slice, and its adjoint (sum of 8 children)
-__global__ void up2_kernel(const bf16* __restrict__ x, int xs, bf16* __restrict__ y, int ys, int yoff, int C, int B,
-                           int D, int H, int W)
+__global__ void up2_kernel(const bf16* __restrict__ x, int xs, bf16* __restrict__ y, int ys, int C, int B, PadVol gf,
+                           PadVol gc)
 {
-    const long long n = (long long)B * D * H * W * C;      // D, H, W: output size
+    const long long n = (long long)B * gf.D * gf.H * gf.W * C;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(e % C);
         const long long v = e / C;
-        const int xx = (int)(v % W), yy = (int)((v / W) % H), zz = (int)((v / ((long long)W * H)) % D);
-        const long long b = v / ((long long)W * H * D);
-        const long long iv = ((b * (D / 2) + zz / 2) * (H / 2) + yy / 2) * (W / 2) + xx / 2;
-        y[v * ys + yoff + c] = x[iv * xs + c];
+        const int xx = (int)(v % gf.W), yy = (int)((v / gf.W) % gf.H), zz = (int)((v / ((long long)gf.W * gf.H)) % gf.D);
+        const long long b = v / ((long long)gf.W * gf.H * gf.D);
+        y[(b * gf.Vp + pad_row(gf, zz, yy, xx)) * ys + c] = x[(b * gc.Vp + pad_row(gc, zz / 2, yy / 2, xx / 2)) * xs + c];
     }
 }
 
-__global__ void up2_adjoint_kernel(const bf16* __restrict__ gy, int gys, int gyoff, bf16* __restrict__ gx, int gxs,
-                                   int C, int B, int D, int H, int W)
+__global__ void up2_adjoint_kernel(const bf16* __restrict__ gy, int gys, bf16* __restrict__ gx, int gxs, int C, int B,
+                                   PadVol gf, PadVol gc)
 {
-    const int Do = D / 2, Ho = H / 2, Wo = W / 2;           // D, H, W: size of gy
-    const long long n = (long long)B * Do * Ho * Wo * C;
+    const long long n = (long long)B * gc.D * gc.H * gc.W * C;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int c = (int)(e % C);
         const long long v = e / C;
-        const int xo = (int)(v % Wo), yo = (int)((v / Wo) % Ho), zo = (int)((v / ((long long)Wo * Ho)) % Do);
-        const long long b = v / ((long long)Wo * Ho * Do);
+        const int xo = (int)(v % gc.W), yo = (int)((v / gc.W) % gc.H), zo = (int)((v / ((long long)gc.W * gc.H)) % gc.D);
+        const long long b = v / ((long long)gc.W * gc.H * gc.D);
         float s = 0.f;
         for (int q = 0; q < 8; ++q) {
-            const long long iv = ((b * D + 2 * zo + (q >> 2)) * H + 2 * yo + ((q >> 1) & 1)) * W + 2 * xo + (q & 1);
-            s += __bfloat162float(gy[iv * gys + gyoff + c]);
+            const long long iv = b * gf.Vp + pad_row(gf, 2 * zo + (q >> 2), 2 * yo + ((q >> 1) & 1), 2 * xo + (q & 1));
+            s += __bfloat162float(gy[iv * gys + c]);
         }
-        gx[v * gxs + c] = __float2bfloat16(s);
+        gx[(b * gc.Vp + pad_row(gc, zo, yo, xo)) * gxs + c] = __float2bfloat16(s);
     }
 }
 
-// network input: channel 0 = subject[b], channel 1 = atlas (shared), rest 0
+// network input (16 channels): 0 = subject[b], 1 = atlas (shared), rest 0
 __global__ void pack_input_kernel(const float* __restrict__ subj, const float* __restrict__ atlas, bf16* __restrict__ x,
-                                  int xs, long long V, int B)
+                                  PadVol g, int B)
 {
-    const long long n = (long long)B * V;
+    const long long V = (long long)g.D * g.H * g.W, n = (long long)B * V;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-        bf16* o = x + v * xs;
-        o[0] = __float2bfloat16(subj[v]);
-        o[1] = __float2bfloat16(atlas[v % V]);
-        for (int c = 2; c < xs; ++c) o[c] = __float2bfloat16(0.f);
+        const long long b = v / V, l = v - b * V;
+        const int xx = (int)(l % g.W), yy = (int)((l / g.W) % g.H), zz = (int)(l / ((long long)g.W * g.H));
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = make_uint4(0u, 0u, 0u, 0u);
+        reinterpret_cast<__nv_bfloat162*>(&lo)[0] = __floats2bfloat162_rn(subj[v], atlas[l]);
+        uint4* o = reinterpret_cast<uint4*>(x + (b * g.Vp + pad_row(g, zz, yy, xx)) * 16);
+        o[0] = lo;
+        o[1] = hi;
     }
 }
 
 // loss = mean over voxels and 3 channels of (pred - target)^2 (block partials),
-// pred and target planar [batch][3][V], n = batch * V voxels;
-// g (channels-last bf16, stride gs) = dloss/dpred, channels 3.. set to zero
-__global__ void velocity_loss_kernel(const float* __restrict__ pred, const float* __restrict__ target, long long n,
-                                     long long V, bf16* __restrict__ g, int gs, double* __restrict__ partials, float inv)
+// pred and target planar [batch][3][V]; g (padded channels-last bf16, stride
+// gs) = dloss/dpred, channels 3.. set to zero
+__global__ void velocity_loss_kernel(const float* __restrict__ pred, const float* __restrict__ target, int B, PadVol g,
+                                     bf16* __restrict__ gout, int gs, double* __restrict__ partials, float inv)
 {
     __shared__ double sh[32];
+    const long long V = (long long)g.D * g.H * g.W, n = (long long)B * V;
     float acc = 0.f;
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
         const long long b = v / V, l = v - b * V;
+        const int xx = (int)(l % g.W), yy = (int)((l / g.W) % g.H), zz = (int)(l / ((long long)g.W * g.H));
+        bf16* o = gout + (b * g.Vp + pad_row(g, zz, yy, xx)) * gs;
         for (int c = 0; c < 3; ++c) {
             const size_t e = ((size_t)b * 3 + c) * V + l;
             const float d = pred[e] - target[e];
             acc += d * d * inv;
-            g[v * gs + c] = __float2bfloat16(2.f * d * inv);
+            o[c] = __float2bfloat16(2.f * d * inv);
         }
-        for (int c = 3; c < gs; ++c) g[v * gs + c] = __float2bfloat16(0.f);
+        for (int c = 3; c < gs; ++c) o[c] = __float2bfloat16(0.f);
     }
     const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-// forward weights (bf16 [np][kp]) and the flipped, transposed weights of the
-// data gradient (bf16 [npd][kpd], k' = tap' * coutp + co, tap' = 26 - tap)
-__global__ void weight_prep_kernel(const float* __restrict__ w, int kp, int np, int cin, int cinp_real, int cout,
-                                   int coutp, bf16* __restrict__ wb, bf16* __restrict__ wd, int kpd, int npd)
-{
-    const long long n = (long long)np * kp;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        wb[e] = __float2bfloat16(w[e]);
-    const long long nd = (long long)npd * kpd;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nd; e += (long long)gridDim.x * blockDim.x) {
-        const int ci = (int)(e / kpd), kd = (int)(e % kpd);
-        const int tapd = kd / coutp, co = kd % coutp;
-        float val = 0.f;
-        if (tapd < 27 && co < cout && ci < cinp_real) val = w[(size_t)co * kp + (26 - tapd) * cin + ci];
-        wd[e] = __float2bfloat16(val);
-    }
 }
 
 // full-resolution velocity from the half-resolution one: trilinear
@@ -548,9 +629,9 @@ __global__ void downsample_image_kernel(const float* __restrict__ I, int D, int 
     }
 }
 
-int ew_grid(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
-
 }  // namespace
+
+static int ew_grid(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16)); }
 
 cudaError_t gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, cudaStream_t s)
 {
@@ -566,39 +647,71 @@ cudaError_t gemm_bf16(const void* A, const void* B, float* C, int M, int N, int 
     return cudaGetLastError();
 }
 
+
+PadVol make_pad(int D, int H, int W)
+{
+    PadVol g;
+    g.D = D;
+    g.H = H;
+    g.W = W;
+    g.Wp = W + 2;
+    g.Hp = H + 2;
+    g.P = (long long)g.Hp * g.Wp;
+    g.Vp = (long long)(D + 2) * g.P;
+    return g;
+}
+
+int conv_window_rows(int W) { return TC_M + 2 * (W + 2) + 2; }
+
+int conv_slot_bytes(int W, int np) { return (32 * conv_window_rows(W) + 288 * np + 127) / 128 * 128; }
+
+bool conv_fits(int W, int np) { return 2 * conv_slot_bytes(W, np) <= CONV_SMEM_MAX; }
+
 cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s)
 {
-    ConvArgs a;
+    WinArgs a;
     a.in = static_cast<const bf16*>(d.in);
     a.in_stride = d.in_stride;
-    a.cin = d.cin;
+    a.nchunk = d.cin / 16;
     a.wt = static_cast<const bf16*>(d.wt);
     a.bias = d.bias;
     a.out = static_cast<bf16*>(d.out);
     a.out_stride = d.out_stride;
-    a.out_off = d.out_off;
     a.cout = d.cout;
+    a.out_vec = (d.out_stride % 8 == 0) && ((reinterpret_cast<uintptr_t>(d.out) & 15) == 0);
     a.out_f32 = d.out_f32;
     a.gate = static_cast<const bf16*>(d.gate);
     a.gate_stride = d.gate_stride;
     a.act = d.act;
     a.slope = d.slope;
-    a.D = d.D;
-    a.H = d.H;
-    a.W = d.W;
-    a.nvox = (long long)d.batch * d.D * d.H * d.W;
-    a.kp = d.kp;
+    a.B = d.batch;
+    a.g = make_pad(d.D, d.H, d.W);
     a.np = d.np;
-    const size_t smem = 2 * ((size_t)CONV_SMEM_STAGE_A + (size_t)d.np * TC_KC * 2);
+    a.R = conv_window_rows(d.W);
+    a.slot_bytes = conv_slot_bytes(d.W, d.np);
+    a.ns = (3 * a.slot_bytes <= 200 * 1024) ? 3 : 2;
+    a.tiles_per_batch = ((long long)d.D * a.g.P + TC_M - 1) / TC_M;
+    if (!conv_fits(d.W, d.np)) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv3_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             2 * (CONV_SMEM_STAGE_A + 256 * TC_KC * 2));
+        cudaError_t e = cudaFuncSetAttribute(conv3_win_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             CONV_SMEM_MAX);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const long long blocks = (a.nvox + TC_M - 1) / TC_M;
-    conv3_fwd_kernel<<<(unsigned)blocks, 128, smem, s>>>(a);
+    const long long blocks = (long long)d.batch * a.tiles_per_batch;
+    conv3_win_kernel<<<(unsigned)blocks, 128, (size_t)a.ns * a.slot_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t packed_weight_elems(int conv_cin, int nrows) { return (size_t)(conv_cin / 16) * 54 * nrows * 8; }
+
+cudaError_t pack_weights(const float* w, int kp, int cin, int cout, int conv_cin, int nrows, int flip, void* out,
+                         cudaStream_t s)
+{
+    const long long n = (long long)packed_weight_elems(conv_cin, nrows);
+    pack_weights_kernel<<<ew_grid(n), 256, 0, s>>>(w, kp, cin, cout, conv_cin / 16, nrows, flip,
+                                                    static_cast<bf16*>(out));
     return cudaGetLastError();
 }
 
@@ -613,18 +726,17 @@ cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, 
     a.gz_stride = gz_stride;
     a.cout = cout;
     a.partial = partial;
-    a.D = D;
-    a.H = H;
-    a.W = W;
-    a.nvox = (long long)batch * D * H * W;
-    a.chunk = ((a.nvox + splits - 1) / splits + TC_KC - 1) / TC_KC * TC_KC;
+    a.g = make_pad(D, H, W);
+    a.nrows = (long long)batch * D * a.g.P;
+    a.rows_total = (long long)batch * a.g.Vp;
+    a.chunk = ((a.nrows + splits - 1) / splits + TC_KC - 1) / TC_KC * TC_KC;
     a.kp = kp;
     a.np = np;
-    const size_t smem = 2 * ((size_t)CONV_SMEM_STAGE_A + (size_t)np * TC_KC * 2);
+    const size_t smem = 2 * ((size_t)TC_M * TC_KC * 2 + (size_t)np * TC_KC * 2);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(conv3_wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             2 * (CONV_SMEM_STAGE_A + 128 * TC_KC * 2));
+                                             2 * (TC_M * TC_KC * 2 + 128 * TC_KC * 2));
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -649,56 +761,53 @@ cudaError_t bias_grad(const void* gz, int stride, long long nvox, int cout, floa
 
 cudaError_t pool2(const void* x, int xs, void* y, int ys, int C, int B, int D, int H, int W, cudaStream_t s)
 {
-    pool2_kernel<<<ew_grid((long long)B * (D / 2) * (H / 2) * (W / 2) * C), 256, 0, s>>>(
-        static_cast<const bf16*>(x), xs, static_cast<bf16*>(y), ys, C, B, D, H, W);
+    const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
+    pool2_kernel<<<ew_grid((long long)B * gc.D * gc.H * gc.W * C), 256, 0, s>>>(
+        static_cast<const bf16*>(x), xs, static_cast<bf16*>(y), ys, C, B, gf, gc);
     return cudaGetLastError();
 }
 
 cudaError_t pool2_adjoint(const void* gy, int gys, const void* x, int xs, void* gx, int gxs, int C, float slope, int B,
                           int D, int H, int W, cudaStream_t s)
 {
+    const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
     pool2_adjoint_kernel<<<ew_grid((long long)B * D * H * W * C), 256, 0, s>>>(
         static_cast<const bf16*>(gy), gys, static_cast<const bf16*>(x), xs, static_cast<bf16*>(gx), gxs, C, slope, B,
-        D, H, W);
+        gf, gc);
     return cudaGetLastError();
 }
 
-cudaError_t up2(const void* x, int xs, void* y, int ys, int yoff, int C, int B, int D, int H, int W, cudaStream_t s)
+cudaError_t up2(const void* x, int xs, void* y, int ys, int C, int B, int D, int H, int W, cudaStream_t s)
 {
+    const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
     up2_kernel<<<ew_grid((long long)B * D * H * W * C), 256, 0, s>>>(static_cast<const bf16*>(x), xs,
-                                                                      static_cast<bf16*>(y), ys, yoff, C, B, D, H, W);
+                                                                      static_cast<bf16*>(y), ys, C, B, gf, gc);
     return cudaGetLastError();
 }
 
-cudaError_t up2_adjoint(const void* gy, int gys, int gyoff, void* gx, int gxs, int C, int B, int D, int H, int W,
-                        cudaStream_t s)
+cudaError_t up2_adjoint(const void* gy, int gys, void* gx, int gxs, int C, int B, int D, int H, int W, cudaStream_t s)
 {
-    up2_adjoint_kernel<<<ew_grid((long long)B * (D / 2) * (H / 2) * (W / 2) * C), 256, 0, s>>>(
-        static_cast<const bf16*>(gy), gys, gyoff, static_cast<bf16*>(gx), gxs, C, B, D, H, W);
+    const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
+    up2_adjoint_kernel<<<ew_grid((long long)B * gc.D * gc.H * gc.W * C), 256, 0, s>>>(
+        static_cast<const bf16*>(gy), gys, static_cast<bf16*>(gx), gxs, C, B, gf, gc);
     return cudaGetLastError();
 }
 
-cudaError_t pack_input(const float* subj, const float* atlas, void* x, int xs, long long V, int B, cudaStream_t s)
+cudaError_t pack_input(const float* subj, const float* atlas, void* x, int B, int D, int H, int W, cudaStream_t s)
 {
-    pack_input_kernel<<<ew_grid((long long)B * V), 256, 0, s>>>(subj, atlas, static_cast<bf16*>(x), xs, V, B);
+    pack_input_kernel<<<ew_grid((long long)B * D * H * W), 256, 0, s>>>(subj, atlas, static_cast<bf16*>(x),
+                                                                        make_pad(D, H, W), B);
     return cudaGetLastError();
 }
 
 int velocity_loss_blocks(long long n) { return ew_grid(n); }
 
-cudaError_t velocity_loss(const float* pred, const float* target, long long n, long long V, void* g, int gs,
+cudaError_t velocity_loss(const float* pred, const float* target, int B, int D, int H, int W, void* g, int gs,
                           double* partials, cudaStream_t s)
 {
-    velocity_loss_kernel<<<ew_grid(n), 256, 0, s>>>(pred, target, n, V, static_cast<bf16*>(g), gs, partials,
-                                                    (float)(1.0 / (3.0 * (double)n)));
-    return cudaGetLastError();
-}
-
-cudaError_t weight_prep(const float* w, int kp, int np, int cin, int cin_real, int cout, int coutp, void* wb, void* wd,
-                        int kpd, int npd, cudaStream_t s)
-{
-    weight_prep_kernel<<<ew_grid(std::max((long long)np * kp, (long long)npd * kpd)), 256, 0, s>>>(
-        w, kp, np, cin, cin_real, cout, coutp, static_cast<bf16*>(wb), static_cast<bf16*>(wd), kpd, npd);
+    const long long n = (long long)B * D * H * W;
+    velocity_loss_kernel<<<ew_grid(n), 256, 0, s>>>(pred, target, B, make_pad(D, H, W), static_cast<bf16*>(g), gs,
+                                                    partials, (float)(1.0 / (3.0 * (double)n)));
     return cudaGetLastError();
 }
 

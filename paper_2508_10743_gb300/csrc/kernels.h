@@ -89,42 +89,60 @@ cudaError_t combine_grad(const float* gshared, const float* gsubj, int B, float 
 
 // ---- tensor-core kernels (k_unet.cu) ----
 cudaError_t gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, cudaStream_t s);
-// one 3x3x3 'same' convolution (see darc_conv3d in darc.h for the fields)
+// a D x H x W volume stored with a one-voxel zero border: padded row of
+// (z, y, x) = ((z + 1) Hp + y + 1) Wp + x + 1, Vp rows per volume
+struct PadVol {
+    int D, H, W, Wp, Hp;
+    long long P, Vp;            // rows per padded plane, per padded volume
+};
+PadVol make_pad(int D, int H, int W);
+// one 3x3x3 'same' convolution over padded channels-last bf16 volumes (see
+// darc_conv3d in darc.h for the fields)
 struct ConvDesc {
-    const void* in;               // bf16 channels-last [batch][D][H][W][in_stride]
+    const void* in;               // [batch][D+2][H+2][W+2][in_stride], channels [0, cin), cin % 16 == 0
     int in_stride, cin;
-    const void* wt;               // bf16 [np][kp]
+    const void* wt;               // packed by pack_weights (cin / 16 chunks, np rows)
     const float* bias;
-    void* out;                    // bf16 channels-last, channels [out_off, out_off + cout)
-    int out_stride, out_off, cout;
+    void* out;                    // same geometry, channels [0, cout) at out
+    int out_stride, cout;
     float* out_f32;               // planar fp32 [batch][cout][D * H * W] (replaces out)
-    const void* gate;             // bf16 channels-last: multiply by the leaky-ReLU slope where gate <= 0
+    const void* gate;             // same geometry: multiply by the leaky-ReLU slope where gate <= 0
     int gate_stride;
     int act;
     float slope;
-    int batch, D, H, W, kp, np;
+    int batch, D, H, W, np;
 };
 cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s);
-// dw [np][kp] fp32 = sum_v gz[v][co] im2col(in)[v][k]; partial: splits x kp x np floats
+// whether two pipeline stages of a conv of this width and np fit in shared memory
+bool conv_fits(int W, int np);
+// bf16 elements of packed weights for a convolution with conv_cin input
+// channels (multiple of 16) and nrows output rows (np)
+size_t packed_weight_elems(int conv_cin, int nrows);
+// pack fp32 masters w[co][k] (k = tap cin + ci, kp per row) for the forward
+// (flip 0: conv_cin = cin, nrows = np) or the data gradient (flip 1:
+// conv_cin = cout rounded up to 16, nrows = cin)
+cudaError_t pack_weights(const float* w, int kp, int cin, int cout, int conv_cin, int nrows, int flip, void* out,
+                         cudaStream_t s);
+// dw [np][kp] fp32 = sum_q gz[q][co] in[q + off(tap)][ci] over the padded
+// rows of the interior planes; partial: splits x kp x np floats
 cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout, float* partial,
                         int splits, float* dw, int batch, int D, int H, int W, int kp, int np, cudaStream_t s);
-// db[c] = sum over voxels of gz[v][c]; (cout + 7) / 8 must divide 256; work:
+// db[c] = sum over rows of gz[v][c]; (cout + 7) / 8 must divide 256; work:
 // bias_grad_work_floats(cout) floats
 int bias_grad_work_floats(int cout);
 cudaError_t bias_grad(const void* gz, int stride, long long nvox, int cout, float* db, float* work, cudaStream_t s);
+// 2x pooling / nearest upsampling between padded volumes; D, H, W: the fine grid
 cudaError_t pool2(const void* x, int xs, void* y, int ys, int C, int B, int D, int H, int W, cudaStream_t s);
 cudaError_t pool2_adjoint(const void* gy, int gys, const void* x, int xs, void* gx, int gxs, int C, float slope, int B,
                           int D, int H, int W, cudaStream_t s);
-cudaError_t up2(const void* x, int xs, void* y, int ys, int yoff, int C, int B, int D, int H, int W, cudaStream_t s);
-cudaError_t up2_adjoint(const void* gy, int gys, int gyoff, void* gx, int gxs, int C, int B, int D, int H, int W,
-                        cudaStream_t s);
-cudaError_t pack_input(const float* subj, const float* atlas, void* x, int xs, long long V, int B, cudaStream_t s);
+cudaError_t up2(const void* x, int xs, void* y, int ys, int C, int B, int D, int H, int W, cudaStream_t s);
+cudaError_t up2_adjoint(const void* gy, int gys, void* gx, int gxs, int C, int B, int D, int H, int W, cudaStream_t s);
+// 16-channel padded network input from planar fp32 subjects [B][V] and atlas [V]
+cudaError_t pack_input(const float* subj, const float* atlas, void* x, int B, int D, int H, int W, cudaStream_t s);
 int velocity_loss_blocks(long long n);
-// pred, target planar [batch][3][V], n = batch * V
-cudaError_t velocity_loss(const float* pred, const float* target, long long n, long long V, void* g, int gs,
+// pred, target planar [batch][3][V]; g padded channels-last, stride gs
+cudaError_t velocity_loss(const float* pred, const float* target, int B, int D, int H, int W, void* g, int gs,
                           double* partials, cudaStream_t s);
-cudaError_t weight_prep(const float* w, int kp, int np, int cin, int cin_real, int cout, int coutp, void* wb, void* wd,
-                        int kpd, int npd, cudaStream_t s);
 cudaError_t upsample_velocity(const float* vh, int Dh, int Hh, int Wh, float* v, int D, int H, int W, int B,
                               cudaStream_t s);
 cudaError_t downsample_image(const float* I, int D, int H, int W, float* Ih, int B, cudaStream_t s);

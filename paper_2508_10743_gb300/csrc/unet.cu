@@ -4,9 +4,10 @@
 // 3-channel velocity field, trained on velocities the plain method produced.
 // This is an addition to the method; the paper has no counterpart.
 //
-// Layout: activations channels-last bf16 [batch][D][H][W][stride]; a skip
-// connection is a channel slice of the decoder's concatenation buffer, so
-// concatenation costs nothing.  Down-sampling: 2x average pooling;
+// Layout: activations channels-last bf16 with a one-voxel zero border,
+// [batch][D+2][H+2][W+2][stride] (borders are never written, so they stay
+// zero); a skip connection is a channel slice of the decoder's concatenation
+// buffer, so concatenation costs nothing.  Down-sampling: 2x average pooling;
 // up-sampling: nearest 2x.  Every conv is 3x3x3 'same' + bias + leaky ReLU
 // (slope 0.2), except the 3-channel head.
 #include "../../include/darc.h"
@@ -28,10 +29,10 @@ constexpr float kSlope = 0.2f;
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Layer {
-    int cin, cinp, cout, coutp8, kp, np, kpd, npd, level, act;
+    int cin, cinp, cout, kp, np, level, act;        // cinp, np: rounded up to 16; kp = 27 cinp
     float *w = nullptr, *b = nullptr, *mw = nullptr, *sw = nullptr, *mb = nullptr, *sb = nullptr;
     float *dw = nullptr, *db = nullptr;
-    void *wb = nullptr, *wd = nullptr;     // bf16 forward / flipped weights
+    void *wb = nullptr, *wd = nullptr;     // bf16 packed forward / data-gradient weights
 };
 
 struct Buf {
@@ -85,10 +86,10 @@ int ualloc(darc_unet* u, T** p, size_t n)
     return DARC_OK;
 }
 
-int balloc(darc_unet* u, Buf& b, long long vox, int stride)
+int balloc(darc_unet* u, Buf& b, long long rows, int stride)
 {
     b.stride = stride;
-    return ualloc(u, reinterpret_cast<uint16_t**>(&b.p), (size_t)vox * stride);
+    return ualloc(u, reinterpret_cast<uint16_t**>(&b.p), (size_t)rows * stride);
 }
 
 void* ch(const Buf& b, int off) { return static_cast<uint16_t*>(b.p) + off; }
@@ -116,7 +117,8 @@ const int kSpec[15][4] = {
 
 int prep_weights(darc_unet* u, Layer& l, cudaStream_t s)
 {
-    UCK(weight_prep(l.w, l.kp, l.np, l.cinp, l.cinp, l.cout, l.coutp8, l.wb, l.wd, l.kpd, l.npd, s));
+    UCK(pack_weights(l.w, l.kp, l.cinp, l.cout, l.cinp, l.np, 0, l.wb, s));
+    UCK(pack_weights(l.w, l.kp, l.cinp, l.cout, l.np, l.cinp, 1, l.wd, s));
     return DARC_OK;
 }
 
@@ -132,7 +134,6 @@ int conv(darc_unet* u, const Layer& l, const Buf& in, int in_off, const Buf& out
     c.bias = l.b;
     c.out = out_f32 ? nullptr : ch(out, out_off);
     c.out_stride = out.stride;
-    c.out_off = 0;
     c.cout = l.cout;
     c.out_f32 = out_f32;
     c.act = l.act;
@@ -141,7 +142,6 @@ int conv(darc_unet* u, const Layer& l, const Buf& in, int in_off, const Buf& out
     c.D = d[0];
     c.H = d[1];
     c.W = d[2];
-    c.kp = l.kp;
     c.np = l.np;
     UCK(conv3_forward(c, s));
     return DARC_OK;
@@ -156,7 +156,7 @@ int dgrad(darc_unet* u, const Layer& l, const Buf& gz, int gz_off, const Buf& gi
     ConvDesc c{};
     c.in = ch(gz, gz_off);
     c.in_stride = gz.stride;
-    c.cin = l.coutp8;
+    c.cin = l.np;
     c.wt = l.wd;
     c.bias = nullptr;
     c.out = ch(gin, gin_off);
@@ -170,8 +170,7 @@ int dgrad(darc_unet* u, const Layer& l, const Buf& gz, int gz_off, const Buf& gi
     c.D = d[0];
     c.H = d[1];
     c.W = d[2];
-    c.kp = l.kpd;
-    c.np = l.npd;
+    c.np = l.cinp;
     UCK(conv3_forward(c, s));
     return DARC_OK;
 }
@@ -179,25 +178,26 @@ int dgrad(darc_unet* u, const Layer& l, const Buf& gz, int gz_off, const Buf& gi
 int wgrad(darc_unet* u, Layer& l, const Buf& in, int in_off, const Buf& gz, int gz_off, int B, cudaStream_t s)
 {
     const int* d = u->dims[l.level];
-    const long long nvox = (long long)B * d[0] * d[1] * d[2];
+    const PadVol g = make_pad(d[0], d[1], d[2]);
+    const long long nrows = (long long)B * d[0] * g.P;
     const int tiles = (l.kp + 127) / 128;
-    int splits = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(608 / tiles, nvox / 1024), 256));
+    int splits = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(608 / tiles, nrows / 1024), 256));
     while ((size_t)splits * l.kp * l.np > u->partial_floats && splits > 1) splits /= 2;
-    UCK(conv3_wgrad(ch(in, in_off), in.stride, l.cinp, ch(gz, gz_off), gz.stride, l.coutp8, u->partial, splits, l.dw,
+    UCK(conv3_wgrad(ch(in, in_off), in.stride, l.cinp, ch(gz, gz_off), gz.stride, l.np, u->partial, splits, l.dw,
                     B, d[0], d[1], d[2], l.kp, l.np, s));
-    UCK(bias_grad(ch(gz, gz_off), gz.stride, nvox, l.cout, l.db, u->partial, s));   // partials are free again
+    // partials are free again once the split reduction has run (same stream)
+    UCK(bias_grad(ch(gz, gz_off), gz.stride, (long long)B * g.Vp, l.cout, l.db, u->partial, s));
     return DARC_OK;
 }
 
 int forward(darc_unet* u, const float* subj, const float* atlas, int B, cudaStream_t s)
 {
     auto& L = u->L;
-    const long long V0 = (long long)u->dims[0][0] * u->dims[0][1] * u->dims[0][2];
     const int* d0 = u->dims[0];
     const int* d1 = u->dims[1];
     const int* d2 = u->dims[2];
     int rc;
-    UCK(pack_input(subj, atlas, u->x0.p, u->x0.stride, V0, B, s));
+    UCK(pack_input(subj, atlas, u->x0.p, B, d0[0], d0[1], d0[2], s));
 #define RUN(x) do { rc = (x); if (rc) return rc; } while (0)
     RUN(conv(u, L[0], u->x0, 0, u->a0, 0, B, s));
     RUN(conv(u, L[1], u->a0, 0, u->cat0, 32, B, s));
@@ -210,13 +210,13 @@ int forward(darc_unet* u, const float* subj, const float* atlas, int B, cudaStre
     UCK(pool2(ch(u->cat2, 128), 192, u->p2.p, 64, 64, B, d2[0], d2[1], d2[2], s));
     RUN(conv(u, L[6], u->p2, 0, u->a3, 0, B, s));
     RUN(conv(u, L[7], u->a3, 0, u->b3, 0, B, s));
-    UCK(up2(u->b3.p, 128, u->cat2.p, 192, 0, 128, B, d2[0], d2[1], d2[2], s));
+    UCK(up2(u->b3.p, 128, u->cat2.p, 192, 128, B, d2[0], d2[1], d2[2], s));
     RUN(conv(u, L[8], u->cat2, 0, u->d2a, 0, B, s));
     RUN(conv(u, L[9], u->d2a, 0, u->d2b, 0, B, s));
-    UCK(up2(u->d2b.p, 64, u->cat1.p, 96, 0, 64, B, d1[0], d1[1], d1[2], s));
+    UCK(up2(u->d2b.p, 64, u->cat1.p, 96, 64, B, d1[0], d1[1], d1[2], s));
     RUN(conv(u, L[10], u->cat1, 0, u->d1a, 0, B, s));
     RUN(conv(u, L[11], u->d1a, 0, u->d1b, 0, B, s));
-    UCK(up2(u->d1b.p, 32, u->cat0.p, 48, 0, 32, B, d0[0], d0[1], d0[2], s));
+    UCK(up2(u->d1b.p, 32, u->cat0.p, 48, 32, B, d0[0], d0[1], d0[2], s));
     RUN(conv(u, L[12], u->cat0, 0, u->d0a, 0, B, s));
     RUN(conv(u, L[13], u->d0a, 0, u->d0b, 0, B, s));
     RUN(conv(u, L[14], u->d0b, 0, u->d0b, 0, B, s, u->pred));
@@ -239,17 +239,17 @@ int backward(darc_unet* u, int B, cudaStream_t s)
     RUN(dgrad(u, L[13], u->gd0b, 0, u->gd0a, 0, &u->d0a, 0, B, s));
     RUN(wgrad(u, L[12], u->cat0, 0, u->gd0a, 0, B, s));
     RUN(dgrad(u, L[12], u->gd0a, 0, u->gcat0, 0, &u->cat0, 0, B, s));
-    UCK(up2_adjoint(u->gcat0.p, 48, 0, u->gd1b.p, 32, 32, B, d0[0], d0[1], d0[2], s));
+    UCK(up2_adjoint(u->gcat0.p, 48, u->gd1b.p, 32, 32, B, d0[0], d0[1], d0[2], s));
     RUN(wgrad(u, L[11], u->d1a, 0, u->gd1b, 0, B, s));
     RUN(dgrad(u, L[11], u->gd1b, 0, u->gd1a, 0, &u->d1a, 0, B, s));
     RUN(wgrad(u, L[10], u->cat1, 0, u->gd1a, 0, B, s));
     RUN(dgrad(u, L[10], u->gd1a, 0, u->gcat1, 0, &u->cat1, 0, B, s));
-    UCK(up2_adjoint(u->gcat1.p, 96, 0, u->gd2b.p, 64, 64, B, d1[0], d1[1], d1[2], s));
+    UCK(up2_adjoint(u->gcat1.p, 96, u->gd2b.p, 64, 64, B, d1[0], d1[1], d1[2], s));
     RUN(wgrad(u, L[9], u->d2a, 0, u->gd2b, 0, B, s));
     RUN(dgrad(u, L[9], u->gd2b, 0, u->gd2a, 0, &u->d2a, 0, B, s));
     RUN(wgrad(u, L[8], u->cat2, 0, u->gd2a, 0, B, s));
     RUN(dgrad(u, L[8], u->gd2a, 0, u->gcat2, 0, &u->cat2, 0, B, s));
-    UCK(up2_adjoint(u->gcat2.p, 192, 0, u->gb3.p, 128, 128, B, d2[0], d2[1], d2[2], s));
+    UCK(up2_adjoint(u->gcat2.p, 192, u->gb3.p, 128, 128, B, d2[0], d2[1], d2[2], s));
     RUN(wgrad(u, L[7], u->a3, 0, u->gb3, 0, B, s));
     RUN(dgrad(u, L[7], u->gb3, 0, u->ga3, 0, &u->a3, 0, B, s));
     RUN(wgrad(u, L[6], u->p2, 0, u->ga3, 0, B, s));
@@ -276,6 +276,7 @@ int check_unet_dims(int D, int H, int W)
 {
     if (D < 16 || H < 16 || W < 16 || D % 8 || H % 8 || W % 8)
         return ufail(DARC_ERR_SHAPE, "U-Net volume must be >= 16 and a multiple of 8 along every axis");
+    if (!conv_fits(W, 256)) return ufail(DARC_ERR_SHAPE, "U-Net volume too wide for the convolution's window");
     return DARC_OK;
 }
 
@@ -307,21 +308,18 @@ int darc_unet_create(darc_unet** out, int D, int H, int W, int max_batch, unsign
     for (int i = 0; i < 15; ++i) {
         Layer l;
         l.cin = kSpec[i][0];
-        l.cinp = round_up(l.cin, 8);
+        l.cinp = round_up(l.cin, 16);
         l.cout = kSpec[i][1];
-        l.coutp8 = round_up(l.cout, 8);
         l.level = kSpec[i][2];
         l.act = kSpec[i][3];
-        l.kp = round_up(27 * l.cinp, 16);
+        l.kp = 27 * l.cinp;
         l.np = round_up(l.cout, 16);
-        l.kpd = round_up(27 * l.coutp8, 16);
-        l.npd = round_up(l.cinp, 16);
         const size_t nw = (size_t)l.np * l.kp;
         if ((rc = ualloc(u, &l.w, nw)) || (rc = ualloc(u, &l.mw, nw)) || (rc = ualloc(u, &l.sw, nw)) ||
             (rc = ualloc(u, &l.dw, nw)) || (rc = ualloc(u, &l.b, l.cout)) || (rc = ualloc(u, &l.mb, l.cout)) ||
             (rc = ualloc(u, &l.sb, l.cout)) || (rc = ualloc(u, &l.db, l.cout)) ||
-            (rc = ualloc(u, reinterpret_cast<uint16_t**>(&l.wb), nw)) ||
-            (rc = ualloc(u, reinterpret_cast<uint16_t**>(&l.wd), (size_t)l.npd * l.kpd)))
+            (rc = ualloc(u, reinterpret_cast<uint16_t**>(&l.wb), packed_weight_elems(l.cinp, l.np))) ||
+            (rc = ualloc(u, reinterpret_cast<uint16_t**>(&l.wd), packed_weight_elems(l.np, l.cinp))))
             return fail_out(rc);
         // He-normal for leaky ReLU; the head starts small so the first
         // proposals stay close to zero velocity
@@ -335,16 +333,18 @@ int darc_unet_create(darc_unet** out, int D, int H, int W, int max_batch, unsign
         u->L.push_back(l);
     }
     const int B = max_batch;
-    const long long V0 = (long long)D * H * W, V1 = V0 / 8, V2 = V1 / 8, V3 = V2 / 8;
+    const long long V0 = (long long)D * H * W;
+    const long long P0 = make_pad(D, H, W).Vp, P1 = make_pad(D / 2, H / 2, W / 2).Vp,
+                    P2 = make_pad(D / 4, H / 4, W / 4).Vp, P3 = make_pad(D / 8, H / 8, W / 8).Vp;
     struct { Buf* b; long long v; int c; } bufs[] = {
-        {&u->x0, V0, 8}, {&u->a0, V0, 16}, {&u->cat0, V0, 48}, {&u->d0a, V0, 16}, {&u->d0b, V0, 16},
-        {&u->gh, V0, 16}, {&u->ga0, V0, 16}, {&u->gcat0, V0, 48}, {&u->gd0a, V0, 16}, {&u->gd0b, V0, 16},
-        {&u->p0, V1, 16}, {&u->a1, V1, 32}, {&u->cat1, V1, 96}, {&u->d1a, V1, 32}, {&u->d1b, V1, 32},
-        {&u->gp0, V1, 16}, {&u->ga1, V1, 32}, {&u->gcat1, V1, 96}, {&u->gd1a, V1, 32}, {&u->gd1b, V1, 32},
-        {&u->p1, V2, 32}, {&u->a2, V2, 64}, {&u->cat2, V2, 192}, {&u->d2a, V2, 64}, {&u->d2b, V2, 64},
-        {&u->gp1, V2, 32}, {&u->ga2, V2, 64}, {&u->gcat2, V2, 192}, {&u->gd2a, V2, 64}, {&u->gd2b, V2, 64},
-        {&u->p2, V3, 64}, {&u->a3, V3, 128}, {&u->b3, V3, 128}, {&u->gp2, V3, 64}, {&u->ga3, V3, 128},
-        {&u->gb3, V3, 128},
+        {&u->x0, P0, 16}, {&u->a0, P0, 16}, {&u->cat0, P0, 48}, {&u->d0a, P0, 16}, {&u->d0b, P0, 16},
+        {&u->gh, P0, 16}, {&u->ga0, P0, 16}, {&u->gcat0, P0, 48}, {&u->gd0a, P0, 16}, {&u->gd0b, P0, 16},
+        {&u->p0, P1, 16}, {&u->a1, P1, 32}, {&u->cat1, P1, 96}, {&u->d1a, P1, 32}, {&u->d1b, P1, 32},
+        {&u->gp0, P1, 16}, {&u->ga1, P1, 32}, {&u->gcat1, P1, 96}, {&u->gd1a, P1, 32}, {&u->gd1b, P1, 32},
+        {&u->p1, P2, 32}, {&u->a2, P2, 64}, {&u->cat2, P2, 192}, {&u->d2a, P2, 64}, {&u->d2b, P2, 64},
+        {&u->gp1, P2, 32}, {&u->ga2, P2, 64}, {&u->gcat2, P2, 192}, {&u->gd2a, P2, 64}, {&u->gd2b, P2, 64},
+        {&u->p2, P3, 64}, {&u->a3, P3, 128}, {&u->b3, P3, 128}, {&u->gp2, P3, 64}, {&u->ga3, P3, 128},
+        {&u->gb3, P3, 128},
     };
     for (auto& e : bufs)
         if ((rc = balloc(u, *e.b, e.v * B, e.c))) return fail_out(rc);
@@ -387,7 +387,7 @@ int darc_unet_train_step(darc_unet* u, const float* subj_dev, const float* atlas
     int rc = forward(u, subj_dev, atlas_dev, B, s);
     if (rc) return rc;
     const long long n = (long long)B * u->D * u->H * u->W;
-    UCK(velocity_loss(u->pred, target_dev, n, (long long)u->D * u->H * u->W, u->gh.p, 16, u->lpart, s));
+    UCK(velocity_loss(u->pred, target_dev, B, u->D, u->H, u->W, u->gh.p, 16, u->lpart, s));
     UCK(reduce_partials(u->lpart, velocity_loss_blocks(n), 1, 1.0, u->loss_dev, 1, 1, s));
     rc = backward(u, B, s);
     if (rc) return rc;
@@ -416,7 +416,7 @@ int darc_unet_gradients(darc_unet* u, const float* subj_dev, const float* atlas_
     int rc = forward(u, subj_dev, atlas_dev, B, s);
     if (rc) return rc;
     const long long n = (long long)B * u->D * u->H * u->W;
-    UCK(velocity_loss(u->pred, target_dev, n, (long long)u->D * u->H * u->W, u->gh.p, 16, u->lpart, s));
+    UCK(velocity_loss(u->pred, target_dev, B, u->D, u->H, u->W, u->gh.p, 16, u->lpart, s));
     UCK(reduce_partials(u->lpart, velocity_loss_blocks(n), 1, 1.0, u->loss_dev, 1, 1, s));
     rc = backward(u, B, s);
     if (rc) return rc;
@@ -521,15 +521,34 @@ int darc_upsample_velocity(const float* vh_dev, int B, int Dh, int Hh, int Wh, f
     return DARC_OK;
 }
 
+size_t darc_conv3d_packed_bytes(int conv_cin, int nrows)
+{
+    if (conv_cin < 16 || conv_cin % 16 || nrows < 16 || nrows % 16) return 0;
+    return packed_weight_elems(conv_cin, nrows) * 2;
+}
+
+int darc_conv3d_pack_weights(const float* w_dev, int kp, int cin, int cout, int flip, void* packed_dev, void* stream)
+{
+    if (!w_dev || !packed_dev) return ufail(DARC_ERR_ARG, "null argument");
+    if (cin < 16 || cin % 16 || cout < 1 || cout > 256 || kp < 27 * cin || (flip != 0 && flip != 1))
+        return ufail(DARC_ERR_SHAPE, "conv3d_pack_weights: cin % 16 == 0, 1 <= cout <= 256, kp >= 27 cin");
+    if ((uintptr_t)packed_dev & 15) return ufail(DARC_ERR_ARG, "packed weights must be 16-byte aligned");
+    const int coutp = round_up(cout, 16);
+    UCK(pack_weights(w_dev, kp, cin, cout, flip ? coutp : cin, flip ? cin : coutp, flip, packed_dev,
+                     (cudaStream_t)stream));
+    return DARC_OK;
+}
+
 int darc_conv3d(const void* in_dev, int in_stride, int cin, const void* wt_dev, const float* bias_dev, void* out_dev,
                 int out_stride, int cout, float* out_f32_dev, const void* gate_dev, int gate_stride, int act,
-                float slope, int batch, int D, int H, int W, int kp, int np, void* stream)
+                float slope, int batch, int D, int H, int W, int np, void* stream)
 {
     if (!in_dev || !wt_dev || (!out_dev && !out_f32_dev)) return ufail(DARC_ERR_ARG, "null argument");
-    if (cin < 8 || cin % 8 || in_stride < cin || in_stride % 8 || kp < 27 * cin || kp % 16 || np < 16 || np > 256 ||
-        np % 16 || cout < 1 || cout > np || (!out_f32_dev && out_stride < cout) || batch < 1 || D < 1 || H < 1 || W < 1 ||
+    if (cin < 16 || cin % 16 || in_stride < cin || in_stride % 8 || np < 16 || np > 256 || np % 16 || cout < 1 ||
+        cout > np || (!out_f32_dev && out_stride < cout) || batch < 1 || D < 1 || H < 1 || W < 1 ||
         (gate_dev && gate_stride < cout))
-        return ufail(DARC_ERR_SHAPE, "conv3d: cin % 8 == 0, kp >= 27 cin with kp % 16 == 0, np % 16 == 0 <= 256");
+        return ufail(DARC_ERR_SHAPE, "conv3d: cin % 16 == 0, in_stride % 8 == 0, np % 16 == 0 <= 256, cout <= np");
+    if (!conv_fits(W, np)) return ufail(DARC_ERR_SHAPE, "conv3d: W too large for the shared-memory window");
     if (((uintptr_t)in_dev & 15) || ((uintptr_t)wt_dev & 15)) return ufail(DARC_ERR_ARG, "operands must be 16-byte aligned");
     ConvDesc c{};
     c.in = in_dev;
@@ -549,23 +568,25 @@ int darc_conv3d(const void* in_dev, int in_stride, int cin, const void* wt_dev, 
     c.D = D;
     c.H = H;
     c.W = W;
-    c.kp = kp;
     c.np = np;
     UCK(conv3_forward(c, (cudaStream_t)stream));
     return DARC_OK;
 }
 
 int darc_conv3d_wgrad(const void* in_dev, int in_stride, int cin, const void* gz_dev, int gz_stride, int cout,
-                      float* dw_dev, float* db_dev, int batch, int D, int H, int W, int kp, int np, void* work_dev,
+                      float* dw_dev, float* db_dev, int batch, int D, int H, int W, int np, void* work_dev,
                       size_t work_bytes, void* stream)
 {
     if (!in_dev || !gz_dev || !dw_dev || !work_dev) return ufail(DARC_ERR_ARG, "null argument");
-    if (cin < 8 || cin % 8 || in_stride % 8 || cout % 8 || gz_stride % 8 || kp < 27 * cin || kp % 16 || np % 16 ||
-        np < 16 || np > 128 || cout > np)
-        return ufail(DARC_ERR_SHAPE, "conv3d_wgrad: channel counts and strides must be multiples of 8");
+    if (cin < 16 || cin % 16 || in_stride % 8 || cout % 8 || gz_stride % 8 || gz_stride < cout || np % 16 ||
+        np < 16 || np > 128 || cout > np || batch < 1 || D < 1 || H < 1 || W < 1)
+        return ufail(DARC_ERR_SHAPE, "conv3d_wgrad: cin % 16 == 0, cout and strides multiples of 8, np <= 128");
     if (db_dev && 256 % (cout / 8)) return ufail(DARC_ERR_SHAPE, "conv3d_wgrad: cout / 8 must divide 256");
-    const long long nvox = (long long)batch * D * H * W;
-    int splits = (int)std::max<long long>(1, std::min<long long>(256, nvox / 1024));
+    if (((uintptr_t)in_dev & 15) || ((uintptr_t)gz_dev & 15)) return ufail(DARC_ERR_ARG, "operands must be 16-byte aligned");
+    const int kp = 27 * cin;
+    const PadVol g = make_pad(D, H, W);
+    const long long nrows = (long long)batch * D * g.P;
+    int splits = (int)std::max<long long>(1, std::min<long long>(256, nrows / 1024));
     while (splits > 1 && (size_t)splits * kp * np * sizeof(float) > work_bytes) splits /= 2;
     if ((size_t)splits * kp * np * sizeof(float) > work_bytes ||
         (db_dev && (size_t)bias_grad_work_floats(cout) * sizeof(float) > work_bytes))
@@ -573,7 +594,8 @@ int darc_conv3d_wgrad(const void* in_dev, int in_stride, int cin, const void* gz
     UCK(conv3_wgrad(in_dev, in_stride, cin, gz_dev, gz_stride, cout, (float*)work_dev, splits, dw_dev, batch, D, H, W,
                     kp, np, (cudaStream_t)stream));
     // the bias partials reuse the workspace once the split-K reduction has consumed it (same stream)
-    if (db_dev) UCK(bias_grad(gz_dev, gz_stride, nvox, cout, db_dev, (float*)work_dev, (cudaStream_t)stream));
+    if (db_dev)
+        UCK(bias_grad(gz_dev, gz_stride, (long long)batch * g.Vp, cout, db_dev, (float*)work_dev, (cudaStream_t)stream));
     return DARC_OK;
 }
 

@@ -103,9 +103,10 @@ _SIGS = {
     "darc_launch_count": (ctypes.c_longlong, [_vp]),
     "darc_exp_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
     "darc_gemm_bf16": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
-    "darc_conv3d": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _i, _vp, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _i,
-                         _vp]),
-    "darc_conv3d_wgrad": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp]),
+    "darc_conv3d": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _i, _vp, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _vp]),
+    "darc_conv3d_packed_bytes": (_sz, [_i, _i]),
+    "darc_conv3d_pack_weights": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "darc_conv3d_wgrad": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _sz, _vp]),
     "darc_resample_half": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
     "darc_upsample_velocity": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
     "darc_unet_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, ctypes.c_ulonglong]),
@@ -421,18 +422,45 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor) -> torch.Tensor:
     return C
 
 
-def conv3d(x: torch.Tensor, cin: int, wt: torch.Tensor, cout: int, bias: Optional[torch.Tensor] = None,
+def _r16(x: int) -> int:
+    return (x + 15) // 16 * 16
+
+
+def pad_volume(x: torch.Tensor) -> torch.Tensor:
+    """[B, D, H, W, C] -> [B, D+2, H+2, W+2, C] with a zero border (the
+    layout of darc_conv3d's volumes)."""
+    B, D, H, W, C = x.shape
+    out = torch.zeros((B, D + 2, H + 2, W + 2, C), dtype=x.dtype, device=x.device)
+    out[:, 1:-1, 1:-1, 1:-1] = x
+    return out
+
+
+def conv3d_pack_weights(w: torch.Tensor, cin: int, cout: int, flip: bool = False) -> torch.Tensor:
+    """Packs fp32 weights w [>= cout, kp] (k = tap * cin + ci) for conv3d:
+    the layer (flip False) or its data gradient (flip True)."""
+    _need(w, "w")
+    conv_cin, nrows = (_r16(cout), cin) if flip else (cin, _r16(cout))
+    nbytes = int(lib().darc_conv3d_packed_bytes(conv_cin, nrows))
+    if nbytes == 0:
+        raise ValueError("cin must be a multiple of 16")
+    out = torch.empty(nbytes // 2, dtype=torch.bfloat16, device=w.device)
+    _check(lib().darc_conv3d_pack_weights(_ptr(w), int(w.shape[1]), cin, cout, int(flip), _ptr(out), _stream()))
+    return out
+
+
+def conv3d(x: torch.Tensor, cin: int, wt: torch.Tensor, cout: int, np_: int, bias: Optional[torch.Tensor] = None,
            act: bool = False, slope: float = 0.2, gate: Optional[torch.Tensor] = None,
            f32_out: bool = False) -> torch.Tensor:
     """3x3x3 'same' convolution on the tensor cores (darc_conv3d).
 
-    x: bf16 channels-last [B, D, H, W, S] (channels [0, cin) read); wt: bf16
-    [np, kp], k = tap * cin + ci.  Returns bf16 [B, D, H, W, cout] or, with
-    f32_out, fp32 planar [B, cout, D, H, W]."""
+    x: bf16 channels-last with a zero border [B, D+2, H+2, W+2, S] (channels
+    [0, cin) read); wt: packed by conv3d_pack_weights.  Returns bf16
+    [B, D+2, H+2, W+2, cout] (zero border) or, with f32_out, fp32 planar
+    [B, cout, D, H, W]."""
     _need(x, "x", torch.bfloat16)
     _need(wt, "wt", torch.bfloat16)
-    B, D, H, W, S = (int(d) for d in x.shape)
-    np_, kp = (int(d) for d in wt.shape)
+    B, Dp, Hp, Wp, S = (int(d) for d in x.shape)
+    D, H, W = Dp - 2, Hp - 2, Wp - 2
     if bias is not None:
         _need(bias, "bias")
     gs = 0
@@ -442,26 +470,28 @@ def conv3d(x: torch.Tensor, cin: int, wt: torch.Tensor, cout: int, bias: Optiona
     if f32_out:
         out = torch.empty((B, cout, D, H, W), dtype=torch.float32, device=x.device)
         _check(lib().darc_conv3d(_ptr(x), S, cin, _ptr(wt), _ptr(bias), None, cout, cout, _ptr(out), _ptr(gate),
-                                 gs, int(act), slope, B, D, H, W, kp, np_, _stream()))
+                                 gs, int(act), slope, B, D, H, W, np_, _stream()))
     else:
-        out = torch.empty((B, D, H, W, cout), dtype=torch.bfloat16, device=x.device)
+        out = torch.zeros((B, Dp, Hp, Wp, cout), dtype=torch.bfloat16, device=x.device)
         _check(lib().darc_conv3d(_ptr(x), S, cin, _ptr(wt), _ptr(bias), _ptr(out), cout, cout, None, _ptr(gate),
-                                 gs, int(act), slope, B, D, H, W, kp, np_, _stream()))
+                                 gs, int(act), slope, B, D, H, W, np_, _stream()))
     return out
 
 
-def conv3d_wgrad(x: torch.Tensor, cin: int, gz: torch.Tensor, cout: int, kp: int, np_: int):
-    """(dw fp32 [np, kp], db fp32 [cout]) of darc_conv3d (darc_conv3d_wgrad);
-    gz: bf16 channels-last [B, D, H, W, S] gradient wrt the pre-activation."""
+def conv3d_wgrad(x: torch.Tensor, cin: int, gz: torch.Tensor, cout: int, np_: int):
+    """(dw fp32 [np, 27 cin], db fp32 [cout]) of conv3d (darc_conv3d_wgrad);
+    x, gz: bf16 channels-last with a zero border, gz the gradient wrt the
+    pre-activation."""
     _need(x, "x", torch.bfloat16)
     _need(gz, "gz", torch.bfloat16)
-    B, D, H, W, S = (int(d) for d in x.shape)
+    B, Dp, Hp, Wp, S = (int(d) for d in x.shape)
+    kp = 27 * cin
     dw = torch.empty((np_, kp), dtype=torch.float32, device=x.device)
     db = torch.empty(cout, dtype=torch.float32, device=x.device)
     nbytes = 64 * kp * np_ * 4
     work = _work(nbytes, x.device)
-    _check(lib().darc_conv3d_wgrad(_ptr(x), S, cin, _ptr(gz), int(gz.shape[-1]), cout, _ptr(dw), _ptr(db), B, D, H,
-                                   W, kp, np_, _ptr(work), nbytes, _stream()))
+    _check(lib().darc_conv3d_wgrad(_ptr(x), S, cin, _ptr(gz), int(gz.shape[-1]), cout, _ptr(dw), _ptr(db), B,
+                                   Dp - 2, Hp - 2, Wp - 2, np_, _ptr(work), nbytes, _stream()))
     return dw, db
 
 

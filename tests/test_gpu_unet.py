@@ -46,8 +46,8 @@ def rup(x, m):
 
 
 def to_oracle_x(x, cin):
-    """bf16 channels-last [B, D, H, W, S] -> fp64 [B, cin, D, H, W]."""
-    return np.ascontiguousarray(x[..., :cin].permute(0, 4, 1, 2, 3).double().cpu().numpy())
+    """bf16 channels-last with a zero border [B, D+2, H+2, W+2, S] -> fp64 [B, cin, D, H, W]."""
+    return np.ascontiguousarray(x[:, 1:-1, 1:-1, 1:-1, :cin].permute(0, 4, 1, 2, 3).double().cpu().numpy())
 
 
 def to_oracle_w(wt, cin, cout):
@@ -65,31 +65,40 @@ def to_gpu_w(w_or, cinp, kp, np_):
     return torch.from_numpy(t).float()
 
 
-def rand_w(g, cin, cout, kp, np_, scale=0.2):
-    w = torch.zeros(np_, kp)
-    w[:cout, :27 * cin] = torch.randn(cout, 27 * cin, generator=g) * scale
-    return w.to(torch.bfloat16)
+def rand_w(g, cin, cout, np_, scale=0.2):
+    """fp32 masters [np, 27 cin] holding bf16 values (zero past cout)."""
+    w = torch.zeros(np_, 27 * cin)
+    w[:cout] = (torch.randn(cout, 27 * cin, generator=g) * scale).to(torch.bfloat16).float()
+    return w
+
+
+def rand_padded(g, B, shape, S, nz=None):
+    x = torch.randn(B, *shape, S, generator=g)
+    if nz is not None:
+        x[..., nz:] = 0
+    return darc.pad_volume(x.to(torch.bfloat16))
 
 
 CONV_CASES = [
-    # B, (D, H, W), cin, stride, cout, np     (voxel counts not multiples of 128: ragged last tile)
+    # B, (D, H, W), cin, stride, cout, np     (row counts not multiples of 128: ragged last tile)
     (2, (6, 7, 9), 16, 16, 16, 16),
-    (1, (5, 8, 12), 8, 8, 3, 16),
+    (1, (5, 8, 12), 16, 16, 3, 16),
     (2, (4, 6, 10), 48, 64, 32, 32),
     (1, (4, 4, 8), 16, 16, 192, 192),
     (1, (4, 5, 6), 128, 128, 128, 128),
+    (1, (3, 4, 112), 16, 16, 256, 256),          # a wide window: two pipeline stages
 ]
 
 
 @pytest.mark.parametrize("B,shape,cin,S,cout,np_", CONV_CASES)
 def test_conv3d_fp32_output_matches_oracle(B, shape, cin, S, cout, np_):
     g = torch.Generator().manual_seed(B * 1000 + cin + cout)
-    kp = rup(27 * cin, 16)
-    x = torch.randn(B, *shape, S, generator=g).to(torch.bfloat16)
-    wt = rand_w(g, cin, cout, kp, np_)
+    x = rand_padded(g, B, shape, S)
+    w = rand_w(g, cin, cout, np_)
     bias = torch.randn(cout, generator=g) * 0.1
-    got = darc.conv3d(x.to(DEV), cin, wt.to(DEV), cout, bias=bias.to(DEV), f32_out=True).cpu().double().numpy()
-    xo, wo, bo = to_oracle_x(x, cin), to_oracle_w(wt, cin, cout), bias.double().numpy()
+    wt = darc.conv3d_pack_weights(w.to(DEV), cin, cout)
+    got = darc.conv3d(x.to(DEV), cin, wt, cout, np_, bias=bias.to(DEV), f32_out=True).cpu().double().numpy()
+    xo, wo, bo = to_oracle_x(x, cin), to_oracle_w(w, cin, cout), bias.double().numpy()
     ref = oracle.conv3d(xo, wo, bo)
     # bf16 x bf16 products are exact in fp32; K + 1 fp32 additions in any order
     bound = 2 * (27 * cin + 1) * U * oracle.conv3d(np.abs(xo), np.abs(wo), np.abs(bo))
@@ -99,14 +108,15 @@ def test_conv3d_fp32_output_matches_oracle(B, shape, cin, S, cout, np_):
 @pytest.mark.parametrize("B,shape,cin,S,cout,np_", CONV_CASES[:3])
 def test_conv3d_bf16_output_with_activation_and_gate(B, shape, cin, S, cout, np_):
     g = torch.Generator().manual_seed(7 + cin)
-    kp = rup(27 * cin, 16)
-    x = torch.randn(B, *shape, S, generator=g).to(torch.bfloat16)
-    wt = rand_w(g, cin, cout, kp, np_)
+    x = rand_padded(g, B, shape, S)
+    w = rand_w(g, cin, cout, np_)
     bias = torch.randn(cout, generator=g) * 0.1
-    gate = torch.randn(B, *shape, cout, generator=g).to(torch.bfloat16)
-    got = darc.conv3d(x.to(DEV), cin, wt.to(DEV), cout, bias=bias.to(DEV), act=True, gate=gate.to(DEV))
-    got = got.permute(0, 4, 1, 2, 3).double().cpu().numpy()
-    xo, wo, bo = to_oracle_x(x, cin), to_oracle_w(wt, cin, cout), bias.double().numpy()
+    gate = rand_padded(g, B, shape, cout)
+    wt = darc.conv3d_pack_weights(w.to(DEV), cin, cout)
+    got = darc.conv3d(x.to(DEV), cin, wt, cout, np_, bias=bias.to(DEV), act=True, gate=gate.to(DEV)).cpu()
+    assert not got[:, 0].any() and not got[:, -1].any() and not got[:, :, 0].any() and not got[:, :, :, -1].any()
+    got = got[:, 1:-1, 1:-1, 1:-1].permute(0, 4, 1, 2, 3).double().numpy()
+    xo, wo, bo = to_oracle_x(x, cin), to_oracle_w(w, cin, cout), bias.double().numpy()
     gf = np.where(to_oracle_x(gate, cout) > 0, 1.0, 0.2)
     ref = ounet.lrelu(oracle.conv3d(xo, wo, bo)) * gf
     bound = 2 * (27 * cin + 1) * U * oracle.conv3d(np.abs(xo), np.abs(wo), np.abs(bo))
@@ -114,48 +124,42 @@ def test_conv3d_bf16_output_with_activation_and_gate(B, shape, cin, S, cout, np_
     assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + bound)
 
 
-@pytest.mark.parametrize("B,shape,cin,cout", [(2, (6, 7, 9), 16, 16), (1, (4, 6, 8), 192, 64), (1, (5, 6, 7), 16, 3)])
-def test_conv3d_as_data_gradient_matches_oracle_adjoint(B, shape, cin, cout):
-    """The data gradient is the forward kernel run on gz with the flipped,
-    transposed weights wd[ci][tap' * coutp + co] = w[co][ci][26 - tap']."""
+@pytest.mark.parametrize("B,shape,cin,cout", [(2, (6, 7, 9), 16, 16), (1, (4, 6, 8), 192, 64), (1, (5, 6, 7), 16, 3),
+                                              (1, (3, 4, 112), 48, 16)])
+def test_conv3d_data_gradient_matches_oracle_adjoint(B, shape, cin, cout):
+    """The data gradient: the same kernel on gz with the weights packed
+    flipped (transposed, mirrored kernel), gated by the layer input."""
     g = torch.Generator().manual_seed(cin * 31 + cout)
-    coutp = rup(cout, 8)
-    w_or = (torch.randn(cout, cin, 3, 3, 3, generator=g) * 0.2).to(torch.bfloat16).double().numpy()
-    gz = torch.zeros(B, *shape, coutp)
-    gz[..., :cout] = torch.randn(B, *shape, cout, generator=g)
-    gz = gz.to(torch.bfloat16)
-    kpd, npd = rup(27 * coutp, 16), rup(cin, 16)
-    wd = np.zeros((npd, kpd))
-    flat = w_or.reshape(cout, cin, 27)
-    for tp in range(27):
-        wd[:cin, tp * coutp:tp * coutp + cout] = flat[:, :, 26 - tp].T
-    wd = torch.from_numpy(wd).to(torch.bfloat16)
-    gate = torch.randn(B, *shape, cin, generator=g).to(torch.bfloat16)
-    got = darc.conv3d(gz.to(DEV), coutp, wd.to(DEV), cin, gate=gate.to(DEV), f32_out=True).cpu().double().numpy()
-    gzo = to_oracle_x(gz, cout)
+    coutp = rup(cout, 16)
+    w = rand_w(g, cin, cout, coutp)
+    gz = rand_padded(g, B, shape, coutp, nz=cout)
+    gate = rand_padded(g, B, shape, cin)
+    wd = darc.conv3d_pack_weights(w.to(DEV), cin, cout, flip=True)
+    got = darc.conv3d(gz.to(DEV), coutp, wd, cin, cin, gate=gate.to(DEV), f32_out=True).cpu().double().numpy()
+    gzo, wo = to_oracle_x(gz, cout), to_oracle_w(w, cin, cout)
     gf = np.where(to_oracle_x(gate, cin) > 0, 1.0, 0.2)
-    ref = oracle.conv3d_adjoint_input(gzo, w_or) * gf
-    bound = 2 * (27 * coutp + 1) * U * oracle.conv3d_adjoint_input(np.abs(gzo), np.abs(w_or))
+    ref = oracle.conv3d_adjoint_input(gzo, wo) * gf
+    bound = 2 * (27 * coutp + 1) * U * oracle.conv3d_adjoint_input(np.abs(gzo), np.abs(wo))
     assert np.all(np.abs(got - ref) <= bound)
 
 
-@pytest.mark.parametrize("B,shape,cin,S,cout", [(2, (6, 7, 9), 16, 16, 16), (2, (16, 16, 20), 8, 8, 8),
+@pytest.mark.parametrize("B,shape,cin,S,cout", [(2, (6, 7, 9), 16, 16, 16), (2, (16, 16, 20), 16, 16, 16),
                                                  (1, (8, 8, 12), 48, 48, 16), (1, (4, 4, 8), 128, 128, 128)])
 def test_conv3d_weight_gradient_matches_oracle(B, shape, cin, S, cout):
     g = torch.Generator().manual_seed(cin * 7 + cout + B)
-    kp, np_ = rup(27 * cin, 16), rup(cout, 16)
-    x = torch.randn(B, *shape, S, generator=g).to(torch.bfloat16)
-    gz = torch.randn(B, *shape, cout, generator=g).to(torch.bfloat16)
-    dw, db = darc.conv3d_wgrad(x.to(DEV), cin, gz.to(DEV), cout, kp, np_)
+    np_ = rup(cout, 16)
+    x = rand_padded(g, B, shape, S)
+    gz = rand_padded(g, B, shape, cout)
+    dw, db = darc.conv3d_wgrad(x.to(DEV), cin, gz.to(DEV), cout, np_)
     xo, gzo = to_oracle_x(x, cin), to_oracle_x(gz, cout)
     ref_dw, ref_db = oracle.conv3d_wgrad(xo, gzo)
     abs_dw, abs_db = oracle.conv3d_wgrad(np.abs(xo), np.abs(gzo))
     nvox = B * int(np.prod(shape))
     got_dw = to_oracle_w(dw, cin, cout)
-    # every partial and the fixed-order split reduction are fp32 sums of at most nvox + 1 terms
+    # every partial and the fixed-order split reduction are fp32 sums of at most nvox + 1 nonzero terms
     assert np.all(np.abs(got_dw - ref_dw) <= 2 * (nvox + 1) * U * abs_dw)
     assert np.linalg.norm(got_dw - ref_dw) <= 1e-5 * np.linalg.norm(ref_dw)
-    assert not dw[cout:].any() and not dw[:, 27 * cin:].any()
+    assert not dw[cout:].any()
     assert np.all(np.abs(db.cpu().double().numpy() - ref_db) <= 2 * (nvox + 1) * U * abs_db)
 
 
