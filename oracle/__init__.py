@@ -107,6 +107,8 @@ def _load():
             "ora_propagate_labels": (_int, [_U8, _D, _int, _int, _int, _int, _U8]),
             "ora_jacobian_det": (_int, [_D, _int, _int, _int, _D]),
             "ora_dice": (None, [_U8, _U8, _long, _int, _D]),
+            "ora_compose": (_int, [_D, _D, _int, _int, _int, _D]),
+            "ora_diffeo_report": (_int, [_D, _int, _int, _int, _int, _D]),
             "ora_conv3d": (_int, [_D, _int, _int, _int, _int, _int, _D, _D, _int, _D]),
             "ora_conv3d_adjoint_input": (_int, [_D, _int, _int, _int, _int, _int, _D, _int, _D]),
             "ora_conv3d_wgrad": (_int, [_D, _D, _int, _int, _int, _int, _int, _int, _D, _D]),
@@ -365,6 +367,26 @@ def dice(a, b, nlab):
     out = np.empty(nlab - 1)
     _load().ora_dice(_pu8(a), _pu8(b), a.size, int(nlab), _p(out))
     return out
+
+
+def compose(a, b):
+    """Displacement of phi_b o phi_a: a(x) + S(b, x + a(x)); a, b [3, D, H, W]."""
+    a, b = _d(a), _d(b)
+    D, H, W = _dims(a.shape)
+    out = np.empty_like(a)
+    _load().ora_compose(_p(a), _p(b), D, H, W, _p(out))
+    return out
+
+
+def diffeo_report(v, T):
+    """(negative-Jacobian fraction of Exp(v), mean and max |Exp(-v) o Exp(v) - id|,
+    min det) of one velocity field [3, D, H, W]."""
+    v = _d(v)
+    D, H, W = _dims(v.shape)
+    st = np.empty(4)
+    if _load().ora_diffeo_report(_p(v), D, H, W, T, _p(st)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return st
 
 
 # ---- learned warm start: 3x3x3 'same' convolution (no counterpart in the paper) ----

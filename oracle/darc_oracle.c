@@ -959,3 +959,63 @@ int ora_conv3d_wgrad(const double *x, const double *gz, int B, int cin, int cout
         }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Composition of two maps given as displacements (Sec. "Diffeomorphisms":   */
+/* phi = id + u): (phi_b o phi_a)(x) = x + a(x) + b(x + a(x)), so the        */
+/* displacement is out(x) = a(x) + S(b, x + a(x)), trilinear, border padded. */
+/* ------------------------------------------------------------------------ */
+int ora_compose(const double *a, const double *b, int D, int H, int W, double *out)
+{
+    const long V = (long)D * H * W;
+    const int n[3] = {D, H, W};
+#pragma omp parallel for schedule(static)
+    for (long z = 0; z < D; ++z)
+        for (long y = 0; y < H; ++y)
+            for (long x = 0; x < W; ++x) {
+                const long l = lin3(n, z, y, x);
+                const double pz = (double)z + a[l], py = (double)y + a[V + l], px = (double)x + a[2 * V + l];
+                for (int ch = 0; ch < 3; ++ch)
+                    out[ch * V + l] = a[ch * V + l] + ora_sample(b + ch * V, D, H, W, pz, py, px, NULL);
+            }
+    return 0;
+}
+
+/* Diffeomorphism report of one velocity field (Sec. "Evaluation metrics":
+ * folding rate |J|<0 %; Sec. "Diffeomorphisms": Exp(-v) inverts Exp(v)):
+ * stats[0] = fraction of voxels with det(I + grad u+) <= 0, u+ = Exp(v);
+ * stats[1], stats[2] = mean and max over voxels of |r(x)|, r the
+ * displacement of Exp(-v) o Exp(v) (zero for an exact inverse);
+ * stats[3] = min det(I + grad u+). */
+int ora_diffeo_report(const double *v, int D, int H, int W, int T, double *stats)
+{
+    const long V = (long)D * H * W;
+    double *up = (double *)malloc(sizeof(double) * 3 * V * (T + 1));
+    double *um = (double *)malloc(sizeof(double) * 3 * V * (T + 1));
+    double *r = (double *)malloc(sizeof(double) * 3 * V);
+    double *det = (double *)malloc(sizeof(double) * V);
+    if (!up || !um || !r || !det) {
+        free(up); free(um); free(r); free(det);
+        return -1;
+    }
+    ora_exp(v, D, H, W, T, 1.0, up);
+    ora_exp(v, D, H, W, T, -1.0, um);
+    const double *uP = up + (long)T * 3 * V, *uM = um + (long)T * 3 * V;
+    ora_compose(uP, uM, D, H, W, r);
+    ora_jacobian_det(uP, D, H, W, det);
+    long neg = 0;
+    double sum = 0.0, mx = 0.0, mn = det[0];
+    for (long l = 0; l < V; ++l) {
+        const double e = sqrt(r[l] * r[l] + r[V + l] * r[V + l] + r[2 * V + l] * r[2 * V + l]);
+        sum += e;
+        if (e > mx) mx = e;
+        if (det[l] <= 0.0) ++neg;
+        if (det[l] < mn) mn = det[l];
+    }
+    stats[0] = (double)neg / (double)V;
+    stats[1] = sum / (double)V;
+    stats[2] = mx;
+    stats[3] = mn;
+    free(up); free(um); free(r); free(det);
+    return 0;
+}
