@@ -31,7 +31,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-MSE, LNCC = 0, 1
+MSE, LNCC, L1, SSIM = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -108,6 +108,10 @@ def _load():
             "ora_jacobian_det": (_int, [_D, _int, _int, _int, _D]),
             "ora_dice": (None, [_U8, _U8, _long, _int, _D]),
             "ora_compose": (_int, [_D, _D, _int, _int, _int, _D]),
+            "ora_l1": (_dbl, [_D, _D, _long, _D, _D]),
+            "ora_ssim": (_dbl, [_D, _D, _int, _int, _int, _int, _D, _D, _D]),
+            "ora_median": (_int, [_D, _int, _long, _D]),
+            "ora_atlas_median": (_int, [_D, _D, _int, _int, _int, _int, _int, _D]),
             "ora_diffeo_report": (_int, [_D, _int, _int, _int, _int, _D]),
             "ora_conv3d": (_int, [_D, _int, _int, _int, _int, _int, _D, _D, _int, _D]),
             "ora_conv3d_adjoint_input": (_int, [_D, _int, _int, _int, _int, _int, _D, _int, _D]),
@@ -367,6 +371,55 @@ def dice(a, b, nlab):
     out = np.empty(nlab - 1)
     _load().ora_dice(_pu8(a), _pu8(b), a.size, int(nlab), _p(out))
     return out
+
+
+def l1(Wimg, A, with_grad=False):
+    """L1 dissimilarity (Sec. "Dissimilarity metrics"): mean |W - A|; with
+    grad also (dL/dW, dL/dA) = (sign(W - A), -sign(W - A)) / V."""
+    Wimg, A = _d(Wimg), _d(A)
+    gW = np.empty_like(Wimg) if with_grad else None
+    gA = np.empty_like(A) if with_grad else None
+    L = _load().ora_l1(_p(Wimg), _p(A), Wimg.size, _p(gW) if with_grad else None, _p(gA) if with_grad else None)
+    return (L, gW, gA) if with_grad else L
+
+
+def ssim(J, A, w, with_grad=False, with_map=False):
+    """SSIM dissimilarity -(1/V) sum ssim over w^3 windows (zero padding,
+    N = w^3, C1 = 1e-4, C2 = 9e-4); optionally (dL/dJ, dL/dA) and the map."""
+    J, A = _d(J), _d(A)
+    D, H, W = _dims(J.shape)
+    gJ = np.empty_like(J) if with_grad else None
+    gA = np.empty_like(A) if with_grad else None
+    m = np.empty_like(J) if with_map else None
+    L = _load().ora_ssim(_p(J), _p(A), D, H, W, int(w), _p(gJ) if with_grad else None,
+                         _p(gA) if with_grad else None, _p(m) if with_map else None)
+    out = [L]
+    if with_grad:
+        out += [gJ, gA]
+    if with_map:
+        out.append(m)
+    return tuple(out) if len(out) > 1 else L
+
+
+def median(X):
+    """Voxel-wise lower median over the first axis: sorted[(n - 1) // 2]."""
+    X = _d(X)
+    n = X.shape[0]
+    out = np.empty(X.shape[1:])
+    if _load().ora_median(_p(X), n, out.size, _p(out)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return out
+
+
+def atlas_median(I_all, v_all, T):
+    """L1 atlas (Sec. "Dissimilarity metrics"): median_i I_i o Exp(v_i)."""
+    I_all, v_all = _d(I_all), _d(v_all)
+    n = I_all.shape[0]
+    D, H, W = _dims(I_all.shape)
+    A = np.empty((D, H, W))
+    if _load().ora_atlas_median(_p(I_all), _p(v_all), n, D, H, W, int(T), _p(A)) != 0:
+        raise MemoryError("oracle allocation failed")
+    return A
 
 
 def compose(a, b):

@@ -34,7 +34,7 @@
 /* configuration (mirrors the knobs Algorithm 1 and Sec. "Experiments" name) */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int dissim;        /* 0 = MSE, 1 = local (windowed) NCC                    */
+    int dissim;        /* 0 = MSE, 1 = local (windowed) NCC, 2 = L1, 3 = SSIM  */
     int window;        /* NCC window edge w (odd)                              */
     int T;             /* scaling-and-squaring steps                           */
     int inner_steps;   /* K2: Adam steps per subject per sweep                 */
@@ -474,6 +474,130 @@ double ora_lncc(const double *J, const double *A, int D, int H, int W, int w, do
 }
 
 /* ------------------------------------------------------------------------ */
+/* L1 dissimilarity (Sec. "Dissimilarity metrics", point-wise):              */
+/*   L = 1/V sum |W - A|;  dL/dW = sign(W - A) / V (0 where W = A, the       */
+/*   subgradient torch's abs takes), dL/dA = -dL/dW.                         */
+/* ------------------------------------------------------------------------ */
+double ora_l1(const double *Wimg, const double *A, long V, double *gW, double *gA)
+{
+    double L = 0.0;
+    for (long l = 0; l < V; ++l) {
+        const double d = Wimg[l] - A[l];
+        L += fabs(d);
+        const double sg = (d > 0.0) ? 1.0 : ((d < 0.0) ? -1.0 : 0.0);
+        if (gW) gW[l] = sg / (double)V;
+        if (gA) gA[l] = -sg / (double)V;
+    }
+    return L / (double)V;
+}
+
+/* ------------------------------------------------------------------------ */
+/* SSIM dissimilarity (Sec. "Dissimilarity metrics", patch-wise).  The      */
+/* paper names the metric only; reading: the structural similarity of Wang */
+/* et al. (2004) over the same w^3 windows as the local NCC (zero padding,   */
+/* normalised by N = w^3), constants C1 = (0.01 * 1)^2, C2 = (0.03 * 1)^2   */
+/* for intensities on [0, 1]:                                                */
+/*   mu = S/N, var = S2/N - mu^2, cov = SJA/N - muJ muA,                     */
+/*   ssim = (2 muJ muA + C1)(2 cov + C2) / ((muJ^2 + muA^2 + C1)(varJ + varA + C2)) */
+/*   L = -(1/V) sum ssim.                                                    */
+/* The gradient has the NCC form: with a = dssim/dS_J, b = dssim/dS_JJ,      */
+/* g = dssim/dS_JA at each window centre,                                    */
+/*   dL/dJ(y) = -1/V [ sum_{x ~ y} a(x) + 2 J(y) sum b(x) + A(y) sum g(x) ]. */
+/* ------------------------------------------------------------------------ */
+double ora_ssim(const double *J, const double *A, int D, int H, int W, int w, double *gJ, double *gA,
+                double *ssim_out)
+{
+    const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+    const int n[3] = {D, H, W};
+    const long V = (long)D * H * W;
+    const int r = w / 2;
+    const double N = (double)w * w * w;
+    double *aJ = (double *)malloc(sizeof(double) * V);
+    double *bJ = (double *)malloc(sizeof(double) * V);
+    double *aA = (double *)malloc(sizeof(double) * V);
+    double *bA = (double *)malloc(sizeof(double) * V);
+    double *gm = (double *)malloc(sizeof(double) * V);
+    double *ss = (double *)malloc(sizeof(double) * V);
+    if (!aJ || !bJ || !aA || !bA || !gm || !ss) {
+        free(aJ); free(bJ); free(aA); free(bA); free(gm); free(ss);
+        return NAN;
+    }
+#pragma omp parallel for schedule(static)
+    for (long z = 0; z < D; ++z)
+        for (long y = 0; y < H; ++y)
+            for (long x = 0; x < W; ++x) {
+                double sJ = 0, sA = 0, sJJ = 0, sAA = 0, sJA = 0;
+                for (long qz = z - r; qz <= z + r; ++qz) {
+                    if (qz < 0 || qz >= D) continue;
+                    for (long qy = y - r; qy <= y + r; ++qy) {
+                        if (qy < 0 || qy >= H) continue;
+                        for (long qx = x - r; qx <= x + r; ++qx) {
+                            if (qx < 0 || qx >= W) continue;
+                            const long q = lin3(n, qz, qy, qx);
+                            sJ += J[q];
+                            sA += A[q];
+                            sJJ += J[q] * J[q];
+                            sAA += A[q] * A[q];
+                            sJA += J[q] * A[q];
+                        }
+                    }
+                }
+                const long l = lin3(n, z, y, x);
+                const double mJ = sJ / N, mA = sA / N;
+                const double vJ = sJJ / N - mJ * mJ, vA = sAA / N - mA * mA;
+                const double cJA = sJA / N - mJ * mA;
+                const double a1 = 2.0 * mJ * mA + C1, a2 = 2.0 * cJA + C2;
+                const double b1 = mJ * mJ + mA * mA + C1, b2 = vJ + vA + C2;
+                const double S = a1 * a2 / (b1 * b2);
+                ss[l] = S;
+                /* d/dS_J: da1 = 2 mA/N, da2 = -2 mA/N, db1 = 2 mJ/N, db2 = -2 mJ/N */
+                aJ[l] = (2.0 / N) * (mA * (a2 - a1) / (b1 * b2) - mJ * S * (1.0 / b1 - 1.0 / b2));
+                aA[l] = (2.0 / N) * (mJ * (a2 - a1) / (b1 * b2) - mA * S * (1.0 / b1 - 1.0 / b2));
+                bJ[l] = -S / (N * b2);           /* db2/dS_JJ = 1/N */
+                bA[l] = -S / (N * b2);
+                gm[l] = 2.0 * a1 / (N * b1 * b2); /* da2/dS_JA = 2/N */
+            }
+    double L = 0.0;
+    for (long l = 0; l < V; ++l) L += ss[l];
+    L = -L / (double)V;
+    if (gJ || gA) {
+#pragma omp parallel for schedule(static)
+        for (long z = 0; z < D; ++z)
+            for (long y = 0; y < H; ++y)
+                for (long x = 0; x < W; ++x) {
+                    double saJ = 0, sbJ = 0, saA = 0, sbA = 0, sg = 0;
+                    for (long qz = z - r; qz <= z + r; ++qz) {
+                        if (qz < 0 || qz >= D) continue;
+                        for (long qy = y - r; qy <= y + r; ++qy) {
+                            if (qy < 0 || qy >= H) continue;
+                            for (long qx = x - r; qx <= x + r; ++qx) {
+                                if (qx < 0 || qx >= W) continue;
+                                const long q = lin3(n, qz, qy, qx);
+                                saJ += aJ[q]; sbJ += bJ[q];
+                                saA += aA[q]; sbA += bA[q];
+                                sg += gm[q];
+                            }
+                        }
+                    }
+                    const long l = lin3(n, z, y, x);
+                    if (gJ) gJ[l] = -(saJ + 2.0 * J[l] * sbJ + A[l] * sg) / (double)V;
+                    if (gA) gA[l] = -(saA + 2.0 * A[l] * sbA + J[l] * sg) / (double)V;
+                }
+    }
+    if (ssim_out) memcpy(ssim_out, ss, sizeof(double) * V);
+    free(aJ); free(bJ); free(aA); free(bA); free(gm); free(ss);
+    return L;
+}
+
+/* the patch-wise dissimilarity of the configuration (1: NCC, 3: SSIM) */
+static double patch_loss(const ora_cfg *cfg, const double *J, const double *A, int D, int H, int W, double *gJ,
+                         double *gA)
+{
+    if (cfg->dissim == 3) return ora_ssim(J, A, D, H, W, cfg->window, gJ, gA, NULL);
+    return ora_lncc(J, A, D, H, W, cfg->window, cfg->ncc_eps, gJ, gA, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adam (Sec. "Experiments": Adam, lr 1e-2, for velocities and atlas).       */
 /* Reading of the silent constants: beta1 0.9, beta2 0.999, eps 1e-8, bias   */
 /* corrected, eps added after the square root (Kingma & Ba).  k is 1-based.  */
@@ -517,8 +641,10 @@ double ora_subject_energy(const double *I, const double *A, const double *v, int
     double L;
     if (cfg->dissim == 0)
         L = ora_mse(Wimg, A, V, gW, NULL);
+    else if (cfg->dissim == 2)
+        L = ora_l1(Wimg, A, V, gW, NULL);
     else
-        L = ora_lncc(Wimg, A, D, H, W, cfg->window, cfg->ncc_eps, gW, NULL, NULL);
+        L = patch_loss(cfg, Wimg, A, D, H, W, gW, NULL);
     const double R = ora_reg(uT, D, H, W, gR);
     if (parts) { parts[0] = L; parts[1] = R; }
     if (gv) {
@@ -611,6 +737,48 @@ int ora_atlas_mean(const double *I_all, const double *v_all, int n, int D, int H
 }
 
 /* ------------------------------------------------------------------------ */
+/* Atlas closed form for L1 (Sec. "Dissimilarity metrics"): the voxel-wise  */
+/* median of the warped cohort, A(x) = median_i I_i o Exp(hat v_i)(x).       */
+/* Reading for an even n: the lower of the two middle values (sorted s_0 <=  */
+/* ... <= s_{n-1}, A = s_{(n-1)/2}), which minimises the L1 sum like any     */
+/* value between the middle two and is the value torch.median returns.      */
+/* ------------------------------------------------------------------------ */
+static int cmp_double(const void *a, const void *b)
+{
+    const double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+int ora_median(const double *X, int n, long V, double *out)
+{
+    double *col = (double *)malloc(sizeof(double) * n);
+    if (!col) return -1;
+    for (long l = 0; l < V; ++l) {
+        for (int i = 0; i < n; ++i) col[i] = X[(long)i * V + l];
+        qsort(col, n, sizeof(double), cmp_double);
+        out[l] = col[(n - 1) / 2];
+    }
+    free(col);
+    return 0;
+}
+
+int ora_atlas_median(const double *I_all, const double *v_all, int n, int D, int H, int W, int T, double *A)
+{
+    const long V = (long)D * H * W;
+    double *u_all = (double *)malloc(sizeof(double) * 3 * V * (T + 1));
+    double *Wall = (double *)malloc(sizeof(double) * V * n);
+    if (!u_all || !Wall) { free(u_all); free(Wall); return -1; }
+    for (int i = 0; i < n; ++i) {
+        ora_exp(v_all + (long)i * 3 * V, D, H, W, T, 1.0, u_all);
+        ora_warp(I_all + (long)i * V, u_all + (long)T * 3 * V, D, H, W, Wall + (long)i * V, NULL);
+    }
+    const int rc = ora_median(Wall, n, V, A);
+    free(u_all);
+    free(Wall);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Mini-batch order for the atlas SGD (Algorithm 1, SGD_for_atlas's         */
 /* "dataloader").  The paper does not say how batches are drawn; reading: a */
 /* fresh uniform shuffle per epoch, from the counter-based SplitMix64        */
@@ -647,8 +815,9 @@ uint64_t ora_splitmix64(uint64_t s0, uint64_t k)
 /* ------------------------------------------------------------------------ */
 /* Atlas by mini-batch SGD (Sec. "Dissimilarity metrics", NCC/SSIM have no  */
 /* closed form; Algorithm 1 SGD_for_atlas): K3 epochs, each a pass over the */
-/* shuffled cohort in mini-batches; per batch the loss is the mean NCC      */
-/* dissimilarity of its warped images W_i = I_i o Exp(hat v_i) to A, and    */
+/* shuffled cohort in mini-batches; per batch the loss is the mean patch-  */
+/* wise (NCC or SSIM) dissimilarity of its warped images W_i = I_i o       */
+/* Exp(hat v_i) to A, and                                                   */
 /* Adam (fresh state per call, as SGD_for_atlas creates its optimiser)       */
 /* updates A.  Reading: A starts from the current atlas (warm start) rather */
 /* than a fresh initialize().  loss_out (nullable) <- mean loss of the last */
@@ -685,8 +854,7 @@ int ora_atlas_sgd(const double *I_all, const double *v_all, int n, int D, int H,
             memset(gA, 0, sizeof(double) * V);
             for (int q = 0; q < nb; ++q) {
                 const int i = perm[b0 + q];
-                ep_loss += ora_lncc(Wall + (long)i * V, A, D, H, W, cfg->window, cfg->ncc_eps,
-                                    NULL, gi, NULL);
+                ep_loss += patch_loss(cfg, Wall + (long)i * V, A, D, H, W, NULL, gi);
                 for (long l = 0; l < V; ++l) gA[l] += gi[l] / (double)nb;
             }
             ++k;
@@ -742,6 +910,8 @@ int ora_sweep(const double *I_all, double *v_all, double *m_all, double *s_all, 
     int rc;
     if (cfg->dissim == 0)
         rc = ora_atlas_mean(I_all, v_all, n, D, H, W, cfg->T, A);
+    else if (cfg->dissim == 2)
+        rc = ora_atlas_median(I_all, v_all, n, D, H, W, cfg->T, A);
     else
         rc = ora_atlas_sgd(I_all, v_all, n, D, H, W, cfg, sweep, A, NULL);
     if (stats) {
