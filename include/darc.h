@@ -48,14 +48,17 @@ typedef enum {
     DARC_ERR_INTERNAL = -7
 } darc_status;
 
-typedef enum { DARC_MSE = 0, DARC_LNCC = 1 } darc_dissim;
+/* Dissimilarities (Sec. "Dissimilarity metrics"): point-wise MSE and L1
+ * (closed-form atlas: mean, voxel-wise median), patch-wise local NCC and
+ * SSIM over w^3 windows (atlas by mini-batch Adam). */
+typedef enum { DARC_MSE = 0, DARC_LNCC = 1, DARC_L1 = 2, DARC_SSIM = 3 } darc_dissim;
 
 /* Method settings.  Defaults (darc_default_config) follow the paper where it
  * gives a number: T = 7 squarings (Sec. "Diffeomorphisms"); Adam lr 1e-2 for
  * velocities and atlas, K3 = 20 atlas epochs (Sec. "Experiments"). */
 typedef struct {
     int dissim;            /* darc_dissim                                         */
-    int ncc_window;        /* odd edge w of the local-NCC window, 3..17           */
+    int ncc_window;        /* odd edge w of the NCC / SSIM window, 3..17          */
     int n_squarings;       /* T, 0..20                                            */
     float lambda;          /* weight of the diffusion regulariser (Eq. 2)         */
     float lr, beta1, beta2, adam_eps;   /* Adam                                   */
@@ -130,6 +133,17 @@ int darc_update_atlas(darc_cohort* c, darc_sweep_stats* stats);
  * Errors: ARG, CUDA. */
 int darc_propagate_labels(darc_cohort* c, const uint8_t* atlas_labels_dev, uint8_t* out_dev,
                           int first, int count);
+
+/* Diffeomorphism report (Sec. "Evaluation metrics": the folding rate
+ * |J|<0 %; Sec. "Diffeomorphisms": Exp(-v) is the inverse of Exp(v)) for
+ * subjects first..first+count-1 from their current velocities:
+ * stats_host float [count][4] = {fraction of voxels with
+ * det(I + grad u) <= 0 for u = Exp(v); mean and max over voxels of
+ * |r(x)|, r the displacement of Exp(-v) o Exp(v) (zero for an exact
+ * inverse; trilinear composition); min det}.  Uses the cohort's scratch;
+ * the cohort's state is unchanged.  Waits for its work.
+ * Errors: ARG, OOM, CUDA. */
+int darc_diffeo_report(darc_cohort* c, int first, int count, float* stats_host);
 
 /* Copies of the state.  Velocity and atlas layouts as above.  set_velocity
  * zeroes subject i's Adam moments and step count (a warm start).
@@ -264,6 +278,18 @@ size_t darc_loss_workspace(int B, int D, int H, int W);
 int darc_mse(const float* J_dev, const float* A_dev, float* loss_dev, float* gJ_dev,
              void* work_dev, int B, int D, int H, int W, void* stream);
 
+/* L1 (Sec. "Dissimilarity metrics", point-wise): L_b = 1/V sum_x
+ * |J[b](x) - A(x)|; gJ_dev (nullable) [B][V] = sign(J - A) / V (0 where
+ * equal).  Layout and workspace as darc_mse.  Errors: ARG, SHAPE, CUDA. */
+int darc_l1(const float* J_dev, const float* A_dev, float* loss_dev, float* gJ_dev,
+            void* work_dev, int B, int D, int H, int W, void* stream);
+
+/* The L1 atlas closed form (Sec. "Dissimilarity metrics"): out_dev[x] =
+ * median over i of X_dev[i][x], X_dev [n][D*H*W].  Reading for even n: the
+ * lower middle value (sorted s_0 <= ... <= s_{n-1}, s_{(n-1)/2}); the result
+ * is always one of the inputs.  1 <= n <= 1600.  Errors: ARG, SHAPE, CUDA. */
+int darc_median(const float* X_dev, int n, int D, int H, int W, float* out_dev, void* stream);
+
 /* Local NCC (Sec. "Dissimilarity metrics", patch-wise NCC; reading: squared
  * correlation over the w^3 window with zero padding, normalised by w^3,
  * denominator + eps): L_b = -1/V sum_x cc_b(x).  gJ_dev (nullable) [B][V] =
@@ -273,6 +299,14 @@ size_t darc_lncc_workspace(int B, int D, int H, int W);
 int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, float* loss_dev,
               float* gJ_dev, float* gA_dev, void* work_dev, int B, int D, int H, int W,
               void* stream);
+
+/* SSIM (Sec. "Dissimilarity metrics", patch-wise; reading: Wang et al.'s
+ * structural similarity over the same w^3 windows as darc_lncc, zero
+ * padding, normalised by w^3, C1 = 1e-4, C2 = 9e-4 for intensities on
+ * [0, 1]): L_b = -1/V sum_x ssim_b(x).  Gradients, layouts and workspace
+ * (darc_lncc_workspace) as darc_lncc.  Errors: ARG, SHAPE, CUDA. */
+int darc_ssim(const float* J_dev, const float* A_dev, int window, float* loss_dev, float* gJ_dev,
+              float* gA_dev, void* work_dev, int B, int D, int H, int W, void* stream);
 
 /* Diffusion regulariser (Eq. 2 second term; reading: forward differences of
  * the displacement, mean over the voxel pairs of each axis, mean over the
@@ -318,6 +352,12 @@ int darc_atlas_mean(const float* I_dev, const float* v_dev, float* A_dev, void* 
  * out[b](x) = labels[r(x + u[b](x))].  Errors: ARG, CUDA. */
 int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* out_dev, int B,
                       int D, int H, int W, void* stream);
+
+/* Composition of two maps given as displacements (Sec. "Diffeomorphisms"):
+ * out[b](x) = a[b](x) + S(b_dev[b], x + a[b](x)), the displacement of
+ * phi_b o phi_a; trilinear, border padded.  All [B][3][V]; out must not
+ * alias a or b.  Errors: ARG, CUDA. */
+int darc_compose(const float* a_dev, const float* b_dev, float* out_dev, int B, int D, int H, int W, void* stream);
 
 /* Folding report (Sec. "Evaluation metrics", |J|<0 %): det(I + grad u) by
  * central differences (one-sided on faces) into det_dev (nullable) [B][V];

@@ -306,7 +306,7 @@ def splitmix64(s0, k):
 
 
 def atlas_sgd(I_all, v_all, A, cfg: Cfg, sweep: int):
-    """NCC atlas update by mini-batch Adam (Algorithm 1, SGD_for_atlas); A updated copy."""
+    """Patch-wise (NCC or SSIM) atlas update by mini-batch Adam (Algorithm 1, SGD_for_atlas); A updated copy."""
     I_all, v_all = _d(I_all), _d(v_all)
     A = _d(A).copy()
     n = I_all.shape[0]

@@ -14,12 +14,12 @@ from __future__ import annotations
 import dataclasses
 from typing import Dict, Tuple
 
-MSE, LNCC = 0, 1
+MSE, LNCC, L1, SSIM = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
 class DarcConfig:
-    dissim: int = LNCC          # 0 = MSE, 1 = local NCC
+    dissim: int = LNCC          # 0 = MSE, 1 = local NCC, 2 = L1, 3 = SSIM
     ncc_window: int = 9         # odd window edge of the local NCC
     n_squarings: int = 7        # T (Sec. "Diffeomorphisms": seven)
     lam: float = 1.0            # weight of the diffusion regulariser (Eq. 2)

@@ -52,11 +52,17 @@ int check_window(int w, int D, int H, int W)
     return DARC_OK;
 }
 
+// point-wise metrics (closed-form atlas) and patch-wise metrics (box
+// windows, atlas by mini-batch Adam)
+bool pointwise(int d) { return d == DARC_MSE || d == DARC_L1; }
+bool patchwise(int d) { return d == DARC_LNCC || d == DARC_SSIM; }
+int patch_metric(int d) { return d == DARC_SSIM ? 1 : 0; }
+
 int check_config(const darc_config* c, int D, int H, int W)
 {
     if (!c) return fail(DARC_ERR_ARG, "null config");
-    if (c->dissim != DARC_MSE && c->dissim != DARC_LNCC) return fail(DARC_ERR_ARG, "unknown dissimilarity");
-    if (c->dissim == DARC_LNCC) {
+    if (!pointwise(c->dissim) && !patchwise(c->dissim)) return fail(DARC_ERR_ARG, "unknown dissimilarity");
+    if (patchwise(c->dissim)) {
         int rc = check_window(c->ncc_window, D, H, W);
         if (rc) return rc;
     }
@@ -279,6 +285,8 @@ struct darc_cohort {
     int* perm_host = nullptr;    // pinned [K3][n]
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     std::map<std::pair<int, int>, long long> graph_kernels;     // kernels per replay of each graph
+    double* dpart = nullptr;                   // diffeomorphism report: block partials (allocated on first use)
+    float* dstats = nullptr;                   //   and per-subject results
     std::map<std::pair<int, int>, int> seen;
     // sharded atlas SGD state
     int sgd_k = 0;
@@ -399,9 +407,9 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     const float* uT = c->u_all + (size_t)plan.slot(T - 1) * fb;
     const double *pLp, *pRp;
     int nL, nR, sL, sR;
-    if (c->cfg.dissim == DARC_MSE) {
+    if (pointwise(c->cfg.dissim)) {
         Prof p(c, s, DARC_K_MSE_WARP_REG, 32.0 * nv);
-        e = mse_warp_reg(Ib, vol.V, c->A, uT, c->cfg.lambda, c->gT, c->pL, cnt, vol, s);
+        e = mse_warp_reg(Ib, vol.V, c->A, uT, c->cfg.lambda, c->gT, c->pL, cnt, vol, c->cfg.dissim == DARC_L1, s);
         pLp = c->pL; pRp = c->pL + 1; nL = nR = voxel_blocks(vol); sL = sR = 2;
         c->launches += 1;
     } else {
@@ -412,8 +420,8 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
         }
         if (e == cudaSuccess) {
             Prof p(c, s, DARC_K_LNCC_FWD, 28.0 * nv);
-            e = lncc_forward(c->Wimg, nullptr, c->A, c->astats, r, c->cfg.ncc_eps, 0, c->coef, c->pL, cnt, vol,
-                             c->boxbuf, s);
+            e = lncc_forward(c->Wimg, nullptr, c->A, c->astats, r, c->cfg.ncc_eps, 0, patch_metric(c->cfg.dissim),
+                             c->coef, c->pL, cnt, vol, c->boxbuf, s);
         }
         if (e == cudaSuccess) {
             Prof p(c, s, DARC_K_LNCC_BWD_WARP_REG, 48.0 * nv);
@@ -505,13 +513,15 @@ int update_atlas_impl(darc_cohort* c)
     const int T = c->cfg.n_squarings, n = c->n, K3 = c->cfg.atlas_epochs;
     const int nbatch = (n + c->cfg.atlas_batch - 1) / c->cfg.atlas_batch;
     // algorithmic bytes: centrality 24n + 12 per voxel; warped cohort (24T + 20) n;
-    // NCC SGD per mini-batch: statistics 12 + per subject 28 + 20 + Adam 24
+    // L1 median: the cached cohort read once, the atlas written; patch-wise SGD
+    // per mini-batch: statistics 12 + per subject 28 + 20 + Adam 24
     double bytes = (24.0 * n + 12.0) + (24.0 * T + 20.0) * n;
-    if (c->cfg.dissim == DARC_LNCC) bytes += 12.0 * n + (double)K3 * (nbatch * (12.0 + 24.0) + n * 48.0);
+    if (c->cfg.dissim == DARC_L1) bytes += 4.0 * n + 4.0;
+    if (patchwise(c->cfg.dissim)) bytes += 12.0 * n + (double)K3 * (nbatch * (12.0 + 24.0) + n * 48.0);
     Prof p(c, c->st, DARC_K_ATLAS, bytes * (double)vol.V);
     const long long chunks = (n + c->bmax - 1) / c->bmax;
     c->launches += 2 + chunks * (T + 1) +
-                   (c->cfg.dissim == DARC_LNCC ? chunks + (long long)K3 * nbatch * 6 + 1 : 1);
+                   (patchwise(c->cfg.dissim) ? chunks + (long long)K3 * nbatch * 6 + 1 : 1);
     return update_atlas_body(c);
 }
 
@@ -532,13 +542,19 @@ int update_atlas_body(darc_cohort* c)
         CK(finalize_mean(c->acc, 1.0 / n, c->A, vol, s));
         return DARC_OK;
     }
-    // local NCC: cache W_i = I_i o Exp(hat v_i), then K3 epochs of mini-batch Adam on A
+    // L1 and patch-wise: cache W_i = I_i o Exp(hat v_i)
     for (int f = 0; f < n; f += c->bmax) {
         const int cnt = std::min(c->bmax, n - f);
         float* uT = nullptr;
         CK(exp_forward_pingpong(c->v + (size_t)f * 3 * vol.V, c->u_all, cnt, vol, T, 1.f, s, &uT));
         CK(warp(c->images + (size_t)f * vol.V, vol.V, uT, c->Wcache + (size_t)f * vol.V, cnt, vol, s));
     }
+    if (c->cfg.dissim == DARC_L1) {
+        // closed form: the voxel-wise median of the warped cohort
+        CK(median(c->Wcache, n, vol.V, c->A, s));
+        return DARC_OK;
+    }
+    // patch-wise: K3 epochs of mini-batch Adam on A
     const int K3 = c->cfg.atlas_epochs, B = c->cfg.atlas_batch, r = c->cfg.ncc_window / 2;
     if (K3 > 0) {
         // Box(W_i), Box(W_i^2) do not depend on A: once per atlas update
@@ -559,7 +575,8 @@ int update_atlas_body(darc_cohort* c)
                 const int nb = std::min(B, n - b0);
                 const int* subj = c->perm_dev + (size_t)ep * n + b0;
                 CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));
-                CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps, c->coef,
+                CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps,
+                                     patch_metric(c->cfg.dissim), c->coef,
                                      c->pL, nb, vol, c->boxbuf, s));
                 CK(reduce_partials(c->pL, box_blocks(vol), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
                 CK(atlas_sgd_backward(c->Wcache, subj, c->A, c->coef, r, c->gsh, c->gA, nb, vol, c->boxbuf, s));
@@ -585,7 +602,7 @@ int fill_atlas_stats(darc_cohort* c, darc_sweep_stats* stats)
     stats->centrality_before = m[0];
     stats->centrality_after = m[1];
     stats->atlas_loss = 0.0;
-    if (c->cfg.dissim == DARC_LNCC && c->cfg.atlas_epochs > 0) {
+    if (patchwise(c->cfg.dissim) && c->cfg.atlas_epochs > 0) {
         std::vector<float> al(c->n);
         CK(cudaMemcpy(al.data(), c->aloss + (size_t)(c->cfg.atlas_epochs - 1) * c->n, sizeof(float) * c->n,
                       cudaMemcpyDeviceToHost));
@@ -644,6 +661,8 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     c->user = (cudaStream_t)stream;
     c->bmax = (cfg->subject_batch > 0) ? std::min(cfg->subject_batch, n) : n;
     rc = check_dims(c->bmax, D, H, W);
+    if (!rc && cfg->dissim == DARC_L1 && median_threads(n) == 0)
+        rc = fail(DARC_ERR_ARG, "the L1 (median) atlas supports at most 1600 subjects per cohort");
     if (rc) { delete c; return rc; }
     const Vol& v = c->vol;
     const int T = cfg->n_squarings;
@@ -681,7 +700,8 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     ALLOC(c->cpart, 2 * (size_t)centrality_blocks(v));
     ALLOC(c->cmetrics, 2);
     ALLOC(c->iota_dev, n);
-    if (cfg->dissim == DARC_LNCC) {
+    if (cfg->dissim == DARC_L1) ALLOC(c->Wcache, (size_t)v.V * n);
+    if (patchwise(cfg->dissim)) {
         ALLOC(c->astats, 2 * v.V);
         ALLOC(c->boxbuf, 3 * (size_t)v.V * bsub);
         ALLOC(c->Wimg, (size_t)v.V * c->bmax);
@@ -719,7 +739,7 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
         cudaMemsetAsync(c->cmetrics, 0, sizeof(double) * 2, s) == cudaSuccess &&
         image_mean_accumulate(images_dev, n, c->acc, v, s) == cudaSuccess &&
         finalize_mean(c->acc, 1.0 / n, c->A, v, s) == cudaSuccess &&
-        (cfg->dissim != DARC_LNCC || atlas_stats(c->A, c->astats, cfg->ncc_window / 2, v, c->boxbuf, s) == cudaSuccess) &&
+        (!patchwise(cfg->dissim) || atlas_stats(c->A, c->astats, cfg->ncc_window / 2, v, c->boxbuf, s) == cudaSuccess) &&
         cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) {
         cudaError_t e = cudaGetLastError();
@@ -825,6 +845,44 @@ int darc_propagate_labels(darc_cohort* c, const uint8_t* labels_dev, uint8_t* ou
     return end(c);
 }
 
+int darc_diffeo_report(darc_cohort* c, int first, int count, float* stats_host)
+{
+    if (!c || !stats_host) return fail(DARC_ERR_ARG, "null argument");
+    if (first < 0 || count < 1 || first + count > c->n) return fail(DARC_ERR_ARG, "subject range out of bounds");
+    const Vol& vol = c->vol;
+    if (!c->dpart) {
+        void* p = nullptr;
+        if (cudaMalloc(&p, sizeof(double) * 4 * (size_t)voxel_blocks(vol) * c->bmax) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DARC_ERR_OOM, "cudaMalloc failed");
+        }
+        c->allocs.push_back(p);
+        c->dpart = (double*)p;
+        if (cudaMalloc(&p, sizeof(float) * 4 * (size_t)c->bmax) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(DARC_ERR_OOM, "cudaMalloc failed");
+        }
+        c->allocs.push_back(p);
+        c->dstats = (float*)p;
+    }
+    int rc = begin(c);
+    if (rc) return rc;
+    const int T = c->cfg.n_squarings;
+    for (int f = first; f < first + count; f += c->bmax) {
+        const int cnt = std::min(c->bmax, first + count - f);
+        const float* vb = c->v + (size_t)f * 3 * vol.V;
+        float *up = nullptr, *um = nullptr;
+        CK(exp_forward_pingpong(vb, c->u_all, cnt, vol, T, 1.f, c->st, &up));
+        CK(exp_forward_pingpong(vb, c->gbuf, cnt, vol, T, -1.f, c->st, &um));
+        CK(compose(up, um, c->gT, cnt, vol, c->st));
+        CK(diffeo_stats(up, c->gT, c->dpart, c->dstats, cnt, vol, c->st));
+        CK(cudaMemcpyAsync(stats_host + 4 * (size_t)(f - first), c->dstats, sizeof(float) * 4 * cnt,
+                           cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    return end(c);
+}
+
 int darc_get_atlas(darc_cohort* c, float* out_dev)
 {
     if (!c || !out_dev) return fail(DARC_ERR_ARG, "null argument");
@@ -840,7 +898,7 @@ int darc_set_atlas(darc_cohort* c, const float* atlas_dev)
     int rc = begin(c);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->A, atlas_dev, sizeof(float) * c->vol.V, cudaMemcpyDeviceToDevice, c->st));
-    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
+    if (patchwise(c->cfg.dissim)) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
     return end(c);
 }
 
@@ -957,7 +1015,7 @@ int darc_load(darc_cohort** out, const char* path, const float* images_dev, void
             ok = std::fread(buf.data(), sizeof(float), F, fp) == F &&
                  cudaMemcpy(arr + i * F, buf.data(), sizeof(float) * F, cudaMemcpyHostToDevice) == cudaSuccess;
     std::fclose(fp);
-    if (ok && cfg.dissim == DARC_LNCC)
+    if (ok && patchwise(cfg.dissim))
         ok = atlas_stats(c->A, c->astats, cfg.ncc_window / 2, c->vol, c->boxbuf, c->st) == cudaSuccess &&
              cudaStreamSynchronize(c->st) == cudaSuccess;
     if (!ok) {
@@ -1001,6 +1059,7 @@ int darc_centrality_apply(darc_cohort* c, const float* sum_dev, long long n_tota
 int darc_atlas_partial(darc_cohort* c, double* acc_dev)
 {
     if (!c || !acc_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (c->cfg.dissim != DARC_MSE) return fail(DARC_ERR_ARG, "a summed atlas is the MSE atlas update");
     int rc = begin(c);
     if (rc) return rc;
     const Vol& vol = c->vol;
@@ -1018,10 +1077,11 @@ int darc_atlas_partial(darc_cohort* c, double* acc_dev)
 int darc_atlas_set_sum(darc_cohort* c, const double* acc_dev, long long n_total)
 {
     if (!c || !acc_dev || n_total < 1) return fail(DARC_ERR_ARG, "bad argument");
+    if (c->cfg.dissim != DARC_MSE) return fail(DARC_ERR_ARG, "a summed atlas is the MSE atlas update");
     int rc = begin(c);
     if (rc) return rc;
     CK(finalize_mean(acc_dev, 1.0 / (double)n_total, c->A, c->vol, c->st));
-    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
+    if (patchwise(c->cfg.dissim)) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
     return end(c);
 }
 
@@ -1034,7 +1094,7 @@ int darc_atlas_batches(darc_cohort* c)
 int darc_atlas_sgd_begin(darc_cohort* c, int sweep, unsigned long long rank_seed)
 {
     if (!c) return fail(DARC_ERR_ARG, "null cohort");
-    if (c->cfg.dissim != DARC_LNCC) return fail(DARC_ERR_ARG, "atlas SGD is the local-NCC atlas update");
+    if (!patchwise(c->cfg.dissim)) return fail(DARC_ERR_ARG, "atlas SGD is the patch-wise (NCC, SSIM) atlas update");
     int rc = begin(c);
     if (rc) return rc;
     const Vol& vol = c->vol;
@@ -1074,7 +1134,8 @@ int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, floa
     const int* subj = c->perm_dev + (size_t)epoch * c->n + b0;
     cudaStream_t s = c->st;
     CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));
-    CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps, c->coef, c->pL, nb, vol,
+    CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim),
+                         c->coef, c->pL, nb, vol,
                          c->boxbuf, s));
     CK(reduce_partials(c->pL, nb * box_blocks(vol), 1, 1.0, loss_dev, 1, 1, s));
     CK(atlas_sgd_backward(c->Wcache, subj, c->A, c->coef, r, c->gsh, c->gA, nb, vol, c->boxbuf, s));
@@ -1104,7 +1165,7 @@ int darc_atlas_sgd_end(darc_cohort* c)
     int rc = begin(c);
     if (rc) return rc;
     c->sgd_open = false;
-    if (c->cfg.dissim == DARC_LNCC) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
+    if (patchwise(c->cfg.dissim)) CK(atlas_stats(c->A, c->astats, c->cfg.ncc_window / 2, c->vol, c->boxbuf, c->st));
     return end(c);
 }
 
@@ -1225,8 +1286,33 @@ int darc_mse(const float* J_dev, const float* A_dev, float* loss_dev, float* gJ_
     const Vol v = make_vol(D, H, W);
     cudaStream_t s = (cudaStream_t)stream;
     double* part = (double*)work_dev;
-    CK(mse_partials(J_dev, A_dev, gJ_dev, part, B, v, s));
+    CK(mse_partials(J_dev, A_dev, gJ_dev, part, B, v, 0, s));
     CK(reduce_partials(part, voxel_blocks(v), 1, 1.0, loss_dev, 1, B, s));
+    return DARC_OK;
+}
+
+int darc_l1(const float* J_dev, const float* A_dev, float* loss_dev, float* gJ_dev, void* work_dev, int B, int D,
+            int H, int W, void* stream)
+{
+    if (!J_dev || !A_dev || !loss_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    const Vol v = make_vol(D, H, W);
+    cudaStream_t s = (cudaStream_t)stream;
+    double* part = (double*)work_dev;
+    CK(mse_partials(J_dev, A_dev, gJ_dev, part, B, v, 1, s));
+    CK(reduce_partials(part, voxel_blocks(v), 1, 1.0, loss_dev, 1, B, s));
+    return DARC_OK;
+}
+
+int darc_median(const float* X_dev, int n, int D, int H, int W, float* out_dev, void* stream)
+{
+    if (!X_dev || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (n < 1) return fail(DARC_ERR_ARG, "n must be >= 1");
+    if (median_threads(n) == 0) return fail(DARC_ERR_ARG, "n too large for the median kernel (at most 1600)");
+    int rc = check_dims(1, D, H, W);
+    if (rc) return rc;
+    CK(median(X_dev, n, (long long)D * H * W, out_dev, (cudaStream_t)stream));
     return DARC_OK;
 }
 
@@ -1238,8 +1324,14 @@ size_t darc_lncc_workspace(int B, int D, int H, int W)
            align256(sizeof(float) * 3 * (size_t)B * v.V);
 }
 
-int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, float* loss_dev, float* gJ_dev,
-              float* gA_dev, void* work_dev, int B, int D, int H, int W, void* stream)
+}  // extern "C"
+
+namespace {
+
+// the patch-wise operator (metric 0: local NCC, 1: SSIM) with the NCC
+// workspace layout
+int patch_op(int metric, const float* J_dev, const float* A_dev, int window, float eps, float* loss_dev,
+             float* gJ_dev, float* gA_dev, void* work_dev, int B, int D, int H, int W, void* stream)
 {
     if (!J_dev || !A_dev || !loss_dev || !work_dev) return fail(DARC_ERR_ARG, "null argument");
     int rc = check_dims(B, D, H, W);
@@ -1256,15 +1348,31 @@ int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, flo
     double* part = cv.take<double>(2 * (size_t)B * nblk_max(v));
     float* P = cv.take<float>(3 * (size_t)B * v.V);
     CK(atlas_stats(A_dev, stats, r, v, P, s));
-    CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 0, coef, part, B, v, P, s));
+    CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 0, metric, coef, part, B, v, P, s));
     CK(reduce_partials(part, box_blocks(v), 1, 1.0, loss_dev, 1, B, s));
     if (gJ_dev) CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 0, gJ_dev, B, v, P, s));
     if (gA_dev) {
-        CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 1, coef, part, B, v, P, s));
+        CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 1, metric, coef, part, B, v, P, s));
         CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 1, gAb, B, v, P, s));
         CK(sum_images(gAb, B, gA_dev, v, s));
     }
     return DARC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int darc_lncc(const float* J_dev, const float* A_dev, int window, float eps, float* loss_dev, float* gJ_dev,
+              float* gA_dev, void* work_dev, int B, int D, int H, int W, void* stream)
+{
+    return patch_op(0, J_dev, A_dev, window, eps, loss_dev, gJ_dev, gA_dev, work_dev, B, D, H, W, stream);
+}
+
+int darc_ssim(const float* J_dev, const float* A_dev, int window, float* loss_dev, float* gJ_dev, float* gA_dev,
+              void* work_dev, int B, int D, int H, int W, void* stream)
+{
+    return patch_op(1, J_dev, A_dev, window, 0.f, loss_dev, gJ_dev, gA_dev, work_dev, B, D, H, W, stream);
 }
 
 int darc_diffusion_reg(const float* u_dev, float* loss_dev, float* gu_dev, void* work_dev, int B, int D, int H,
@@ -1319,14 +1427,15 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     auto sq = [&](const float* src, float scale, float* dst) { return exp_square(src, scale, dst, B, v, s); };
     CK(exp_forward_plan(plan, v_dev, u_all, F, s0, sq));
     const float* uT = u_all + (size_t)plan.slot(T - 1) * F;
-    if (cfg->dissim == DARC_MSE) {
-        CK(mse_warp_reg(I_dev, v.V, A_dev, uT, cfg->lambda, gT, pL, B, v, s));
+    if (pointwise(cfg->dissim)) {
+        CK(mse_warp_reg(I_dev, v.V, A_dev, uT, cfg->lambda, gT, pL, B, v, cfg->dissim == DARC_L1, s));
         CK(reduce_partials(pL, voxel_blocks(v), 2, 1.0, energy_dev, 2, B, s));
     } else {
         const int r = cfg->ncc_window / 2;
         CK(atlas_stats(A_dev, stats, r, v, P, s));
         CK(warp(I_dev, v.V, uT, Wimg, B, v, s));
-        CK(lncc_forward(Wimg, nullptr, A_dev, stats, r, cfg->ncc_eps, 0, coef, pL, B, v, P, s));
+        CK(lncc_forward(Wimg, nullptr, A_dev, stats, r, cfg->ncc_eps, 0, patch_metric(cfg->dissim), coef, pL, B,
+                        v, P, s));
         CK(lncc_backward_warp_reg(Wimg, A_dev, coef, r, I_dev, v.V, uT, cfg->lambda, gT, pR, B, v, P, s));
         CK(reduce_partials(pL, box_blocks(v), 1, 1.0, energy_dev, 2, B, s));
         CK(reduce_partials(pR, box_blocks(v), 1, 1.0, energy_dev + 1, 2, B, s));
@@ -1414,6 +1523,16 @@ int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* ou
     int rc = check_dims(B, D, H, W);
     if (rc) return rc;
     CK(label_gather(labels_dev, u_dev, out_dev, B, make_vol(D, H, W), (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+int darc_compose(const float* a_dev, const float* b_dev, float* out_dev, int B, int D, int H, int W, void* stream)
+{
+    if (!a_dev || !b_dev || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (out_dev == a_dev || out_dev == b_dev) return fail(DARC_ERR_ARG, "out must not alias a or b");
+    int rc = check_dims(B, D, H, W);
+    if (rc) return rc;
+    CK(compose(a_dev, b_dev, out_dev, B, make_vol(D, H, W), (cudaStream_t)stream));
     return DARC_OK;
 }
 

@@ -140,4 +140,21 @@ __device__ __forceinline__ double block_sum(float x, double* sh /* >= 32 doubles
     return tot;
 }
 
+// minimum over the block (valid in thread 0)
+__device__ __forceinline__ double block_min(float x, double* sh /* >= 32 doubles */)
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    float m = x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) sh[tid >> 5] = m;
+    __syncthreads();
+    double r = 3.0e38;
+    if (tid == 0)
+        for (int k = 0; k < (nthr >> 5); ++k) r = fmin(r, sh[k]);
+    __syncthreads();
+    return r;
+}
+
 }  // namespace darc_impl

@@ -105,9 +105,17 @@ warp_backward_kernel(const float* __restrict__ I, size_t I_bstride, const float*
     }
 }
 
+// point-wise loss of d = W - A (Sec. "Dissimilarity metrics"): l1 = 0 -> d^2
+// with derivative 2 d; l1 = 1 -> |d| with the subgradient sign(d) (0 at 0)
+__device__ __forceinline__ float pw_loss(float d, int l1) { return l1 ? fabsf(d) : d * d; }
+__device__ __forceinline__ float pw_grad(float d, int l1)
+{
+    return l1 ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) : 2.f * d;
+}
+
 __global__ void __launch_bounds__(VT_THREADS)
 mse_kernel(const float* __restrict__ J, const float* __restrict__ A, float* __restrict__ gJ,
-           double* __restrict__ partials, Vol v, int nzt, float invV)
+           double* __restrict__ partials, Vol v, int nzt, float invV, int l1)
 {
     __shared__ double sh[32];
     const int x = blockIdx.x * VT_X + threadIdx.x;
@@ -121,8 +129,8 @@ mse_kernel(const float* __restrict__ J, const float* __restrict__ A, float* __re
             if (z >= v.D) break;
             const long long l = ((long long)z * v.H + y) * v.W + x;
             const float d = __ldg(Jb + l) - __ldg(A + l);
-            acc = fmaf(d * invV, d, acc);
-            if (gJ) gJ[(size_t)b * v.V + l] = 2.f * invV * d;
+            acc = fmaf(invV, pw_loss(d, l1), acc);
+            if (gJ) gJ[(size_t)b * v.V + l] = invV * pw_grad(d, l1);
         }
     }
     const double s = block_sum(acc, sh);
@@ -160,12 +168,13 @@ reg_kernel(const float* __restrict__ u, float* __restrict__ gu, double* __restri
         partials[(size_t)b * gridDim.x * gridDim.y * nzt + block_index_in_subject(zt)] = s;
 }
 
-// MSE subject step, fused: W = S(I, x + u_T), L = mean (W - A)^2,
-// gT = (2 (W - A)/V) dS(I)/dp + lambda dR/du_T; partials {L, R} per block.
+// Point-wise subject step, fused: W = S(I, x + u_T), L = mean l(W - A)
+// (MSE or L1), gT = (l'(W - A)/V) dS(I)/dp + lambda dR/du_T; partials {L, R}
+// per block.
 __global__ void __launch_bounds__(VT_THREADS)
 mse_warp_reg_kernel(const float* __restrict__ I, size_t I_bstride, const float* __restrict__ A,
                     const float* __restrict__ uT, float lambda, float* __restrict__ gT,
-                    double* __restrict__ partials, Vol v, int nzt, float invV, RegW rw)
+                    double* __restrict__ partials, Vol v, int nzt, float invV, RegW rw, int l1)
 {
     __shared__ double sh[32];
     const int x = blockIdx.x * VT_X + threadIdx.x;
@@ -184,8 +193,8 @@ mse_warp_reg_kernel(const float* __restrict__ I, size_t I_bstride, const float* 
             float dz, dy, dx;
             const float Wv = tri_grad(Ib, c, v, dz, dy, dx);
             const float d = Wv - __ldg(A + l);
-            accL = fmaf(d * invV, d, accL);
-            const float gW = 2.f * invV * d;
+            accL = fmaf(invV, pw_loss(d, l1), accL);
+            const float gW = invV * pw_grad(d, l1);
             float g[3];
             accR += reg_at(ub, v, z, y, x, l, rw, g);
             gb[l] = fmaf(gW, dz, lambda * g[0]);
@@ -229,6 +238,31 @@ label_gather_kernel(const uint8_t* __restrict__ lab, const float* __restrict__ u
     }
 }
 
+// det(I + grad u) at voxel (z, y, x): central differences inside, one-sided
+// on the faces
+__device__ __forceinline__ float jac_det_at(const float* __restrict__ ub, const Vol& v, int z, int y, int x)
+{
+    const int n[3] = {v.D, v.H, v.W};
+    const long long st[3] = {(long long)v.H * v.W, (long long)v.W, 1};
+    const int q[3] = {z, y, x};
+    const long long l = ((long long)z * v.H + y) * v.W + x;
+    float J[3][3];
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb) {
+        long long lo = l, hi = l;
+        float h;
+        if (q[bb] == 0) { hi = l + st[bb]; h = 1.f; }
+        else if (q[bb] == n[bb] - 1) { lo = l - st[bb]; h = 1.f; }
+        else { lo = l - st[bb]; hi = l + st[bb]; h = 2.f; }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            J[a][bb] = (a == bb ? 1.f : 0.f) + (__ldg(ub + a * v.V + hi) - __ldg(ub + a * v.V + lo)) / h;
+    }
+    return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
 __global__ void __launch_bounds__(VT_THREADS)
 jacobian_kernel(const float* __restrict__ u, float* __restrict__ det,
                 unsigned long long* __restrict__ count, Vol v, int nzt)
@@ -242,29 +276,11 @@ jacobian_kernel(const float* __restrict__ u, float* __restrict__ det,
     const float* ub = u + (size_t)b * 3 * v.V;
     unsigned int mine = 0;
     if (x < v.W && y < v.H) {
-        const int n[3] = {v.D, v.H, v.W};
-        const long long st[3] = {(long long)v.H * v.W, (long long)v.W, 1};
         for (int k = 0; k < VT_Z; ++k) {
             const int z = zt * VT_Z + k;
             if (z >= v.D) break;
-            const int q[3] = {z, y, x};
-            const long long l = ((long long)z * v.H + y) * v.W + x;
-            float J[3][3];
-#pragma unroll
-            for (int bb = 0; bb < 3; ++bb) {
-                long long lo = l, hi = l;
-                float h;
-                if (q[bb] == 0) { hi = l + st[bb]; h = 1.f; }
-                else if (q[bb] == n[bb] - 1) { lo = l - st[bb]; h = 1.f; }
-                else { lo = l - st[bb]; hi = l + st[bb]; h = 2.f; }
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    J[a][bb] = (a == bb ? 1.f : 0.f) + (__ldg(ub + a * v.V + hi) - __ldg(ub + a * v.V + lo)) / h;
-            }
-            const float d = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                            J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                            J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-            if (det) det[(size_t)b * v.V + l] = d;
+            const float d = jac_det_at(ub, v, z, y, x);
+            if (det) det[(size_t)b * v.V + ((long long)z * v.H + y) * v.W + x] = d;
             mine += (d <= 0.f);
         }
     }
@@ -272,6 +288,119 @@ jacobian_kernel(const float* __restrict__ u, float* __restrict__ det,
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0 && count && nneg)
         atomicAdd(count + b, (unsigned long long)nneg);
+}
+
+// voxel-wise lower median over n rows: out[l] = sorted_i X[i][l] at (n - 1)/2.
+// One thread per voxel; its n values sit in its own column of shared memory
+// (no barrier: a thread reads only what it wrote); the value whose rank
+// window [#less, #less-or-equal) holds (n - 1)/2 is selected, so the result
+// is one of the inputs, exactly.
+__global__ void median_kernel(const float* __restrict__ X, int n, long long V, float* __restrict__ out)
+{
+    extern __shared__ float col[];
+    const int t = threadIdx.x, bd = blockDim.x;
+    const long long l = blockIdx.x * (long long)bd + t;
+    if (l >= V) return;
+    for (int i = 0; i < n; ++i) col[i * bd + t] = __ldg(X + (size_t)i * V + l);
+    const int k = (n - 1) / 2;
+    float m = col[t];
+    for (int i = 0; i < n; ++i) {
+        const float xi = col[i * bd + t];
+        int lt = 0, le = 0;
+        for (int j = 0; j < n; ++j) {
+            const float xj = col[j * bd + t];
+            lt += xj < xi;
+            le += xj <= xi;
+        }
+        if (lt <= k && k < le) {
+            m = xi;
+            break;
+        }
+    }
+    out[l] = m;
+}
+
+// displacement of phi_b o phi_a: out(x) = a(x) + S(b, x + a(x))
+__global__ void __launch_bounds__(VT_THREADS)
+compose_kernel(const float* __restrict__ a, const float* __restrict__ bf, float* __restrict__ out, Vol v, int nzt)
+{
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    if (x >= v.W || y >= v.H) return;
+    const float* a0 = a + (size_t)b * 3 * v.V;
+    const float* b0 = bf + (size_t)b * 3 * v.V;
+    float* o0 = out + (size_t)b * 3 * v.V;
+    for (int k = 0; k < VT_Z; ++k) {
+        const int z = zt * VT_Z + k;
+        if (z >= v.D) break;
+        const long long l = ((long long)z * v.H + y) * v.W + x;
+        const float uz = __ldg(a0 + l), uy = __ldg(a0 + v.V + l), ux = __ldg(a0 + 2 * v.V + l);
+        const Cell c = make_cell(z, y, x, uz, uy, ux, v);
+        o0[l] = uz + tri(b0, c, v);
+        o0[l + v.V] = uy + tri(b0 + v.V, c, v);
+        o0[l + 2 * v.V] = ux + tri(b0 + 2 * v.V, c, v);
+    }
+}
+
+// per block: {voxels with det(I + grad u) <= 0, sum |r|, max |r|, min det}
+__global__ void __launch_bounds__(VT_THREADS)
+diffeo_stats_kernel(const float* __restrict__ u, const float* __restrict__ r, double* __restrict__ partials, Vol v,
+                    int nzt)
+{
+    __shared__ double sh[32];
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    const float* ub = u + (size_t)b * 3 * v.V;
+    const float* rb = r + (size_t)b * 3 * v.V;
+    float neg = 0.f, sum = 0.f, mx = 0.f, mn = 3.0e38f;
+    if (x < v.W && y < v.H) {
+        for (int k = 0; k < VT_Z; ++k) {
+            const int z = zt * VT_Z + k;
+            if (z >= v.D) break;
+            const long long l = ((long long)z * v.H + y) * v.W + x;
+            const float d = jac_det_at(ub, v, z, y, x);
+            const float e = sqrtf(rb[l] * rb[l] + rb[v.V + l] * rb[v.V + l] + rb[2 * v.V + l] * rb[2 * v.V + l]);
+            neg += (d <= 0.f);
+            sum += e;
+            mx = fmaxf(mx, e);
+            mn = fminf(mn, d);
+        }
+    }
+    const int nb = gridDim.x * gridDim.y * nzt;
+    const int blk = (blockIdx.z % nzt) * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x;
+    double* out = partials + ((size_t)b * nb + blk) * 4;
+    const double s0 = block_sum(neg, sh);
+    const double s1 = block_sum(sum, sh);
+    const double s2 = -block_min(-mx, sh);
+    const double s3 = block_min(mn, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        out[0] = s0;
+        out[1] = s1;
+        out[2] = s2;
+        out[3] = s3;
+    }
+}
+
+// stats[b] = {negative fraction, mean |r|, max |r|, min det} (fixed order)
+__global__ void diffeo_stats_finish_kernel(const double* __restrict__ partials, int nb, long long V,
+                                           float* __restrict__ stats)
+{
+    if (threadIdx.x != 0) return;
+    const int b = blockIdx.x;
+    double neg = 0.0, sum = 0.0, mx = 0.0, mn = 3.0e38;
+    for (int j = 0; j < nb; ++j) {
+        const double* p = partials + ((size_t)b * nb + j) * 4;
+        neg += p[0];
+        sum += p[1];
+        mx = fmax(mx, p[2]);
+        mn = fmin(mn, p[3]);
+    }
+    stats[4 * b + 0] = (float)(neg / (double)V);
+    stats[4 * b + 1] = (float)(sum / (double)V);
+    stats[4 * b + 2] = (float)mx;
+    stats[4 * b + 3] = (float)mn;
 }
 
 dim3 vgrid(int B, const Vol& v, int& nzt)
@@ -303,11 +432,11 @@ cudaError_t warp_backward(const float* I, size_t I_bstride, const float* u, cons
 }
 
 cudaError_t mse_partials(const float* J, const float* A, float* gJ, double* partials, int B,
-                         const Vol& v, cudaStream_t s)
+                         const Vol& v, int l1, cudaStream_t s)
 {
     int nzt;
     const dim3 g = vgrid(B, v, nzt);
-    mse_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(J, A, gJ, partials, v, nzt, (float)(1.0 / (double)v.V));
+    mse_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(J, A, gJ, partials, v, nzt, (float)(1.0 / (double)v.V), l1);
     return cudaGetLastError();
 }
 
@@ -322,13 +451,13 @@ cudaError_t reg_partials(const float* u, float* gu, double* partials, int B, con
 
 cudaError_t mse_warp_reg(const float* I, size_t I_bstride, const float* A, const float* uT,
                          float lambda, float* gT, double* partials, int B, const Vol& v,
-                         cudaStream_t s)
+                         int l1, cudaStream_t s)
 {
     int nzt;
     const dim3 g = vgrid(B, v, nzt);
     mse_warp_reg_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, A, uT, lambda, gT, partials, v,
                                                       nzt, (float)(1.0 / (double)v.V),
-                                                      reg_weights(v));
+                                                      reg_weights(v), l1);
     return cudaGetLastError();
 }
 
@@ -338,6 +467,46 @@ cudaError_t label_gather(const uint8_t* labels, const float* u, uint8_t* out, in
     int nzt;
     const dim3 g = vgrid(B, v, nzt);
     label_gather_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(labels, u, out, v, nzt);
+    return cudaGetLastError();
+}
+
+int median_threads(int n)
+{
+    int bd = 256;
+    while (bd > 32 && (size_t)n * bd * sizeof(float) > 48 * 1024) bd /= 2;
+    return (size_t)n * bd * sizeof(float) <= 200 * 1024 ? bd : 0;
+}
+
+cudaError_t median(const float* X, int n, long long V, float* out, cudaStream_t s)
+{
+    const int bd = median_threads(n);
+    if (bd == 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)n * bd * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    median_kernel<<<(unsigned)((V + bd - 1) / bd), bd, smem, s>>>(X, n, V, out);
+    return cudaGetLastError();
+}
+
+cudaError_t compose(const float* a, const float* b, float* out, int B, const Vol& v, cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    compose_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(a, b, out, v, nzt);
+    return cudaGetLastError();
+}
+
+cudaError_t diffeo_stats(const float* u, const float* r, double* partials, float* stats, int B, const Vol& v,
+                         cudaStream_t s)
+{
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    diffeo_stats_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(u, r, partials, v, nzt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    diffeo_stats_finish_kernel<<<B, 32, 0, s>>>(partials, voxel_blocks(v), v.V, stats);
     return cudaGetLastError();
 }
 

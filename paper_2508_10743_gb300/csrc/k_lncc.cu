@@ -1,10 +1,14 @@
-// k_lncc.cu -- local (windowed) NCC forward and adjoint (sm_103a).
+// k_lncc.cu -- patch-wise dissimilarities (local NCC, SSIM): forward and
+// adjoint (sm_103a).
 //
 // Patch-wise NCC (arXiv 2508.10743, Sec. "Dissimilarity metrics"), read as
 // the squared correlation over the w^3 window centred at each voxel, zero
 // padding outside the volume, normalised by N = w^3:
 //   P = S_JA - S_J S_A / N, sJ = S_JJ - S_J^2 / N, sA = S_AA - S_A^2 / N,
 //   cc = P^2 / (sJ sA + eps),  L = -1/V sum_x cc(x).
+// SSIM (same section) over the same windows and sums: mu = S/N, var and
+// cov from the second moments, ssim = (2 muJ muA + C1)(2 cov + C2) /
+// ((muJ^2 + muA^2 + C1)(varJ + varA + C2)), L = -1/V sum_x ssim(x).
 // The adjoint is again a box sum (the zero-padded box filter is
 // self-adjoint):  dL/dJ(y) = -1/V [Box(a) + 2 J(y) Box(b) + A(y) Box(g)]
 // with a = dcc/dS_J, b = dcc/dS_JJ, g = dcc/dS_JA (mirror for A).
@@ -179,6 +183,37 @@ __device__ __forceinline__ CCTerms cc_terms(float SJ, float SJJ, float SJA, floa
     return t;
 }
 
+// SSIM over the same window from the same five sums (Wang et al. 2004,
+// C1 = (0.01)^2, C2 = (0.03)^2 for intensities on [0, 1]), and its
+// derivatives wrt the sums of the differentiated image X (J, or A when
+// wrt_atlas): c0 = dssim/dS_X, c1 = dssim/dS_XX, c2 = dssim/dS_XY.
+__device__ __forceinline__ CCTerms ssim_terms(float SJ, float SJJ, float SJA, float SA, float SAA,
+                                              float invN, bool wrt_atlas)
+{
+    constexpr float C1 = 1.0e-4f, C2 = 9.0e-4f;
+    const float mJ = SJ * invN, mA = SA * invN;
+    const float vJ = SJJ * invN - mJ * mJ, vA = SAA * invN - mA * mA;
+    const float cJA = SJA * invN - mJ * mA;
+    const float a1 = fmaf(2.f * mJ, mA, C1), a2 = fmaf(2.f, cJA, C2);
+    const float b1 = mJ * mJ + mA * mA + C1, b2 = vJ + vA + C2;
+    const float ib1 = 1.f / b1, ib2 = 1.f / b2, ib = ib1 * ib2;
+    CCTerms t;
+    t.cc = a1 * a2 * ib;
+    const float mX = wrt_atlas ? mA : mJ, mY = wrt_atlas ? mJ : mA;
+    t.c0 = 2.f * invN * (mY * (a2 - a1) * ib - mX * t.cc * (ib1 - ib2));
+    t.c1 = -t.cc * invN * ib2;
+    t.c2 = 2.f * invN * a1 * ib;
+    return t;
+}
+
+// the patch-wise metric of a launch: 0 = local NCC, 1 = SSIM
+__device__ __forceinline__ CCTerms patch_terms(int metric, float SJ, float SJJ, float SJA, float SA, float SAA,
+                                               float invN, float eps, bool wrt_atlas)
+{
+    return metric ? ssim_terms(SJ, SJJ, SJA, SA, SAA, invN, wrt_atlas)
+                  : cc_terms(SJ, SJJ, SJA, SA, SAA, invN, eps, wrt_atlas);
+}
+
 struct FwdOp {
     static constexpr bool kReduces = true;
     const float* J;
@@ -190,7 +225,7 @@ struct FwdOp {
     int nblk;
     long long V;
     float invN, eps, negInvV;
-    int wrt_atlas;
+    int wrt_atlas, metric;
     __device__ const float* row(int b) const { return J + (size_t)(subj ? subj[b] : b) * V; }
     __device__ void load(int b, long long l, float* o) const
     {
@@ -201,8 +236,8 @@ struct FwdOp {
     }
     __device__ float emit(int b, int, int, int, long long l, const float* S) const
     {
-        const CCTerms t = cc_terms(S[0], S[1], S[2], __ldg(stats + l), __ldg(stats + V + l), invN,
-                                   eps, wrt_atlas != 0);
+        const CCTerms t = patch_terms(metric, S[0], S[1], S[2], __ldg(stats + l), __ldg(stats + V + l), invN,
+                                      eps, wrt_atlas != 0);
         float* cb = coef + (size_t)b * 3 * V;
         cb[l] = t.c0;
         cb[V + l] = t.c1;
@@ -316,6 +351,7 @@ struct AtlasFwdOp {
     int nblk;
     long long V;
     float invN, eps, negInvV;
+    int metric;
     __device__ void load(int b, long long l, float* o) const
     {
         o[0] = __ldg(J + (size_t)subj[b] * V + l) * __ldg(A + l);
@@ -323,8 +359,8 @@ struct AtlasFwdOp {
     __device__ float emit(int b, int, int, int, long long l, const float* S) const
     {
         const float* js = jstats + (size_t)subj[b] * 2 * V;
-        const CCTerms t = cc_terms(__ldg(js + l), __ldg(js + V + l), S[0], __ldg(astats + l),
-                                   __ldg(astats + V + l), invN, eps, true);
+        const CCTerms t = patch_terms(metric, __ldg(js + l), __ldg(js + V + l), S[0], __ldg(astats + l),
+                                      __ldg(astats + V + l), invN, eps, true);
         float* cb = coef + (size_t)b * 3 * V;
         cb[l] = t.c0;
         cb[V + l] = t.c1;
@@ -429,12 +465,12 @@ cudaError_t image_stats(const float* J, float* stats, int B, int r, const Vol& v
 }
 
 cudaError_t atlas_sgd_forward(const float* J, const float* jstats, const int* subj, const float* A,
-                              const float* astats, int r, float eps, float* coef, double* partials,
+                              const float* astats, int r, float eps, int metric, float* coef, double* partials,
                               int nb, const Vol& v, float* P, cudaStream_t s)
 {
     const int w = 2 * r + 1;
     AtlasFwdOp op{J, jstats, subj, A, astats, coef, partials, box_blocks(v), v.V,
-                  (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V)};
+                  (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V), metric};
     return launch_box<1>(op, nb, v, r, P, s);
 }
 
@@ -450,12 +486,12 @@ cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, 
 }
 
 cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const float* stats,
-                         int r, float eps, int wrt_atlas, float* coef, double* partials, int B,
+                         int r, float eps, int wrt_atlas, int metric, float* coef, double* partials, int B,
                          const Vol& v, float* P, cudaStream_t s)
 {
     const int w = 2 * r + 1;
     FwdOp op{J, subj, A, stats, coef, partials, box_blocks(v), v.V,
-             (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V), wrt_atlas};
+             (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V), wrt_atlas, metric};
     return launch_box<3>(op, B, v, r, P, s);
 }
 

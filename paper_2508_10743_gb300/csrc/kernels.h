@@ -31,16 +31,28 @@ cudaError_t warp_backward(const float* I, size_t I_bstride, const float* u, cons
                           float* gu, int B, const Vol& v, cudaStream_t s);
 // partials: double [B][nblk] laid out per subject, nblk = voxel_blocks(v)
 int voxel_blocks(const Vol& v);
+// l1 = 0: MSE (d^2, 2d); l1 = 1: L1 (|d|, sign d)
 cudaError_t mse_partials(const float* J, const float* A, float* gJ, double* partials, int B,
-                         const Vol& v, cudaStream_t s);
+                         const Vol& v, int l1, cudaStream_t s);
 cudaError_t reg_partials(const float* u, float* gu, double* partials, int B, const Vol& v,
                          cudaStream_t s);
-// fused MSE subject step: from u_T and I: W, MSE, its gradient through the
-// warp, plus lambda * the regulariser gradient -> gT; partials [B][nblk][2]
+// fused point-wise subject step (l1 = 0: MSE, 1: L1): from u_T and I: W,
+// the loss, its gradient through the warp, plus lambda * the regulariser
+// gradient -> gT; partials [B][nblk][2]
 cudaError_t mse_warp_reg(const float* I, size_t I_bstride, const float* A, const float* uT,
                          float lambda, float* gT, double* partials, int B, const Vol& v,
-                         cudaStream_t s);
+                         int l1, cudaStream_t s);
+// out[l] = lower median over the n rows of X [n][V]; median_threads(n) == 0:
+// n too large for the shared-memory columns (cudaErrorInvalidValue)
+int median_threads(int n);
+cudaError_t median(const float* X, int n, long long V, float* out, cudaStream_t s);
 cudaError_t label_gather(const uint8_t* labels, const float* u, uint8_t* out, int B, const Vol& v,
+                         cudaStream_t s);
+// displacement of phi_b o phi_a: out = a + S(b, x + a)  ([B][3][V])
+cudaError_t compose(const float* a, const float* b, float* out, int B, const Vol& v, cudaStream_t s);
+// stats[b][4] = {fraction det(I + grad u) <= 0, mean |r|, max |r|, min det};
+// partials: B * voxel_blocks(v) * 4 doubles
+cudaError_t diffeo_stats(const float* u, const float* r, double* partials, float* stats, int B, const Vol& v,
                          cudaStream_t s);
 cudaError_t jacobian_det(const float* u, float* det, unsigned long long* count, int B,
                          const Vol& v, cudaStream_t s);
@@ -152,11 +164,12 @@ cudaError_t downsample_image(const float* I, int D, int H, int W, float* Ih, int
 int box_blocks(const Vol& v);
 // window statistics of the atlas: stats[0] = Box(A), stats[1] = Box(A^2)
 cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, float* P, cudaStream_t s);
-// forward: box sums of J, J^2, J*A; cc; loss partials [B][nblk]; per-voxel
-// coefficients coef [B][3][V]: wrt_atlas = 0 -> dcc/d(S_J, S_JJ, S_JA),
-// 1 -> dcc/d(S_A, S_AA, S_JA).  J rows are J + subj[b]*V when subj != null.
+// forward: box sums of J, J^2, J*A; the patch metric m (metric 0: local
+// NCC cc, 1: SSIM); loss partials [B][nblk] of -m/V; per-voxel coefficients
+// coef [B][3][V]: wrt_atlas = 0 -> dm/d(S_J, S_JJ, S_JA), 1 -> dm/d(S_A,
+// S_AA, S_JA).  J rows are J + subj[b]*V when subj != null.
 cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const float* stats,
-                         int r, float eps, int wrt_atlas, float* coef, double* partials, int B,
+                         int r, float eps, int wrt_atlas, int metric, float* coef, double* partials, int B,
                          const Vol& v, float* P, cudaStream_t s);
 // backward: g = -1/V [Box(c0) + 2 X Box(c1) + Y Box(c2)], X = J (Y = A) or,
 // for wrt_atlas, X = A (Y = J); writes g [B][V]
@@ -174,7 +187,7 @@ cudaError_t image_stats(const float* J, float* stats, int B, int r, const Vol& v
 // atlas SGD for a mini-batch (rows subj[0..nb)): coefficients wrt the atlas,
 // loss partials [nb][nblk]
 cudaError_t atlas_sgd_forward(const float* J, const float* jstats, const int* subj, const float* A,
-                              const float* astats, int r, float eps, float* coef, double* partials,
+                              const float* astats, int r, float eps, int metric, float* coef, double* partials,
                               int nb, const Vol& v, float* P, cudaStream_t s);
 // gshared [V] = Box(sum a) + 2 A Box(sum b); gsubj [nb][V] = J_b Box(g_b)
 cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, const float* coef,

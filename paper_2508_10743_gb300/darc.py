@@ -103,6 +103,11 @@ _SIGS = {
     "darc_launch_count": (ctypes.c_longlong, [_vp]),
     "darc_exp_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
     "darc_gemm_bf16": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "darc_compose": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_l1": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_median": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
+    "darc_ssim": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_diffeo_report": (_i, [_vp, _i, _i, _vp]),
     "darc_conv3d": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _i, _vp, _vp, _i, _i, _f, _i, _i, _i, _i, _i, _vp]),
     "darc_conv3d_packed_bytes": (_sz, [_i, _i]),
     "darc_conv3d_pack_weights": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
@@ -344,6 +349,15 @@ class Cohort:
             _check(lib().darc_profile_read(self._h, kid, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
             out[name] = (ms.value, n.value, by.value)
         return out
+
+    def diffeo_report(self, first: int = 0, count: Optional[int] = None):
+        """Per subject: {neg_jacobian_fraction, ic_mean, ic_max, min_det} of
+        Exp(v) and Exp(-v) o Exp(v) (darc_diffeo_report)."""
+        count = self.n - first if count is None else count
+        out = (ctypes.c_float * (4 * count))()
+        _check(lib().darc_diffeo_report(self._h, first, count, ctypes.cast(out, ctypes.c_void_p)))
+        keys = ("neg_jacobian_fraction", "ic_mean", "ic_max", "min_det")
+        return [{k: out[4 * i + j] for j, k in enumerate(keys)} for i in range(count)]
 
     def launch_count(self) -> int:
         return int(lib().darc_launch_count(self._h))
@@ -653,6 +667,44 @@ def lncc(J: torch.Tensor, A: torch.Tensor, window: int, eps: float = 1e-5, grad_
     return loss, gJ, gA
 
 
+def l1(J: torch.Tensor, A: torch.Tensor, want_grad: bool = True):
+    """L1 dissimilarity per subject (darc_l1): (loss [B], dL/dJ or None)."""
+    _need(J, "J")
+    _need(A, "A")
+    B = J.shape[0]
+    D, H, W = _dims(J)
+    loss = torch.empty(B, dtype=torch.float32, device=J.device)
+    gJ = torch.empty_like(J) if want_grad else None
+    work = _work(lib().darc_loss_workspace(B, D, H, W), J.device)
+    _check(lib().darc_l1(_ptr(J), _ptr(A), _ptr(loss), _ptr(gJ), _ptr(work), B, D, H, W, _stream()))
+    return loss, gJ
+
+
+def median(X: torch.Tensor) -> torch.Tensor:
+    """Voxel-wise lower median over the first axis (darc_median): X [n, D, H, W]."""
+    _need(X, "X")
+    n = X.shape[0]
+    D, H, W = _dims(X)
+    out = torch.empty((D, H, W), dtype=torch.float32, device=X.device)
+    _check(lib().darc_median(_ptr(X), n, D, H, W, _ptr(out), _stream()))
+    return out
+
+
+def ssim(J: torch.Tensor, A: torch.Tensor, window: int, grad_J: bool = True, grad_A: bool = False):
+    """SSIM dissimilarity -mean ssim per subject (darc_ssim): (loss, dL/dJ, sum_b dL/dA)."""
+    _need(J, "J")
+    _need(A, "A")
+    B = J.shape[0]
+    D, H, W = _dims(J)
+    loss = torch.empty(B, dtype=torch.float32, device=J.device)
+    gJ = torch.empty_like(J) if grad_J else None
+    gA = torch.empty_like(A) if grad_A else None
+    work = _work(lib().darc_lncc_workspace(B, D, H, W), J.device)
+    _check(lib().darc_ssim(_ptr(J), _ptr(A), window, _ptr(loss), _ptr(gJ), _ptr(gA), _ptr(work),
+                           B, D, H, W, _stream()))
+    return loss, gJ, gA
+
+
 def diffusion_reg(u: torch.Tensor, want_grad: bool = True):
     _need(u, "u")
     B = u.shape[0]
@@ -715,6 +767,17 @@ def label_gather(labels: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
     D, H, W = _dims(u)
     out = torch.empty((B, D, H, W), dtype=torch.uint8, device=u.device)
     _check(lib().darc_label_gather(_ptr(labels), _ptr(u), _ptr(out), B, D, H, W, _stream()))
+    return out
+
+
+def compose(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """Displacement of phi_b o phi_a: a + S(b, x + a), fields [B, 3, D, H, W]."""
+    _need(a, "a")
+    _need(b, "b")
+    B = a.shape[0]
+    D, H, W = _dims(a)
+    out = torch.empty_like(a)
+    _check(lib().darc_compose(_ptr(a), _ptr(b), _ptr(out), B, D, H, W, _stream()))
     return out
 
 

@@ -3,8 +3,11 @@
 Eq. 3 updates each subject against the frozen atlas independently, so the
 subject updates stay on the rank that holds the subject.  Only two steps need
 the whole cohort: the centrality activation (the mean velocity over all
-subjects) and the atlas re-estimate (the mean warped image for MSE; for local
-NCC the atlas gradient of every mini-batch).  ``ShardedSweep`` runs a sweep
+subjects) and the atlas re-estimate (the mean warped image for MSE; for the
+patch-wise metrics, local NCC and SSIM, the atlas gradient of every
+mini-batch).  The L1 atlas, a voxel-wise median over all subjects, needs
+every subject's warped value at each voxel (an all-to-all by spatial slab)
+and is not sharded.  ``ShardedSweep`` runs a sweep
 with one sum all-reduce at each of those points and nothing else crosses
 ranks.
 
@@ -67,6 +70,8 @@ class ShardedSweep:
 
     def update_atlas(self, sweep: int) -> dict:
         out = self.centrality()
+        if self.cfg.dissim == configs.L1:
+            raise NotImplementedError("the L1 (median) atlas is not sharded; run the cohort in one process")
         if self.cfg.dissim == configs.MSE:
             acc = self._allreduce(self._sum_local([s.atlas_partial() for s in self.shards]))
             for s in self.shards:

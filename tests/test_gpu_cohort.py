@@ -100,6 +100,49 @@ def test_sweeps_match_the_oracle_mse():
     assert np.abs(np64(c.atlas()) - st.A).max() <= 1e-3 * np.abs(st.A).max()
 
 
+def test_sweeps_match_the_oracle_l1():
+    """L1 subject steps and the median atlas (Sec. "Dissimilarity metrics")."""
+    shape, n = (12, 16, 34), 5
+    co = cohort_images(n, shape, 13)
+    cfg = configs.DarcConfig(dissim=configs.L1, n_squarings=6, lam=0.1, inner_steps=2)
+    c = darc.Cohort(co.images.to(DEV).contiguous(), cfg)
+    st = oracle.State(np64(co.images))
+    for sweep in range(2):
+        gs = c.sweep()
+        os_ = oracle.sweep(st, _ocfg(cfg))
+        assert gs["centrality_after"] < 1e-6
+        assert abs(gs["loss_data"] - os_["loss_data"]) <= 1e-3 * os_["loss_data"]
+    v = np.stack([np64(c.velocity(i)) for i in range(n)])
+    assert np.mean(np.abs(v - st.v) <= 1e-3) > 0.99
+    # the median picks one subject's warped value per voxel: the atlases agree
+    # wherever the two middle candidates are not within rounding of each other
+    assert np.mean(np.abs(np64(c.atlas()) - st.A) <= 1e-3) > 0.99
+
+
+def test_ssim_atlas_update_matches_oracle_sgd():
+    shape, n = (12, 18, 33), 5
+    co = cohort_images(n, shape, 14)
+    cfg = configs.DarcConfig(dissim=configs.SSIM, ncc_window=5, n_squarings=7, atlas_epochs=3,
+                             atlas_batch=2, seed=12)
+    c = darc.Cohort(co.images.to(DEV).contiguous(), cfg)
+    v = [synth.random_field(shape, 3.0, 1.5, 310 + i) for i in range(n)]
+    for i in range(n):
+        c.set_velocity(i, v[i].to(DEV).contiguous())
+    A0 = np64(c.atlas())
+    stats = c.update_atlas()
+    vv = np.ascontiguousarray(np.stack([np64(x) for x in v]))
+    oracle.centrality(vv)
+    A_ref, loss_ref = oracle.atlas_sgd(np64(co.images), vv, A0, _ocfg(cfg), sweep=0)
+    A = np64(c.atlas())
+    step_ref = A_ref - A0
+    agree = np.abs((A - A0) - step_ref) <= 0.05 * np.abs(step_ref).max()
+    assert agree.mean() > 0.99
+    assert abs(stats["atlas_loss"] - loss_ref) <= 1e-3 * abs(loss_ref)
+    # one subject step with SSIM from the same state
+    losses = c.subject_step(0, n, 1, want_loss=True)
+    assert all(np.isfinite(losses))
+
+
 def test_ncc_atlas_update_matches_oracle_sgd():
     shape, n = (12, 18, 33), 5
     co = cohort_images(n, shape, 4)
@@ -194,6 +237,43 @@ def test_subject_batches_give_the_same_result():
     # float atomics in the adjoint make bitwise equality too strict; Adam may
     # flip the rare step of a near-zero gradient
     assert float(((out[0] - out[1]).abs() <= 1e-4).float().mean()) > 0.99
+
+
+def test_diffeo_report_matches_oracle():
+    """Folding fraction, Exp(-v) o Exp(v) inverse-consistency error and min
+    det per subject; the third subject's field is large enough to fold."""
+    shape, n, T = (12, 14, 16), 3, 7
+    co = cohort_images(n, shape, 10)
+    imgs = co.images.to(DEV).contiguous()
+    c = darc.Cohort(imgs, configs.DarcConfig(dissim=configs.MSE, n_squarings=T))
+    vs = [synth.random_field(shape, 2.0, d, 140 + i) for i, d in enumerate((1.0, 3.0, 9.0))]
+    for i, v in enumerate(vs):
+        c.set_velocity(i, v.to(DEV).contiguous())
+    rep = c.diffeo_report()
+    V = float(np.prod(shape))
+    def lip(u):                                  # max |finite difference| of a field
+        return max(np.abs(np.diff(u, axis=a)).max() for a in (1, 2, 3))
+
+    for i, v in enumerate(vs):
+        ref = oracle.diffeo_report(np64(v), T)
+        got = rep[i]
+        up, um = oracle.exp(np64(v), T)[-1], oracle.exp(np64(v), T, sign=-1.0)[-1]
+        # Exp on the GPU is within 1e-4 max|u| of the oracle (test_gpu_ops);
+        # r = u+ + S(u-, x + u+) moves by at most du+ (1 + Lip(u-)) + du-
+        du_p, du_m = 1e-4 * np.abs(up).max(), 1e-4 * np.abs(um).max()
+        r_tol = du_p * (1.0 + lip(um)) + du_m + 1e-6
+        assert abs(got["ic_mean"] - ref[1]) <= r_tol
+        assert abs(got["ic_max"] - ref[2]) <= r_tol
+        # det of central differences: each entry moves by <= du+, a 3x3 det by <= 6 du+ (1 + Lip)^2
+        d_tol = 6.0 * du_p * (1.0 + lip(up)) ** 2 + 1e-6
+        assert abs(got["min_det"] - ref[3]) <= d_tol
+        det = oracle.jacobian_det(up)
+        near = float(np.sum(np.abs(det) <= d_tol)) / V     # fold decisions can differ only there
+        assert abs(got["neg_jacobian_fraction"] - ref[0]) <= near + 1e-7
+    assert rep[0]["neg_jacobian_fraction"] == 0.0 and rep[2]["neg_jacobian_fraction"] > 0.0
+    # the report leaves the cohort's state alone
+    for i, v in enumerate(vs):
+        assert torch.equal(c.velocity(i).cpu(), v)
 
 
 def test_checkpoint_stride_gives_the_same_sweep():

@@ -145,7 +145,45 @@ def test_lncc(shape, w):
     assert rel_l2(np64(gA), gA_ref) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("dissim,w,T", [(configs.MSE, 9, 6), (configs.LNCC, 5, 7), (configs.LNCC, 9, 7)])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("w", [3, 7])
+def test_ssim(shape, w):
+    J = image(shape, 81, B=2)
+    A = (0.6 * image(shape, 81)[0] + 0.4 * image(shape, 86)[0]).contiguous()
+    loss, gJ, gA = darc.ssim(J.to(DEV), A.to(DEV), w, grad_J=True, grad_A=True)
+    gA_ref = np.zeros(shape)
+    for b in range(2):
+        L, rgJ, rgA = oracle.ssim(np64(J[b]), np64(A), w, with_grad=True)
+        assert abs(float(loss[b]) - L) <= FWD_TOL * abs(L)
+        assert rel_l2(np64(gJ[b]), rgJ) <= GRAD_TOL
+        gA_ref += rgA
+    assert rel_l2(np64(gA), gA_ref) <= GRAD_TOL
+
+
+def test_l1():
+    shape = (13, 17, 33)
+    J = image(shape, 82, B=2)
+    A = (0.5 * image(shape, 82)[0] + 0.5 * image(shape, 87)[0]).contiguous()
+    loss, gJ = darc.l1(J.to(DEV), A.to(DEV))
+    for b in range(2):
+        L, rgJ, _ = oracle.l1(np64(J[b]), np64(A), with_grad=True)
+        assert abs(float(loss[b]) - L) <= FWD_TOL * L
+        # the same float32 inputs on both sides: every sign decision is exact
+        assert np.abs(np64(gJ[b]) - rgJ).max() <= 1e-7 * np.abs(rgJ).max()
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 32, 33, 64])
+def test_median_is_exact(n):
+    g = torch.Generator().manual_seed(n)
+    X = torch.rand(n, 9, 10, 37, generator=g)
+    X[:, 0, 0, :5] = 0.25                        # ties
+    got = darc.median(X.to(DEV)).cpu()
+    ref = oracle.median(np64(X))
+    assert np.array_equal(got.double().numpy(), ref)
+
+
+@pytest.mark.parametrize("dissim,w,T", [(configs.MSE, 9, 6), (configs.LNCC, 5, 7), (configs.LNCC, 9, 7),
+                                        (configs.L1, 9, 6), (configs.SSIM, 5, 7)])
 def test_subject_gradient(dissim, w, T):
     shape = (18, 21, 35)
     I, A = image(shape, 90, B=2), image(shape, 95)[0].contiguous()
@@ -175,6 +213,15 @@ def test_subject_gradient_with_checkpointed_squarings(stride):
         E, parts, g = oracle.subject_energy(np64(I[b]), np64(A), np64(v[b]), ocfg)
         assert abs(float(energy[b, 0]) - parts[0]) <= FWD_TOL * abs(parts[0])
         assert rel_l2(np64(gv[b]), g) <= GRAD_TOL
+
+
+def test_compose_matches_oracle():
+    shape = (11, 13, 35)
+    a, b = field(shape, 120, max_disp=2.5, B=2), field(shape, 130, max_disp=3.5, B=2)
+    out = darc.compose(a.to(DEV), b.to(DEV))
+    for i in range(2):
+        ref = oracle.compose(np64(a[i]), np64(b[i]))
+        assert np.abs(np64(out[i]) - ref).max() <= FWD_TOL * np.abs(ref).max()
 
 
 def test_adam_step():
