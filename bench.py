@@ -19,6 +19,7 @@ host cores (bounded sample, the only other place this script runs oracle/).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -41,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default="brain")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--checkpoint-stride", type=int, default=0,
+                    help="keep every k-th squaring field and recompute the rest (0: keep all)")
     return ap.parse_args()
 
 
@@ -196,7 +199,7 @@ def main():
     # ---- workload: this rank's cohort (subjects are the units; weak scaling) ----
     co = synth.make_cohort(wl.n, wl.shape, wl.seed + 7919 * rank, device=dev, keep_disp=False, **wl.gen)
     images = co.images.contiguous()
-    cfg = wl.config
+    cfg = dataclasses.replace(wl.config, checkpoint_stride=args.checkpoint_stride)
     c = darc.Cohort(images, cfg)
     for i in range(wl.n):
         c.set_velocity(i, (-co.w[i]).contiguous())
@@ -308,7 +311,7 @@ def main():
         "config": {"workload": wl.name, "subjects_per_gpu": wl.n, "shape": list(wl.shape),
                    "dissimilarity": "local NCC %d^3" % cfg.ncc_window, "squarings": cfg.n_squarings,
                    "inner_steps": cfg.inner_steps, "atlas_epochs": cfg.atlas_epochs,
-                   "atlas_batch": cfg.atlas_batch,
+                   "atlas_batch": cfg.atlas_batch, "checkpoint_stride": cfg.checkpoint_stride,
                    "parallelism": (f"{wl.n * world} subjects sharded over {world} GPUs, all-reduce at centrality and "
                                    f"per atlas step" if world > 1 else "one GPU"),
                    "l2": "inputs larger than L2 (state %.1f GB per GPU)" % (wl.n * wl.voxels * 4 * 10 / 1e9),

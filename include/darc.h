@@ -145,6 +145,30 @@ int darc_propagate_labels(darc_cohort* c, const uint8_t* atlas_labels_dev, uint8
  * Errors: ARG, OOM, CUDA. */
 int darc_diffeo_report(darc_cohort* c, int first, int count, float* stats_host);
 
+/* PCA shape model (Sec. "Shape synthesis"): the principal components of
+ * the cohort's current velocities, from the eigenpairs of the n x n Gram
+ * matrix of the centred velocities (Jacobi rotations on the host).
+ * eigvals_host double [n]: the eigenvalues lambda_k of the sample
+ * covariance (1/(n - 1)), descending (at most n - 1 are nonzero);
+ * weights_host (nullable) double [n][n]: row k = the subject weights e_k of
+ * mode k, U_k = sum_i e_k[i] (v_i - mean) / sqrt((n - 1) lambda_k), signed so
+ * that its largest-magnitude entry is positive.  Kept in the cohort for
+ * darc_shape_sample.  Waits for its work.  Errors: ARG, OOM, CUDA. */
+int darc_shape_pca(darc_cohort* c, double* eigvals_host, double* weights_host);
+
+/* The host eigensolver behind darc_shape_pca: a_host [n][n] symmetric ->
+ * mu_host [n] descending, e_host [n][n] (row k the unit eigenvector of
+ * mu_k, largest-magnitude entry positive).  Host memory only; needs no GPU.
+ * Errors: ARG. */
+int darc_sym_eigen(const double* a_host, int n, double* mu_host, double* e_host);
+
+/* New velocities v_out_dev [m][3][V] = mean + sum_{j<p} sqrt(lambda_j)
+ * z_host[k][j] U_j (Sec. "Shape synthesis", alpha_j ~ N(0, lambda_j) drawn
+ * by the caller as standard normal z_host [m][p]); phi_new = Exp(v_out).
+ * Requires darc_shape_pca; 0 <= p <= n - 1.  Waits for its work.
+ * Errors: ARG, CUDA. */
+int darc_shape_sample(darc_cohort* c, const double* z_host, int m, int p, float* v_out_dev);
+
 /* Copies of the state.  Velocity and atlas layouts as above.  set_velocity
  * zeroes subject i's Adam moments and step count (a warm start).
  * set_atlas replaces A (and its NCC window statistics).  Errors: ARG, CUDA. */
@@ -352,6 +376,13 @@ int darc_atlas_mean(const float* I_dev, const float* v_dev, float* A_dev, void* 
  * out[b](x) = labels[r(x + u[b](x))].  Errors: ARG, CUDA. */
 int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* out_dev, int B,
                       int D, int H, int W, void* stream);
+
+/* Mesh vertices moved by a forward map (Sec. "Shape synthesis"): out_dev
+ * [P][3] = pts_dev[p] + S(u_dev, pts_dev[p]) for points in (z, y, x) voxel
+ * coordinates and a displacement u_dev [3][D][H][W] (trilinear, border
+ * padded).  Errors: ARG, CUDA. */
+int darc_warp_points(const float* u_dev, int D, int H, int W, const float* pts_dev, long long P, float* out_dev,
+                     void* stream);
 
 /* Composition of two maps given as displacements (Sec. "Diffeomorphisms"):
  * out[b](x) = a[b](x) + S(b_dev[b], x + a[b](x)), the displacement of

@@ -9,6 +9,7 @@
 #include "../../include/darc.h"
 #include "kernels.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -287,6 +288,10 @@ struct darc_cohort {
     std::map<std::pair<int, int>, long long> graph_kernels;     // kernels per replay of each graph
     double* dpart = nullptr;                   // diffeomorphism report: block partials (allocated on first use)
     float* dstats = nullptr;                   //   and per-subject results
+    float* pca_mean = nullptr;                 // PCA shape model (allocated on first use): mean velocity [3V],
+    double* pca_gram = nullptr;                //   Gram partials and matrix, sampling coefficients
+    float* pca_coef = nullptr;
+    std::vector<double> pca_mu, pca_e;         //   Gram eigenvalues (descending), eigenvectors [n][n] by row
     std::map<std::pair<int, int>, int> seen;
     // sharded atlas SGD state
     int sgd_k = 0;
@@ -594,6 +599,64 @@ int update_atlas_body(darc_cohort* c)
     return DARC_OK;
 }
 
+// Eigenpairs of a symmetric n x n matrix by cyclic Jacobi rotations (Jacobi
+// 1846; Golub & Van Loan, Matrix Computations, Sec. 8.5): each rotation
+// zeroes one off-diagonal pair; sweeps run until the off-diagonal mass is
+// below 1e-30 of the total.  On return mu[k] (descending) and e[k][i] (row k
+// an eigenvector), each eigenvector signed so that its entry of largest
+// magnitude (the first such) is positive.
+void sym_eigen(std::vector<double> a, int n, std::vector<double>& mu, std::vector<double>& e)
+{
+    std::vector<double> V((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    auto A = [&](int i, int j) -> double& { return a[(size_t)i * n + j]; };
+    double total = 0.0;
+    for (double x : a) total += x * x;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                if (i != j) off += A(i, j) * A(i, j);
+        if (off <= 1e-30 * total || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (A(p, q) == 0.0) continue;
+                const double theta = (A(q, q) - A(p, p)) / (2.0 * A(p, q));
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+                for (int k = 0; k < n; ++k) {          // columns p, q
+                    const double akp = A(k, p), akq = A(k, q);
+                    A(k, p) = cs * akp - sn * akq;
+                    A(k, q) = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < n; ++k) {          // rows p, q
+                    const double apk = A(p, k), aqk = A(q, k);
+                    A(p, k) = cs * apk - sn * aqk;
+                    A(q, k) = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < n; ++k) {          // eigenvectors are the columns of V
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = cs * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return A(x, x) > A(y, y); });
+    mu.assign(n, 0.0);
+    e.assign((size_t)n * n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        const int col = order[k];
+        mu[k] = A(col, col);
+        int big = 0;
+        for (int i = 1; i < n; ++i)
+            if (std::fabs(V[(size_t)i * n + col]) > std::fabs(V[(size_t)big * n + col])) big = i;
+        const double sg = V[(size_t)big * n + col] < 0 ? -1.0 : 1.0;
+        for (int i = 0; i < n; ++i) e[(size_t)k * n + i] = sg * V[(size_t)i * n + col];
+    }
+}
+
 int fill_atlas_stats(darc_cohort* c, darc_sweep_stats* stats)
 {
     double m[2] = {0, 0};
@@ -879,6 +942,80 @@ int darc_diffeo_report(darc_cohort* c, int first, int count, float* stats_host)
         CK(cudaMemcpyAsync(stats_host + 4 * (size_t)(f - first), c->dstats, sizeof(float) * 4 * cnt,
                            cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
+    }
+    return end(c);
+}
+
+int darc_shape_pca(darc_cohort* c, double* eigvals_host, double* weights_host)
+{
+    if (!c || !eigvals_host) return fail(DARC_ERR_ARG, "null argument");
+    const int n = c->n;
+    if (n < 2) return fail(DARC_ERR_ARG, "PCA needs at least two subjects");
+    const long long M = 3 * c->vol.V;
+    if (!c->pca_mean) {
+        void* p = nullptr;
+        const size_t bytes[3] = {sizeof(float) * (size_t)M,
+                                 sizeof(double) * ((size_t)gram_splits(n) + 1) * n * n,
+                                 sizeof(float) * 8 * (size_t)n};
+        void** dst[3] = {(void**)&c->pca_mean, (void**)&c->pca_gram, (void**)&c->pca_coef};
+        for (int k = 0; k < 3; ++k) {
+            if (cudaMalloc(&p, bytes[k]) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(DARC_ERR_OOM, "cudaMalloc failed");
+            }
+            c->allocs.push_back(p);
+            *dst[k] = p;
+        }
+    }
+    int rc = begin(c);
+    if (rc) return rc;
+    double* G = c->pca_gram + (size_t)gram_splits(n) * n * n;
+    CK(field_mean(c->v, n, M, c->pca_mean, c->st));
+    CK(gram(c->v, c->pca_mean, n, M, c->pca_gram, G, c->st));
+    std::vector<double> Gh((size_t)n * n);
+    CK(cudaMemcpyAsync(Gh.data(), G, sizeof(double) * n * n, cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    sym_eigen(Gh, n, c->pca_mu, c->pca_e);
+    for (int k = 0; k < n; ++k) eigvals_host[k] = std::max(c->pca_mu[k], 0.0) / (double)(n - 1);
+    if (weights_host) std::memcpy(weights_host, c->pca_e.data(), sizeof(double) * n * n);
+    return end(c);
+}
+
+int darc_sym_eigen(const double* a_host, int n, double* mu_host, double* e_host)
+{
+    if (!a_host || !mu_host || !e_host) return fail(DARC_ERR_ARG, "null argument");
+    if (n < 1 || n > 4096) return fail(DARC_ERR_ARG, "n must be 1..4096");
+    std::vector<double> mu, e;
+    sym_eigen(std::vector<double>(a_host, a_host + (size_t)n * n), n, mu, e);
+    std::memcpy(mu_host, mu.data(), sizeof(double) * n);
+    std::memcpy(e_host, e.data(), sizeof(double) * (size_t)n * n);
+    return DARC_OK;
+}
+
+int darc_shape_sample(darc_cohort* c, const double* z_host, int m, int p, float* v_out_dev)
+{
+    if (!c || !z_host || !v_out_dev) return fail(DARC_ERR_ARG, "null argument");
+    const int n = c->n;
+    if (c->pca_mu.empty()) return fail(DARC_ERR_ARG, "call darc_shape_pca first");
+    if (m < 1 || p < 0 || p > n - 1) return fail(DARC_ERR_ARG, "need m >= 1 and 0 <= p <= n - 1");
+    const long long M = 3 * c->vol.V;
+    int rc = begin(c);
+    if (rc) return rc;
+    // v_new = mean + sum_j sqrt(lambda_j) z_j U_j with U_j = Xc^T e_j / sqrt(mu_j) and
+    // lambda_j = mu_j / (n - 1): the weight of subject i is sum_j e_j[i] z_j / sqrt(n - 1)
+    std::vector<float> coef(8 * (size_t)n);
+    for (int k0 = 0; k0 < m; k0 += 8) {
+        const int mk = std::min(8, m - k0);
+        for (int k = 0; k < mk; ++k)
+            for (int i = 0; i < n; ++i) {
+                double w = 0.0;
+                for (int j = 0; j < p; ++j)
+                    if (c->pca_mu[j] > 0.0) w += c->pca_e[(size_t)j * n + i] * z_host[(size_t)(k0 + k) * p + j];
+                coef[(size_t)k * n + i] = (float)(w / std::sqrt((double)(n - 1)));
+            }
+        CK(cudaMemcpyAsync(c->pca_coef, coef.data(), sizeof(float) * mk * n, cudaMemcpyHostToDevice, c->st));
+        CK(combine_fields(c->v, c->pca_mean, n, M, c->pca_coef, mk, v_out_dev + (size_t)k0 * M, c->st));
+        CK(cudaStreamSynchronize(c->st));                 // coef is reused by the next group
     }
     return end(c);
 }
@@ -1523,6 +1660,18 @@ int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* ou
     int rc = check_dims(B, D, H, W);
     if (rc) return rc;
     CK(label_gather(labels_dev, u_dev, out_dev, B, make_vol(D, H, W), (cudaStream_t)stream));
+    return DARC_OK;
+}
+
+int darc_warp_points(const float* u_dev, int D, int H, int W, const float* pts_dev, long long P, float* out_dev,
+                     void* stream)
+{
+    if (!u_dev || !pts_dev || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    if (P < 0) return fail(DARC_ERR_ARG, "negative point count");
+    int rc = check_dims(1, D, H, W);
+    if (rc) return rc;
+    if (P == 0) return DARC_OK;
+    CK(warp_points(u_dev, make_vol(D, H, W), pts_dev, P, out_dev, (cudaStream_t)stream));
     return DARC_OK;
 }
 

@@ -48,6 +48,17 @@ int median_threads(int n);
 cudaError_t median(const float* X, int n, long long V, float* out, cudaStream_t s);
 cudaError_t label_gather(const uint8_t* labels, const float* u, uint8_t* out, int B, const Vol& v,
                          cudaStream_t s);
+// ---- PCA shape synthesis (k_shape.cu) ----
+// mean[l] = 1/n sum_i v[i][l], v [n][M]
+cudaError_t field_mean(const float* v, int n, long long M, float* mean, cudaStream_t s);
+// G [n][n] = centred Gram matrix of the rows of v; partial: gram_splits(n) * n * n doubles
+int gram_splits(int n);
+cudaError_t gram(const float* v, const float* mean, int n, long long M, double* partial, double* G, cudaStream_t s);
+// out[k] = mean + sum_i coef[k][i] (v_i - mean), k < m <= 8, coef float [m][n]
+cudaError_t combine_fields(const float* v, const float* mean, int n, long long M, const float* coef, int m,
+                           float* out, cudaStream_t s);
+// out[p] = pts[p] + S(u, pts[p]), u [3][V], points [P][3] (z, y, x)
+cudaError_t warp_points(const float* u, const Vol& v, const float* pts, long long P, float* out, cudaStream_t s);
 // displacement of phi_b o phi_a: out = a + S(b, x + a)  ([B][3][V])
 cudaError_t compose(const float* a, const float* b, float* out, int B, const Vol& v, cudaStream_t s);
 // stats[b][4] = {fraction det(I + grad u) <= 0, mean |r|, max |r|, min det};

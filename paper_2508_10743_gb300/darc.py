@@ -104,6 +104,10 @@ _SIGS = {
     "darc_exp_backward_noalloc": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _f, _vp]),
     "darc_gemm_bf16": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "darc_compose": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_shape_pca": (_i, [_vp, _vp, _vp]),
+    "darc_sym_eigen": (_i, [_vp, _i, _vp, _vp]),
+    "darc_shape_sample": (_i, [_vp, _vp, _i, _i, _vp]),
+    "darc_warp_points": (_i, [_vp, _i, _i, _i, _vp, ctypes.c_longlong, _vp, _vp]),
     "darc_l1": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
     "darc_median": (_i, [_vp, _i, _i, _i, _i, _vp, _vp]),
     "darc_ssim": (_i, [_vp, _vp, _i, _vp, _vp, _vp, _vp, _i, _i, _i, _i, _vp]),
@@ -358,6 +362,25 @@ class Cohort:
         _check(lib().darc_diffeo_report(self._h, first, count, ctypes.cast(out, ctypes.c_void_p)))
         keys = ("neg_jacobian_fraction", "ic_mean", "ic_max", "min_det")
         return [{k: out[4 * i + j] for j, k in enumerate(keys)} for i in range(count)]
+
+    def shape_pca(self):
+        """(eigenvalues [n] descending, subject weights [n, n]) of the PCA of
+        the current velocities (darc_shape_pca)."""
+        import numpy as np
+        ev = np.zeros(self.n)
+        w = np.zeros((self.n, self.n))
+        _check(lib().darc_shape_pca(self._h, ev.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p)))
+        return ev, w
+
+    def shape_sample(self, z) -> torch.Tensor:
+        """Velocities [m, 3, D, H, W] = mean + sum_j sqrt(lambda_j) z[:, j] U_j
+        for standard normal draws z [m, p] (darc_shape_sample)."""
+        import numpy as np
+        z = np.ascontiguousarray(np.atleast_2d(z), dtype=np.float64)
+        m, p = z.shape
+        out = torch.empty((m, 3, *self.shape), dtype=torch.float32, device=self.device)
+        _check(lib().darc_shape_sample(self._h, z.ctypes.data_as(ctypes.c_void_p), m, p, _ptr(out)))
+        return out
 
     def launch_count(self) -> int:
         return int(lib().darc_launch_count(self._h))
@@ -767,6 +790,29 @@ def label_gather(labels: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
     D, H, W = _dims(u)
     out = torch.empty((B, D, H, W), dtype=torch.uint8, device=u.device)
     _check(lib().darc_label_gather(_ptr(labels), _ptr(u), _ptr(out), B, D, H, W, _stream()))
+    return out
+
+
+def sym_eigen(a):
+    """(eigenvalues descending, eigenvectors as rows) of a symmetric matrix
+    by the library's host Jacobi solver (darc_sym_eigen)."""
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    n = a.shape[0]
+    mu, e = np.zeros(n), np.zeros((n, n))
+    _check(lib().darc_sym_eigen(a.ctypes.data_as(ctypes.c_void_p), n, mu.ctypes.data_as(ctypes.c_void_p),
+                                e.ctypes.data_as(ctypes.c_void_p)))
+    return mu, e
+
+
+def warp_points(u: torch.Tensor, pts: torch.Tensor) -> torch.Tensor:
+    """Points [P, 3] (z, y, x) moved by the displacement u [3, D, H, W]:
+    p + S(u, p) (darc_warp_points)."""
+    _need(u, "u")
+    _need(pts, "pts")
+    D, H, W = _dims(u)
+    out = torch.empty_like(pts)
+    _check(lib().darc_warp_points(_ptr(u), D, H, W, _ptr(pts), int(pts.shape[0]), _ptr(out), _stream()))
     return out
 
 

@@ -6,6 +6,9 @@ runs `--warmup` untimed launches then `--reps` launches of the chosen
 operator on one or a few brain-shaped subjects (160x192x224 by default) and
 prints the mean CUDA-event time.  Inputs are seeded synthetic fields and
 images; the velocities reach the workload's 6-voxel displacement scale.
+`unet_step` times training steps of the warm-start network instead (pass
+`--shape 80 96 112`), `unet_forward` its forward pass; the timed launches
+sit inside an NVTX range named "step".
 """
 from __future__ import annotations
 
@@ -20,7 +23,8 @@ from . import configs, darc, synth
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", required=True,
-                    choices=["exp_square", "exp_adjoint", "lncc", "subject_grad", "warp"])
+                    choices=["exp_square", "exp_adjoint", "lncc", "subject_grad", "warp", "unet_step",
+                             "unet_forward"])
     ap.add_argument("--shape", type=int, nargs=3, default=[160, 192, 224])
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--window", type=int, default=9)
@@ -32,6 +36,20 @@ def main():
     dev = torch.device("cuda:0")
     shape = tuple(a.shape)
     B = a.batch
+    if a.kernel.startswith("unet"):
+        g = torch.Generator(device=dev).manual_seed(0)
+        subj = torch.rand(B, *shape, device=dev, generator=g)
+        atlas = torch.rand(*shape, device=dev, generator=g)
+        tgt = torch.randn(B, 3, *shape, device=dev, generator=g) * 0.5
+        net = darc.UNet(shape, max_batch=B, seed=1, device=dev)
+
+        def run_net():
+            if a.kernel == "unet_step":
+                net.train_step(subj, atlas, tgt, lr=3e-4, want_loss=False)
+            else:
+                net.forward(subj, atlas)
+        _time(run_net, a, shape, B)
+        return
     v = torch.stack([synth.random_field(shape, 8.0, a.max_disp, 10 + b, device=dev) for b in range(B)]).contiguous()
     I = torch.stack([synth.random_image(shape, 20 + b, n_ell=12, radii=(4.0, 20.0), device=dev)
                      for b in range(B)]).contiguous()
@@ -52,15 +70,21 @@ def main():
         else:
             darc.subject_grad(cfg, I, A, v)
 
+    _time(run, a, shape, B)
+
+
+def _time(run, a, shape, B):
     for _ in range(a.warmup):
         run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("step")
     e0.record()
     for _ in range(a.reps):
         run()
     e1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     print(json.dumps({"kernel": a.kernel, "shape": shape, "batch": B, "ms": e0.elapsed_time(e1) / a.reps}))
 
 

@@ -89,3 +89,22 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(d, "LIB_PATH", "/nonexistent/libdarc.so")
     with pytest.raises(RuntimeError, match="not built"):
         d.lib()
+
+
+def test_host_eigensolver_matches_numpy(darc):
+    """darc_sym_eigen (behind the PCA shape model) runs on the host."""
+    import numpy as np
+    for n, seed in ((1, 0), (2, 1), (7, 2), (33, 3)):
+        r = np.random.Generator(np.random.PCG64(seed))
+        X = r.normal(size=(n, 3 * n + 1))
+        a = X @ X.T
+        mu, e = darc.sym_eigen(a)
+        ref = np.linalg.eigvalsh(a)[::-1]
+        assert np.allclose(mu, ref, rtol=1e-10, atol=1e-10 * abs(ref).max())
+        assert np.allclose(e @ e.T, np.eye(n), atol=1e-10)
+        assert np.allclose(e @ a @ e.T, np.diag(mu), atol=1e-9 * abs(ref).max())
+        big = np.argmax(np.abs(e), axis=1)
+        assert np.all(e[np.arange(n), big] > 0)
+    # a degenerate spectrum (identity) still gives an orthonormal basis
+    mu, e = darc.sym_eigen(np.eye(4))
+    assert np.allclose(mu, 1.0) and np.allclose(e @ e.T, np.eye(4))

@@ -330,3 +330,42 @@ def test_sharded_hooks_reproduce_the_fused_updates():
     ShardedSweep([split], cfg).update_atlas(0)
     step_f, step_s = np64(fused.atlas()) - A0, np64(split.atlas()) - A0
     assert np.mean(np.abs(step_f - step_s) <= 1e-3 * np.abs(step_f).max()) > 0.99
+
+
+def test_shape_pca_sampling_and_point_warp_match_oracle():
+    """PCA of the velocities (Sec. "Shape synthesis"): eigenvalues, samples
+    for given standard normal draws, and mesh vertices moved by a map."""
+    from oracle import shape as oshape
+    dims, n = (6, 7, 8), 6
+    co = cohort_images(n, dims, 15)
+    c = darc.Cohort(co.images.to(DEV).contiguous(), configs.DarcConfig(dissim=configs.MSE, n_squarings=7))
+    vs = [synth.random_field(dims, 2.0, 1.0 + 0.3 * i, 400 + i) for i in range(n)]
+    for i, v in enumerate(vs):
+        c.set_velocity(i, v.to(DEV).contiguous())
+    ev, w = c.shape_pca()
+    vv = np.stack([np64(v) for v in vs])
+    mean, lam, U = oshape.pca(vv)
+    assert np.allclose(ev[:n - 1], lam[:n - 1], rtol=1e-4)
+    assert abs(ev[n - 1]) <= 1e-5 * ev[0]
+    # modes are unique up to sign: align the oracle's with the library's
+    Xc = vv.reshape(n, -1) - mean.ravel()
+    p = 4
+    sg = np.empty(p)
+    for k in range(p):
+        e_or = Xc @ U[:, k]
+        e_or /= np.linalg.norm(e_or)
+        d = float(e_or @ w[k])
+        assert abs(abs(d) - 1.0) <= 1e-4
+        sg[k] = np.sign(d)
+    z = np.random.Generator(np.random.PCG64(16)).normal(size=(3, p))
+    got = np64(c.shape_sample(z))
+    ref = oshape.sample(mean, lam, U, z * sg)
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+    # z = 0 gives the mean velocity
+    assert np.abs(np64(c.shape_sample(np.zeros((1, p))))[0] - mean).max() <= 1e-6 * np.abs(vv).max()
+    # vertices moved by a map
+    u = synth.random_field(dims, 2.0, 1.5, 420)
+    pts = torch.tensor([[0.0, 0.0, 0.0], [2.5, 3.25, 4.75], [5.0, 6.0, 7.0], [-1.0, 3.0, 9.5], [1.1, 0.2, 6.9]])
+    got = np64(darc.warp_points(u.to(DEV).contiguous(), pts.to(DEV).contiguous()))
+    ref = oshape.warp_points(np64(u), np64(pts))
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
