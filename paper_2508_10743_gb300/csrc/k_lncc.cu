@@ -56,20 +56,33 @@ __global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, fl
     float ys[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) ys[c] = 0.f;
-    for (int yi = y0 - r; yi < yend + r; ++yi) {
+    // a row with its halo is at most 32 + 2 * 8 values: two per lane; the
+    // next row is loaded into registers while the current one is summed
+    float pre[2][NCH];
+    auto fetch = [&](int yi) {
         const bool yin = yi >= 0 && yi < v.H;
-        for (int j = lane; j < LXW; j += 32) {
-            const int xx = x0 - r + j;
-            float vals[NCH];
-            if (yin && xx >= 0 && xx < v.W) {
-                op.load(b, ((long long)z * v.H + yi) * v.W + xx, vals);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int j = lane + 32 * k, xx = x0 - r + j;
+            if (j < LXW && yin && xx >= 0 && xx < v.W) {
+                op.load(b, ((long long)z * v.H + yi) * v.W + xx, pre[k]);
             } else {
 #pragma unroll
-                for (int c = 0; c < NCH; ++c) vals[c] = 0.f;
+                for (int c = 0; c < NCH; ++c) pre[k][c] = 0.f;
             }
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) row[c * LXW + j] = vals[c];
         }
+    };
+    fetch(y0 - r);
+    for (int yi = y0 - r; yi < yend + r; ++yi) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int j = lane + 32 * k;
+            if (j < LXW) {
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) row[c * LXW + j] = pre[k][c];
+            }
+        }
+        if (yi + 1 < yend + r) fetch(yi + 1);
         __syncwarp();
         const int slot = (yi - (y0 - r)) % NR, old = (slot + 1) % NR;
         const bool drop = yi - w >= y0 - r;
@@ -112,16 +125,32 @@ __global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, con
             for (int q = max(z0 - r, 0); q <= min(z0 + r, v.D - 1); ++q) s += __ldg(Pb + c * v.V + q * plane + col);
             S[c] = s;
         }
-        for (int zo = z0; zo < z1; ++zo) {
-            if (zo > z0) {
-                const int qa = zo + r, qd = zo - r - 1;
+        // four planes at a time: their entering and leaving planes are loaded
+        // first (out-of-range ones as exact zeros), then summed in order
+        for (int zo = z0; zo < z1; zo += 4) {
+            float add[4][NCH], drp[4][NCH];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int zz = zo + u;
+                const bool step = zz > z0 && zz < z1;
+                const int qa = zz + r, qd = zz - r - 1;
 #pragma unroll
                 for (int c = 0; c < NCH; ++c) {
-                    if (qa < v.D) S[c] += __ldg(Pb + c * v.V + qa * plane + col);
-                    if (qd >= 0) S[c] -= __ldg(Pb + c * v.V + qd * plane + col);
+                    add[u][c] = (step && qa < v.D) ? __ldg(Pb + c * v.V + qa * plane + col) : 0.f;
+                    drp[u][c] = (step && qd >= 0) ? __ldg(Pb + c * v.V + qd * plane + col) : 0.f;
                 }
             }
-            acc += op.emit(b, zo, y, x, zo * plane + col, S);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int zz = zo + u;
+                if (zz >= z1) break;
+#pragma unroll
+                for (int c = 0; c < NCH; ++c) {
+                    S[c] += add[u][c];
+                    S[c] -= drp[u][c];
+                }
+                acc += op.emit(b, zz, y, x, zz * plane + col, S);
+            }
         }
     }
     if (Op::kReduces) {
