@@ -303,7 +303,9 @@ __global__ void pack_weights_kernel(const float* __restrict__ w, int kp, int cin
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradient as a GEMM over the padded rows of the interior planes:
+// Weight gradient as a GEMM over the padded rows of the interior planes,
+// gathered per (tap, channel) row (used when a call has fewer splits than
+// batches; conv3_wgrad_win_kernel below is the fast path):
 //   dW[co][k] = sum_q gz[q][co] in[q + off(tap)][ci],  k = tap cin + ci.
 // Rows (TMEM lanes) are k in tiles of 128, columns co (np <= 128), K runs
 // over a CTA's range of rows.  Border rows contribute zero (gz is zero
@@ -413,6 +415,146 @@ conv3_wgrad_kernel(WgradArgs a)
         if (row < a.kp) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) out[c + j] = (steps > 0 && ok) ? r8[j] : (ok ? 0.f : __int_as_float(0x7fc00000));
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient on staged windows.  For a fixed (dz, dy) the three dx taps
+// read the input at row q + off(dz, dy) + dx - 1, so one window of Kc + 2
+// input rows serves all three: a CTA owns (dz, dy), a tile of up to 128
+// input channels (TMEM lanes) and a range of rows of one batch (the K
+// dimension), and keeps three accumulators of np columns, one per dx.
+// Both operands are staged in the no-swizzle MN-major layout -- each
+// 16-byte unit holds 8 consecutive channels of one row, the rows of one
+// 8-channel group follow each other 16 bytes apart -- which is the
+// channels-last storage itself, so nothing is transposed; the dx tap is a
+// descriptor whose start moves by dx rows.  In MN-major no-swizzle
+// descriptors the leading offset is the distance between 8-row K groups
+// (128 bytes here) and the stride offset the distance between 8-channel
+// groups (checked on the GPU against the oracle's weight gradient).
+constexpr int WG_KC = 64;                 // rows (K) per stage
+constexpr int WG_RA = WG_KC + 2;          // input window rows per stage
+
+struct WgradWinArgs {
+    const bf16* in;
+    int in_stride, cin;                   // cin % 16 == 0
+    const bf16* gz;
+    int gz_stride, cout;                  // cout % 8 == 0 channels read
+    float* partial;                       // [B * sp][kp][np]
+    PadVol g;
+    int B, sp;                            // splits per batch
+    long long chunk;                      // rows per split (multiple of WG_KC)
+    int kp, np, ns, slot_bytes;
+};
+
+__global__ void __launch_bounds__(128)
+conv3_wgrad_win_kernel(WgradWinArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t mbar[3];
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const PadVol g = a.g;
+    const int dz = blockIdx.x / 3, dy = blockIdx.x - 3 * dz;
+    const int c0 = blockIdx.y * TC_M, nci = min(TC_M, a.cin - c0), ng = nci / 8;
+    const int b = blockIdx.z / a.sp, spi = blockIdx.z - b * a.sp;
+    const long long DP = (long long)g.D * g.P;
+    const long long r0 = (long long)spi * a.chunk, r1 = min(DP, r0 + a.chunk);
+    const long long base = (long long)b * g.Vp + g.P;            // padded row of interior row 0 of batch b
+    const long long rows_total = (long long)a.B * g.Vp;
+    const long long off = (long long)(dz - 1) * g.P + (long long)(dy - 1) * g.Wp;
+    const int steps = r1 > r0 ? (int)((r1 - r0 + WG_KC - 1) / WG_KC) : 0;
+    const uint32_t strideA = (uint32_t)WG_RA * 16u, strideB = (uint32_t)WG_KC * 16u;
+    const int bytesA = 16 * WG_RA * 16;                           // 16 channel groups (M = 128)
+    uint32_t ncols = 32;
+    while ((int)ncols < 3 * a.np) ncols <<= 1;
+    // channel groups the tile does not use stay zero in every slot
+    for (int e = tid; e < a.ns * (16 - ng) * WG_RA; e += 128) {
+        const int slot = e / ((16 - ng) * WG_RA), rest = e - slot * (16 - ng) * WG_RA;
+        const int gi = ng + rest / WG_RA, r = rest % WG_RA;
+        *reinterpret_cast<uint4*>(smem + (size_t)slot * a.slot_bytes + gi * strideA + r * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 0) umma::tmem_alloc(&tslot, ncols);
+    if (tid == 0) {
+        for (int k = 0; k < a.ns; ++k) umma::mbar_init(&mbar[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tslot;
+    const uint32_t idesc = umma::idesc_bf16_f32_mn(TC_M, a.np);
+
+    auto load = [&](int st, int slot) {
+        uint8_t* As = smem + (size_t)slot * a.slot_bytes;
+        uint8_t* Bs = As + bytesA;
+        const long long k0 = r0 + (long long)st * WG_KC;
+        const long long ga = base + k0 + off - 1;                // window row 0 (dx = 0)
+        for (int e = tid; e < ng * WG_RA; e += 128) {
+            const int gi = e / WG_RA, r = e - gi * WG_RA;
+            const long long q = ga + r;
+            const bool ok = q >= 0 && q < rows_total;
+            const bf16* src = ok ? a.in + q * a.in_stride + c0 + 8 * gi : a.in;
+            cp_async16(As + gi * strideA + r * 16, src, ok ? 16 : 0);
+        }
+        for (int e = tid; e < (a.np / 8) * WG_KC; e += 128) {
+            const int go = e / WG_KC, r = e - go * WG_KC;
+            const bool ok = k0 + r < r1 && 8 * go < a.cout;
+            const bf16* src = ok ? a.gz + (base + k0 + r) * a.gz_stride + 8 * go : a.gz;
+            cp_async16(Bs + go * strideB + r * 16, src, ok ? 16 : 0);
+        }
+    };
+
+    for (int p = 0; p < a.ns - 1; ++p) {
+        if (p < steps) load(p, p);
+        cp_async_commit();
+    }
+    bool ok = true;
+    for (int i = 0; i < steps; ++i) {
+        const int j = i + a.ns - 1;
+        if (j < steps) {
+            const int sj = j % a.ns;
+            if (j >= a.ns) ok = umma::mbar_wait(&mbar[sj], (uint32_t)(((j - a.ns) / a.ns) & 1), TC_WAIT) && ok;
+            load(j, sj);
+        }
+        cp_async_commit();
+        if (a.ns == 3) cp_async_wait<2>();
+        else cp_async_wait<1>();
+        umma::fence_smem_async();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+            const uint32_t As = umma::smem_u32(smem + (size_t)(i % a.ns) * a.slot_bytes);
+            const uint32_t Bs = As + bytesA;
+            for (int dx = 0; dx < 3; ++dx)
+                for (int kq = 0; kq < WG_KC / 16; ++kq) {
+                    const uint32_t sa = As + (uint32_t)(dx + 16 * kq) * 16u, sb = Bs + (uint32_t)(16 * kq) * 16u;
+                    const uint64_t da = umma::smem_desc(sa, 128, strideA);
+                    const uint64_t db = umma::smem_desc(sb, 128, strideB);
+                    umma::mma_bf16(tmem + (uint32_t)(dx * a.np), da, db, idesc, (i > 0) || (kq > 0));
+                }
+            umma::commit(&mbar[i % a.ns]);
+        }
+    }
+    if (steps > 0) ok = umma::mbar_wait(&mbar[(steps - 1) % a.ns], (uint32_t)(((steps - 1) / a.ns) & 1), TC_WAIT) && ok;
+    umma::fence_after_sync();
+    // epilogue: lane = input channel c0 + 32 w + lane, columns dx * np + co
+    const int ci = c0 + 32 * warp + lane;
+    for (int dx = 0; dx < 3; ++dx) {
+        const int tap = 9 * dz + 3 * dy + dx;
+        float* out = a.partial + ((size_t)blockIdx.z * a.kp + (size_t)tap * a.cin + ci) * a.np;
+        for (int c = 0; c < a.np; c += 8) {
+            float r8[8];
+            umma::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(dx * a.np + c), r8);
+            if (ci < c0 + nci) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    out[c + q] = (steps > 0 && ok) ? r8[q] : (ok ? 0.f : __int_as_float(0x7fc00000));
+            }
         }
     }
     umma::fence_before_sync();
@@ -715,8 +857,9 @@ cudaError_t pack_weights(const float* w, int kp, int cin, int cout, int conv_cin
     return cudaGetLastError();
 }
 
-cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout, float* partial,
-                        int splits, float* dw, int batch, int D, int H, int W, int kp, int np, cudaStream_t s)
+cudaError_t conv3_wgrad_gather(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout,
+                               float* partial, int splits, float* dw, int batch, int D, int H, int W, int kp, int np,
+                               cudaStream_t s)
 {
     WgradArgs a;
     a.in = static_cast<const bf16*>(in);
@@ -745,6 +888,54 @@ cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, 
     if (e != cudaSuccess) return e;
     conv3_wgrad_reduce_kernel<<<ew_grid((long long)kp * np), 256, 0, s>>>(partial, splits, kp, np, dw);
     return cudaGetLastError();
+}
+
+// the window kernel: splits are taken per batch (a K range never crosses a
+// batch), at most `splits` in all
+cudaError_t conv3_wgrad_win(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout,
+                            float* partial, int splits, float* dw, int batch, int D, int H, int W, int kp, int np,
+                            cudaStream_t s)
+{
+    WgradWinArgs a;
+    a.in = static_cast<const bf16*>(in);
+    a.in_stride = in_stride;
+    a.cin = cin;
+    a.gz = static_cast<const bf16*>(gz);
+    a.gz_stride = gz_stride;
+    a.cout = cout;
+    a.partial = partial;
+    a.g = make_pad(D, H, W);
+    a.B = batch;
+    a.sp = std::max(1, splits / batch);
+    const long long DP = (long long)D * a.g.P;
+    a.chunk = ((DP + a.sp - 1) / a.sp + WG_KC - 1) / WG_KC * WG_KC;
+    a.kp = kp;
+    a.np = np;
+    a.slot_bytes = (16 * WG_RA * 16 + np * WG_KC * 2 + 127) / 128 * 128;
+    a.ns = (3 * a.slot_bytes <= 200 * 1024) ? 3 : 2;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv3_wgrad_win_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             CONV_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const dim3 grid(9, (cin + TC_M - 1) / TC_M, a.sp * batch);
+    conv3_wgrad_win_kernel<<<grid, 128, (size_t)a.ns * a.slot_bytes, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    conv3_wgrad_reduce_kernel<<<ew_grid((long long)kp * np), 256, 0, s>>>(partial, a.sp * batch, kp, np, dw);
+    return cudaGetLastError();
+}
+
+cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout, float* partial,
+                        int splits, float* dw, int batch, int D, int H, int W, int kp, int np, cudaStream_t s)
+{
+    // the window kernel needs one split per batch at least (its partial sums
+    // are laid out per batch split)
+    if (splits >= batch && cin % 16 == 0 && np <= 128)
+        return conv3_wgrad_win(in, in_stride, cin, gz, gz_stride, cout, partial, splits, dw, batch, D, H, W, kp, np, s);
+    return conv3_wgrad_gather(in, in_stride, cin, gz, gz_stride, cout, partial, splits, dw, batch, D, H, W, kp, np, s);
 }
 
 int bias_grad_work_floats(int cout) { return BG_BLOCKS * ((cout + 7) / 8) * 8; }

@@ -43,6 +43,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
          | ((uint32_t)(M >> 4) << 24);       // M / 16
 }
 
+// The same with both operands MN-major: a core matrix is 8 K-rows of 16
+// bytes, each row holding 8 consecutive M (or N) elements.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N)
+{
+    return idesc_bf16_f32(M, N) | (1u << 15) | (1u << 16);
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot_smem, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"

@@ -586,7 +586,7 @@ int darc_conv3d_wgrad(const void* in_dev, int in_stride, int cin, const void* gz
     const int kp = 27 * cin;
     const PadVol g = make_pad(D, H, W);
     const long long nrows = (long long)batch * D * g.P;
-    int splits = (int)std::max<long long>(1, std::min<long long>(256, nrows / 1024));
+    int splits = (int)std::max<long long>(batch, std::min<long long>(256, nrows / 1024));
     while (splits > 1 && (size_t)splits * kp * np * sizeof(float) > work_bytes) splits /= 2;
     if ((size_t)splits * kp * np * sizeof(float) > work_bytes ||
         (db_dev && (size_t)bias_grad_work_floats(cout) * sizeof(float) > work_bytes))

@@ -144,7 +144,8 @@ def test_conv3d_data_gradient_matches_oracle_adjoint(B, shape, cin, cout):
 
 
 @pytest.mark.parametrize("B,shape,cin,S,cout", [(2, (6, 7, 9), 16, 16, 16), (2, (16, 16, 20), 16, 16, 16),
-                                                 (1, (8, 8, 12), 48, 48, 16), (1, (4, 4, 8), 128, 128, 128)])
+                                                 (1, (8, 8, 12), 48, 48, 16), (1, (4, 4, 8), 128, 128, 128),
+                                                 (2, (5, 6, 8), 192, 192, 64), (3, (9, 10, 40), 32, 48, 32)])
 def test_conv3d_weight_gradient_matches_oracle(B, shape, cin, S, cout):
     g = torch.Generator().manual_seed(cin * 7 + cout + B)
     np_ = rup(cout, 16)
