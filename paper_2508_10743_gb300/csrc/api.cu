@@ -434,7 +434,7 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
                                        c->pR, cnt, vol, c->boxbuf, s);
         }
         pLp = c->pL; pRp = c->pR; nL = nR = box_blocks(vol); sL = sR = 1;
-        c->launches += 3;
+        c->launches += 5;           // warp, two box passes of two kernels each
     }
     if (e != cudaSuccess) return e;
     e = finish_step(pLp, nL, sL, pRp, nR, sR, c->loss + 2 * f, c->flags + f, c->k + f, c->bias + f,
@@ -516,17 +516,30 @@ int update_atlas_impl(darc_cohort* c)
 {
     const Vol& vol = c->vol;
     const int T = c->cfg.n_squarings, n = c->n, K3 = c->cfg.atlas_epochs;
-    const int nbatch = (n + c->cfg.atlas_batch - 1) / c->cfg.atlas_batch;
     // algorithmic bytes: centrality 24n + 12 per voxel; warped cohort (24T + 20) n;
-    // L1 median: the cached cohort read once, the atlas written; patch-wise SGD
-    // per mini-batch: statistics 12 + per subject 28 + 20 + Adam 24
+    // L1 median: the cached cohort read once, the atlas written; patch-wise:
+    // the cohort's window statistics 12n, then per mini-batch of nb subjects
+    // either the fused pair (Adam state 24, the two shared coefficients written
+    // and read 16, per subject 24: J twice, its statistics, its coefficient
+    // written and read) or the unfused chain (statistics 12, Adam 24, per
+    // subject 28 + 20)
     double bytes = (24.0 * n + 12.0) + (24.0 * T + 20.0) * n;
     if (c->cfg.dissim == DARC_L1) bytes += 4.0 * n + 4.0;
-    if (patchwise(c->cfg.dissim)) bytes += 12.0 * n + (double)K3 * (nbatch * (12.0 + 24.0) + n * 48.0);
-    Prof p(c, c->st, DARC_K_ATLAS, bytes * (double)vol.V);
     const long long chunks = (n + c->bmax - 1) / c->bmax;
-    c->launches += 2 + chunks * (T + 1) +
-                   (patchwise(c->cfg.dissim) ? chunks + (long long)K3 * nbatch * 6 + 1 : 1);
+    long long launches = 2 + chunks * (T + 1) + 1;
+    if (patchwise(c->cfg.dissim)) {
+        // per mini-batch: fused 2 + 1 + 2 kernels, unfused 2 + 2 + 1 + 4 + 1
+        bytes += 12.0 * n;
+        launches += 2 * chunks + 1;
+        for (int b0 = 0; b0 < n; b0 += c->cfg.atlas_batch) {
+            const int nb = std::min(c->cfg.atlas_batch, n - b0);
+            const bool fused = nb <= ATLAS_FUSED_MAX;
+            bytes += K3 * (fused ? 40.0 + 24.0 * nb : 36.0 + 48.0 * nb);
+            launches += (long long)K3 * (fused ? 5 : 10);
+        }
+    }
+    Prof p(c, c->st, DARC_K_ATLAS, bytes * (double)vol.V);
+    c->launches += launches;
     return update_atlas_body(c);
 }
 
@@ -578,6 +591,28 @@ int update_atlas_body(darc_cohort* c)
         for (int ep = 0; ep < K3; ++ep) {
             for (int b0 = 0; b0 < n; b0 += B) {
                 const int nb = std::min(B, n - b0);
+                if (nb <= ATLAS_FUSED_MAX) {
+                    // two box passes: the batch's metrics with Box(A), Box(A^2); the
+                    // adjoint with the Adam step (subject rows from the host's order)
+                    const int* sh = c->perm_host + (size_t)ep * n + b0;
+                    const float* Jr[ATLAS_FUSED_MAX];
+                    const float* jr[ATLAS_FUSED_MAX];
+                    for (int b = 0; b < nb; ++b) {
+                        Jr[b] = c->Wcache + (size_t)sh[b] * vol.V;
+                        jr[b] = c->jstats + (size_t)sh[b] * 2 * vol.V;
+                    }
+                    CK(atlas_sgd_fused_forward(Jr, jr, nb, c->A, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim),
+                                               c->coef, c->pL, vol, c->boxbuf, s));
+                    CK(reduce_partials(c->pL, box_blocks(vol), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
+                    ++kk;
+                    const double c1 = 1.0 - std::pow((double)c->cfg.beta1, kk);
+                    const double c2 = 1.0 - std::pow((double)c->cfg.beta2, kk);
+                    CK(atlas_sgd_fused_adam(Jr, nb, c->coef, r, c->A, c->Am, c->As,
+                                            (float)(-1.0 / ((double)vol.V * nb)), (float)(c->cfg.lr / c1),
+                                            (float)(1.0 / std::sqrt(c2)), c->cfg.beta1, c->cfg.beta2,
+                                            c->cfg.adam_eps, vol, c->boxbuf, s));
+                    continue;
+                }
                 const int* subj = c->perm_dev + (size_t)ep * n + b0;
                 CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));
                 CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps,

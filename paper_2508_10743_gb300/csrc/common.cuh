@@ -140,6 +140,16 @@ __device__ __forceinline__ double block_sum(float x, double* sh /* >= 32 doubles
     return tot;
 }
 
+// One Adam step of a parameter th with moments m, s and gradient g
+// (Kingma & Ba 2015): lr_c1 = lr / (1 - beta1^k), isc2 = 1 / sqrt(1 - beta2^k).
+__device__ __forceinline__ void adam1(float& th, float& m, float& s, float g, float b1, float b2,
+                                      float lr_c1, float isc2, float eps)
+{
+    m = fmaf(b1, m, (1.f - b1) * g);
+    s = fmaf(b2, s, (1.f - b2) * g * g);
+    th -= lr_c1 * m / fmaf(sqrtf(s), isc2, eps);
+}
+
 // minimum over the block (valid in thread 0)
 __device__ __forceinline__ double block_min(float x, double* sh /* >= 32 doubles */)
 {

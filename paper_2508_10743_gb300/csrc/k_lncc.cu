@@ -22,6 +22,7 @@
 #include "kernels.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace darc_impl {
 namespace {
@@ -105,6 +106,19 @@ __global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, fl
     }
 }
 
+// Number of block reductions an Op's epilogue feeds: 1 (emit returns the
+// value) unless the Op declares kNRed, whose emit_n adds kNRed values.
+template <class Op, class = void>
+struct NRed {
+    static constexpr int value = 1;
+    static constexpr bool multi = false;
+};
+template <class Op>
+struct NRed<Op, std::void_t<decltype(Op::kNRed)>> {
+    static constexpr int value = Op::kNRed;
+    static constexpr bool multi = true;
+};
+
 // 3-D window sums along z from the 2-D sums, then the Op's epilogue
 template <int NCH, class Op>
 __global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc)
@@ -114,7 +128,10 @@ __global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, con
     const int y = blockIdx.y * ZY + threadIdx.y;
     const int b = blockIdx.z / nzc, zc = blockIdx.z % nzc;
     const int z0 = zc * ZC, z1 = min(v.D, z0 + ZC);
-    float acc = 0.f;
+    constexpr int NR = NRed<Op>::value;
+    float acc[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) acc[k] = 0.f;
     if (x < v.W && y < v.H) {
         const long long col = (long long)y * v.W + x, plane = (long long)v.H * v.W;
         const float* Pb = P + (size_t)b * NCH * v.V;
@@ -149,14 +166,20 @@ __global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, con
                     S[c] += add[u][c];
                     S[c] -= drp[u][c];
                 }
-                acc += op.emit(b, zz, y, x, zz * plane + col, S);
+                if constexpr (!NRed<Op>::multi)
+                    acc[0] += op.emit(b, zz, y, x, zz * plane + col, S);
+                else
+                    op.emit_n(b, zz, y, x, zz * plane + col, S, acc);
             }
         }
     }
     if (Op::kReduces) {
-        const double s2 = block_sum(acc, red);
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            op.partial(b, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc), s2);
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            const double s2 = block_sum(acc[k], red);
+            if (threadIdx.x == 0 && threadIdx.y == 0)
+                op.partial(b * NR + k, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc), s2);
+        }
     }
 }
 
@@ -446,6 +469,87 @@ struct AtlasBwdSubjOp {
     __device__ void partial(int, int, double) const {}
 };
 
+// Atlas SGD, one box pass per mini-batch of NB subjects (rows known on the
+// host): channels Box(A), Box(A^2) and Box(J_b A) for each b.  The epilogue
+// evaluates the NB patch metrics and keeps what the adjoint needs.  Because
+// Box is linear, the two coefficients that multiply terms shared by the
+// batch are summed over b here: coef [2 + NB][V] = {sum_b dm_b/dS_A,
+// sum_b dm_b/dS_AA, dm_b/dS_JA for each b}; loss partials [NB][nblk].
+template <int NB>
+struct AtlasFwdFusedOp {
+    static constexpr bool kReduces = true;
+    static constexpr int kNRed = NB;
+    const float* J[NB];    // warped subject b [V]
+    const float* js[NB];   // its window statistics [2][V]
+    const float* A;
+    float* coef;
+    double* partials;
+    int nblk;
+    long long V;
+    float invN, eps, negInvV;
+    int metric;
+    __device__ void load(int, long long l, float* o) const
+    {
+        const float a = __ldg(A + l);
+        o[0] = a;
+        o[1] = a * a;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) o[2 + b] = __ldg(J[b] + l) * a;
+    }
+    __device__ void emit_n(int, int, int, int, long long l, const float* S, float* acc) const
+    {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const CCTerms t = patch_terms(metric, __ldg(js[b] + l), __ldg(js[b] + V + l), S[2 + b], S[0], S[1],
+                                          invN, eps, true);
+            s0 += t.c0;
+            s1 += t.c1;
+            coef[(size_t)(2 + b) * V + l] = t.c2;
+            acc[b] += t.cc * negInvV;
+        }
+        coef[l] = s0;
+        coef[V + l] = s1;
+    }
+    __device__ void partial(int b, int blk, double s) const { partials[(size_t)b * nblk + blk] = s; }
+};
+
+// Atlas SGD, the adjoint of a mini-batch in one box pass with the Adam step
+// in its epilogue: g = scale [Box(sum a) + 2 A Box(sum b) + sum_b J_b Box(g_b)],
+// then A, m, s updated in place.  A is read and written only at the
+// thread's own voxel (the XY pass reads the coefficients alone).
+template <int NB>
+struct AtlasBwdAdamOp {
+    static constexpr bool kReduces = false;
+    const float* J[NB];
+    const float* coef;     // [2 + NB][V] from AtlasFwdFusedOp
+    float* A;
+    float* m;
+    float* s;
+    long long V;
+    float scale, lr_c1, isc2, b1, b2, eps;
+    __device__ void load(int, long long l, float* o) const
+    {
+#pragma unroll
+        for (int c = 0; c < 2 + NB; ++c) o[c] = __ldg(coef + (size_t)c * V + l);
+    }
+    __device__ float emit(int, int, int, int, long long l, const float* S) const
+    {
+        float a = A[l];
+        float g = S[0] + 2.f * a * S[1];
+        // each subject's term rounded on its own, as a separate product
+#pragma unroll
+        for (int b = 0; b < NB; ++b) g += __fmul_rn(__ldg(J[b] + l), S[2 + b]);
+        float mm = m[l], ss = s[l];
+        adam1(a, mm, ss, g * scale, b1, b2, lr_c1, isc2, eps);
+        A[l] = a;
+        m[l] = mm;
+        s[l] = ss;
+        return 0.f;
+    }
+    __device__ void partial(int, int, double) const {}
+};
+
 template <int NCH, class Op>
 cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, float* P, cudaStream_t s)
 {
@@ -512,6 +616,76 @@ cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, 
     if (e != cudaSuccess) return e;
     AtlasBwdSubjOp each{coef, J, subj, gsubj, v.V};
     return launch_box<1>(each, nb, v, r, P, s);
+}
+
+template <int NB>
+cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* jsrows, const float* A, int r,
+                               float eps, int metric, float* coef, double* partials, const Vol& v, float* P,
+                               cudaStream_t s)
+{
+    const int w = 2 * r + 1;
+    AtlasFwdFusedOp<NB> op{};
+    for (int b = 0; b < NB; ++b) {
+        op.J[b] = Jrows[b];
+        op.js[b] = jsrows[b];
+    }
+    op.A = A;
+    op.coef = coef;
+    op.partials = partials;
+    op.nblk = box_blocks(v);
+    op.V = v.V;
+    op.invN = (float)(1.0 / ((double)w * w * w));
+    op.eps = eps;
+    op.negInvV = (float)(-1.0 / (double)v.V);
+    op.metric = metric;
+    return launch_box<2 + NB>(op, 1, v, r, P, s);
+}
+
+template <int NB>
+cudaError_t atlas_fused_adam_nb(const float* const* Jrows, const float* coef, int r, float* A, float* m, float* s_,
+                                float scale, float lr_c1, float isc2, float b1, float b2, float eps, const Vol& v,
+                                float* P, cudaStream_t s)
+{
+    AtlasBwdAdamOp<NB> op{};
+    for (int b = 0; b < NB; ++b) op.J[b] = Jrows[b];
+    op.coef = coef;
+    op.A = A;
+    op.m = m;
+    op.s = s_;
+    op.V = v.V;
+    op.scale = scale;
+    op.lr_c1 = lr_c1;
+    op.isc2 = isc2;
+    op.b1 = b1;
+    op.b2 = b2;
+    op.eps = eps;
+    return launch_box<2 + NB>(op, 1, v, r, P, s);
+}
+
+cudaError_t atlas_sgd_fused_forward(const float* const* Jrows, const float* const* jsrows, int nb, const float* A,
+                                    int r, float eps, int metric, float* coef, double* partials, const Vol& v,
+                                    float* P, cudaStream_t s)
+{
+    switch (nb) {
+    case 1: return atlas_fused_fwd_nb<1>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
+    case 2: return atlas_fused_fwd_nb<2>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
+    case 3: return atlas_fused_fwd_nb<3>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
+    case 4: return atlas_fused_fwd_nb<4>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t atlas_sgd_fused_adam(const float* const* Jrows, int nb, const float* coef, int r, float* A, float* m,
+                                 float* s_, float scale, float lr_c1, float isc2, float b1, float b2, float eps,
+                                 const Vol& v, float* P, cudaStream_t s)
+{
+    switch (nb) {
+    case 1: return atlas_fused_adam_nb<1>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
+    case 2: return atlas_fused_adam_nb<2>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
+    case 3: return atlas_fused_adam_nb<3>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
+    case 4: return atlas_fused_adam_nb<4>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const float* stats,

@@ -77,14 +77,6 @@ finish_step_kernel(const double* __restrict__ pL, int nblkL, int strideL,
     }
 }
 
-__device__ __forceinline__ void adam1(float& th, float& m, float& s, float g, float b1, float b2,
-                                      float lr_c1, float isc2, float eps)
-{
-    m = fmaf(b1, m, (1.f - b1) * g);
-    s = fmaf(b2, s, (1.f - b2) * g * g);
-    th -= lr_c1 * m / fmaf(sqrtf(s), isc2, eps);
-}
-
 // grid (blocks over N/4, B); theta/m/s/g float4 when N % 4 == 0
 __global__ void __launch_bounds__(RT)
 adam_fields_kernel(float* __restrict__ th, float* __restrict__ m, float* __restrict__ s,

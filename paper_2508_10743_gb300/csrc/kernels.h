@@ -205,4 +205,17 @@ cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, 
                                int r, float* gshared, float* gsubj, int nb, const Vol& v, float* P,
                                cudaStream_t s);
 
+// The same mini-batch step in two box passes when nb <= ATLAS_FUSED_MAX and
+// the subjects' rows are known on the host: forward with coef [2 + nb][V]
+// (sum_b dm/dS_A, sum_b dm/dS_AA, dm_b/dS_JA), loss partials [nb][nblk],
+// P >= (2 + nb) V floats; then the adjoint with the Adam step of A (scale
+// multiplies the gradient, as in atlas_adam).  A, m, s are updated in place.
+constexpr int ATLAS_FUSED_MAX = 4;
+cudaError_t atlas_sgd_fused_forward(const float* const* Jrows, const float* const* jsrows, int nb, const float* A,
+                                    int r, float eps, int metric, float* coef, double* partials, const Vol& v,
+                                    float* P, cudaStream_t s);
+cudaError_t atlas_sgd_fused_adam(const float* const* Jrows, int nb, const float* coef, int r, float* A, float* m,
+                                 float* s_, float scale, float lr_c1, float isc2, float b1, float b2, float eps,
+                                 const Vol& v, float* P, cudaStream_t s);
+
 }  // namespace darc_impl

@@ -143,11 +143,14 @@ def test_ssim_atlas_update_matches_oracle_sgd():
     assert all(np.isfinite(losses))
 
 
-def test_ncc_atlas_update_matches_oracle_sgd():
-    shape, n = (12, 18, 33), 5
+# mini-batches of 1 to 4 subjects take the two-pass step with the Adam update
+# in the adjoint's epilogue; 6 takes the unfused chain (and a last batch of 1)
+@pytest.mark.parametrize("n,batch", [(5, 2), (7, 3), (9, 4), (7, 6)])
+def test_ncc_atlas_update_matches_oracle_sgd(n, batch):
+    shape = (12, 18, 33)
     co = cohort_images(n, shape, 4)
     cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=7, atlas_epochs=3,
-                             atlas_batch=2, seed=11)
+                             atlas_batch=batch, seed=11)
     c = darc.Cohort(co.images.to(DEV).contiguous(), cfg)
     v = [synth.random_field(shape, 3.0, 1.5, 300 + i) for i in range(n)]
     for i in range(n):
