@@ -22,6 +22,19 @@
 namespace darc_impl {
 namespace {
 
+#define DARC_PRAGMA(x) _Pragma(#x)
+#define DARC_UNROLL(n) DARC_PRAGMA(unroll n)
+
+// Squaring tiles: 32 x 8 x SQ_Z voxels per block, each thread walking SQ_Z
+// planes, SQ_UNROLL of them with their gathers in flight together.
+#ifndef DARC_SQ_Z
+#define DARC_SQ_Z 4
+#endif
+#ifndef DARC_SQ_UNROLL
+#define DARC_SQ_UNROLL 1
+#endif
+constexpr int SQ_Z = DARC_SQ_Z;
+
 __global__ void __launch_bounds__(VT_THREADS)
 exp_square_kernel(const float* __restrict__ src, float scale, float* __restrict__ dst, Vol v,
                   int nzt)
@@ -35,9 +48,9 @@ exp_square_kernel(const float* __restrict__ src, float scale, float* __restrict_
     const float* s1 = s0 + v.V;
     const float* s2 = s1 + v.V;
     float* d0 = dst + (size_t)b * 3 * v.V;
-#pragma unroll 1
-    for (int k = 0; k < VT_Z; ++k) {
-        const int z = zt * VT_Z + k;
+    DARC_UNROLL(DARC_SQ_UNROLL)
+    for (int k = 0; k < SQ_Z; ++k) {
+        const int z = zt * SQ_Z + k;
         if (z >= v.D) break;
         const long long l = ((long long)z * v.H + y) * v.W + x;
         const float uz = scale * __ldg(s0 + l), uy = scale * __ldg(s1 + l), ux = scale * __ldg(s2 + l);
@@ -221,7 +234,7 @@ cudaError_t exp_square(const float* src, float scale, float* dst, int B, const V
                        cudaStream_t s)
 {
     int nzt;
-    const dim3 grid = voxel_grid(B, v, nzt, VT_Z);
+    const dim3 grid = voxel_grid(B, v, nzt, SQ_Z);
     exp_square_kernel<<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, dst, v, nzt);
     return cudaGetLastError();
 }
