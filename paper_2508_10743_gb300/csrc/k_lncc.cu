@@ -30,8 +30,24 @@ namespace {
 // XY pass: a block of XW warps covers a 32-column strip, YC output rows and
 // XW consecutive planes (one plane per warp).
 constexpr int XW = 8, YC = 32;
-// Z pass: 32 x 8 columns per block, ZC output planes per thread.
-constexpr int ZX = 32, ZY = 8, ZC = 32;
+// Z pass: 32 x 8 columns per block, ZC output planes per thread; the
+// entering and leaving values of ZU planes are loaded ahead of their sums:
+// four planes for one or two channels, two for three or more (whose wider
+// state and epilogues need the registers for occupancy); ZMINB > 0 asks for
+// that many resident blocks per SM (a register cap).
+#ifndef DARC_BOX_ZC
+#define DARC_BOX_ZC 32
+#endif
+#ifndef DARC_BOX_ZU_NARROW
+#define DARC_BOX_ZU_NARROW 4
+#endif
+#ifndef DARC_BOX_ZU_WIDE
+#define DARC_BOX_ZU_WIDE 2
+#endif
+#ifndef DARC_BOX_ZMINB
+#define DARC_BOX_ZMINB 0
+#endif
+constexpr int ZX = 32, ZY = 8, ZC = DARC_BOX_ZC;
 
 size_t xy_smem_bytes(int nch, int r)
 {
@@ -121,13 +137,14 @@ struct NRed<Op, std::void_t<decltype(Op::kNRed)>> {
 
 // 3-D window sums along z from the 2-D sums, then the Op's epilogue
 template <int NCH, class Op>
-__global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc)
+__global__ void __launch_bounds__(ZX * ZY, DARC_BOX_ZMINB) box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc)
 {
     __shared__ double red[32];
     const int x = blockIdx.x * ZX + threadIdx.x;
     const int y = blockIdx.y * ZY + threadIdx.y;
     const int b = blockIdx.z / nzc, zc = blockIdx.z % nzc;
     const int z0 = zc * ZC, z1 = min(v.D, z0 + ZC);
+    constexpr int ZU = NCH >= 3 ? DARC_BOX_ZU_WIDE : DARC_BOX_ZU_NARROW;
     constexpr int NR = NRed<Op>::value;
     float acc[NR];
 #pragma unroll
@@ -142,12 +159,12 @@ __global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, con
             for (int q = max(z0 - r, 0); q <= min(z0 + r, v.D - 1); ++q) s += __ldg(Pb + c * v.V + q * plane + col);
             S[c] = s;
         }
-        // four planes at a time: their entering and leaving planes are loaded
+        // ZU planes at a time: their entering and leaving planes are loaded
         // first (out-of-range ones as exact zeros), then summed in order
-        for (int zo = z0; zo < z1; zo += 4) {
-            float add[4][NCH], drp[4][NCH];
+        for (int zo = z0; zo < z1; zo += ZU) {
+            float add[ZU][NCH], drp[ZU][NCH];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < ZU; ++u) {
                 const int zz = zo + u;
                 const bool step = zz > z0 && zz < z1;
                 const int qa = zz + r, qd = zz - r - 1;
@@ -158,7 +175,7 @@ __global__ void __launch_bounds__(ZX * ZY) box_z_kernel(Op op, Vol v, int r, con
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < ZU; ++u) {
                 const int zz = zo + u;
                 if (zz >= z1) break;
 #pragma unroll
