@@ -440,17 +440,24 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     e = finish_step(pLp, nL, sL, pRp, nR, sR, c->loss + 2 * f, c->flags + f, c->k + f, c->bias + f,
                     c->nonfinite, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, cnt, s);
     if (e != cudaSuccess) return e;
-    float* gv = (T >= 2) ? c->gT : c->gbuf;
+    // the adjoint chain runs on interleaved gradients (one float4 a voxel, so a
+    // scattered corner is one 16-byte atomic), ping-ponging between the two
+    // halves of gbuf; gT (planar) is its input, the last output feeds Adam
+    float4* g4[2] = {reinterpret_cast<float4*>(c->gbuf), reinterpret_cast<float4*>(c->gbuf) + (size_t)cnt * vol.V};
+    const float4* gv = nullptr;
     {
         const float* gin = c->gT;
+        int interleaved = 0;
         auto adj = [&](int t, const float* src, float scale) {
-            float* gout = (t == 0) ? gv : c->gbuf + (size_t)((T - 1 - t) % 2) * fb;
-            cudaError_t err = cudaMemsetAsync(gout, 0, fb * sizeof(float), s);
+            float4* gout = g4[(T - 1 - t) % 2];
+            cudaError_t err = cudaMemsetAsync(gout, 0, (size_t)cnt * vol.V * sizeof(float4), s);
             if (err != cudaSuccess) return err;
             Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
             c->launches += 1;
-            err = exp_square_adjoint(src, scale, gin, gout, scale, cnt, vol, s);
-            gin = gout;
+            err = exp_square_adjoint4(src, scale, gin, interleaved, gout, scale, cnt, vol, s);
+            gin = reinterpret_cast<const float*>(gout);
+            interleaved = 1;
+            gv = gout;
             return err;
         };
         e = exp_backward_plan(plan, vb, c->u_all, fb, s0, sq, adj);
@@ -458,9 +465,8 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     if (e != cudaSuccess) return e;
     Prof p(c, s, DARC_K_ADAM, 84.0 * nv);
     c->launches += 2;
-    return adam_fields(c->v + (size_t)f * 3 * vol.V, c->m + (size_t)f * 3 * vol.V,
-                       c->s + (size_t)f * 3 * vol.V, gv, 1.f, c->bias + f, c->flags + f, c->cfg.beta1,
-                       c->cfg.beta2, c->cfg.adam_eps, cnt, 3 * vol.V, s);
+    return adam_fields_g4(c->v + (size_t)f * 3 * vol.V, c->m + (size_t)f * 3 * vol.V, c->s + (size_t)f * 3 * vol.V,
+                          gv, c->bias + f, c->flags + f, c->cfg.beta1, c->cfg.beta2, c->cfg.adam_eps, cnt, vol.V, s);
 }
 
 int run_steps(darc_cohort* c, int first, int count, int steps)
@@ -791,7 +797,7 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     ALLOC(c->A, v.V);
     ALLOC(c->u_all, F * c->bmax * std::max(CkPlan(T, cfg->checkpoint_stride).fields(), 2));
     ALLOC(c->gT, F * c->bmax);
-    ALLOC(c->gbuf, 2 * F * c->bmax);
+    ALLOC(c->gbuf, 2 * 4 * (size_t)v.V * c->bmax);   // two interleaved float4 gradient sets
     ALLOC(c->pL, 2 * (size_t)nb * bsub);
     ALLOC(c->pR, (size_t)nb * bsub);
     ALLOC(c->acc, v.V);

@@ -222,6 +222,116 @@ exp_square_adjoint_kernel(const float* __restrict__ src, float scale, const floa
     }
 }
 
+// Interleaved gradient fields: one float4 (z, y, x, 0) per voxel, so that a
+// corner's three channels leave as one 16-byte atomic.  The lane exchange
+// and the z carry work as above on whole corners.
+__device__ __forceinline__ void emit4_xpair(float4* o, int a, bool act, float4 lo, const float4& hi, int lane)
+{
+    const int pa = __shfl_up_sync(FULL_MASK, act ? a : -4, 1);
+    const bool absorb = act && lane > 0 && pa >= 0 && pa + 1 == a;
+    const bool given = __shfl_down_sync(FULL_MASK, absorb, 1) && lane < 31;
+    const float hz = __shfl_up_sync(FULL_MASK, hi.x, 1);
+    const float hy = __shfl_up_sync(FULL_MASK, hi.y, 1);
+    const float hx = __shfl_up_sync(FULL_MASK, hi.z, 1);
+    if (absorb) {
+        lo.x += hz;
+        lo.y += hy;
+        lo.z += hx;
+    }
+    if (!act) return;
+    atomicAdd(o + a, lo);
+    if (!given) atomicAdd(o + a + 1, hi);
+}
+
+// IN4: the incoming gradient is interleaved too (else planar [3][V]); the
+// outgoing one is always interleaved [V] float4 per field.
+template <bool IN4>
+__global__ void __launch_bounds__(VT_THREADS)
+exp_square_adjoint4_kernel(const float* __restrict__ src, float scale, const float* __restrict__ gin,
+                           float4* __restrict__ gout, float out_scale, Vol v, int nzt)
+{
+    const int lane = threadIdx.x;
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt;
+    const int b = blockIdx.z / nzt;
+    const bool xy_ok = (x < v.W) && (y < v.H);
+    const float* s0 = src + (size_t)b * 3 * v.V;
+    const float* s1 = s0 + v.V;
+    const float* s2 = s1 + v.V;
+    const float* g0 = gin + (size_t)b * (IN4 ? 4 : 3) * v.V;
+    float4* o = gout + (size_t)b * v.V;
+    const int plane = v.H * v.W;
+    float4 cl[2], cu[2];             // carried upper-z pairs: [dy] lower / upper x-corner
+    int ca = -1;                     // base index of the carried pairs (-1: none)
+    for (int k = 0; k < ADJ_Z; ++k) {
+        const int z = zt * ADJ_Z + k;
+        const bool active = xy_ok && z < v.D;
+        float w[8];
+        float4 gs = make_float4(0.f, 0.f, 0.f, 0.f);
+        int cb = -4;
+        if (active) {
+            const int l = z * plane + y * v.W + x;
+            const Cell c = make_cell(z, y, x, scale * __ldg(s0 + l), scale * __ldg(s1 + l),
+                                     scale * __ldg(s2 + l), v);
+            float gz, gy, gx;
+            if (IN4) {
+                const float4 g4 = __ldg(reinterpret_cast<const float4*>(g0) + l);
+                gz = g4.x;
+                gy = g4.y;
+                gx = g4.z;
+            } else {
+                gz = __ldg(g0 + l);
+                gy = __ldg(g0 + v.V + l);
+                gx = __ldg(g0 + 2 * v.V + l);
+            }
+            float dz0, dy0, dx0, dz1, dy1, dx1, dz2, dy2, dx2;
+            tri_grad(s0, c, v, dz0, dy0, dx0);
+            tri_grad(s1, c, v, dz1, dy1, dx1);
+            tri_grad(s2, c, v, dz2, dy2, dx2);
+            // identity + Jacobian term at the source voxel itself (scale: du_t = scale d src)
+            atomicAdd(o + l, make_float4((gz + scale * (gz * dz0 + gy * dz1 + gx * dz2)) * out_scale,
+                                         (gy + scale * (gz * dy0 + gy * dy1 + gx * dy2)) * out_scale,
+                                         (gx + scale * (gz * dx0 + gy * dx1 + gx * dx2)) * out_scale, 0.f));
+            tri_weights(c, w);
+            gs = make_float4(gz * out_scale, gy * out_scale, gx * out_scale, 0.f);
+            cb = c.base;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w[q] = 0.f;
+        }
+        const bool merge = active && ca == cb;
+        if (ca >= 0 && !merge) {                     // the carried corners are not this cell's: send them
+            atomicAdd(o + ca, cl[0]);
+            atomicAdd(o + ca + 1, cu[0]);
+            atomicAdd(o + ca + v.W, cl[1]);
+            atomicAdd(o + ca + v.W + 1, cu[1]);
+        }
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const float wl = w[2 * dy], wh = w[2 * dy + 1];
+            float4 lo = make_float4(wl * gs.x, wl * gs.y, wl * gs.z, 0.f);
+            const float4 hi = make_float4(wh * gs.x + (merge ? cu[dy].x : 0.f), wh * gs.y + (merge ? cu[dy].y : 0.f),
+                                          wh * gs.z + (merge ? cu[dy].z : 0.f), 0.f);
+            if (merge) {
+                lo.x += cl[dy].x;
+                lo.y += cl[dy].y;
+                lo.z += cl[dy].z;
+            }
+            emit4_xpair(o, cb + dy * v.W, active, lo, hi, lane);
+        }
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const float wl = w[4 + 2 * dy], wh = w[5 + 2 * dy];
+            cl[dy] = make_float4(wl * gs.x, wl * gs.y, wl * gs.z, 0.f);
+            cu[dy] = make_float4(wh * gs.x, wh * gs.y, wh * gs.z, 0.f);
+        }
+        ca = active ? cb + plane : -1;
+    }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) emit4_xpair(o, ca + dy * v.W, ca >= 0, cl[dy], cu[dy], lane);
+}
+
 dim3 voxel_grid(int B, const Vol& v, int& nzt, int zt)
 {
     nzt = div_up(v.D, zt);
@@ -248,6 +358,20 @@ cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, 
     const int vec2 = (v.V % 2 == 0) && ((reinterpret_cast<uintptr_t>(gout) & 7) == 0);
     exp_square_adjoint_kernel<<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, gin, gout, out_scale, v,
                                                                 nzt, vec2);
+    return cudaGetLastError();
+}
+
+cudaError_t exp_square_adjoint4(const float* src, float scale, const float* gin, int gin_interleaved,
+                                float4* gout, float out_scale, int B, const Vol& v, cudaStream_t s)
+{
+    if ((reinterpret_cast<uintptr_t>(gout) & 15) || (gin_interleaved && (reinterpret_cast<uintptr_t>(gin) & 15)))
+        return cudaErrorMisalignedAddress;
+    int nzt;
+    const dim3 grid = voxel_grid(B, v, nzt, ADJ_Z);
+    if (gin_interleaved)
+        exp_square_adjoint4_kernel<true><<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, gin, gout, out_scale, v, nzt);
+    else
+        exp_square_adjoint4_kernel<false><<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, gin, gout, out_scale, v, nzt);
     return cudaGetLastError();
 }
 

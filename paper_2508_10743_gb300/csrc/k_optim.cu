@@ -116,6 +116,62 @@ adam_fields_kernel(float* __restrict__ th, float* __restrict__ m, float* __restr
     }
 }
 
+// The same step for B velocity fields [3][V] whose gradient is interleaved,
+// one float4 (z, y, x, 0) per voxel; grid (blocks over V/4, B), four voxels
+// a thread when V % 4 == 0.
+__global__ void __launch_bounds__(RT)
+adam_fields_g4_kernel(float* __restrict__ th, float* __restrict__ m, float* __restrict__ s,
+                      const float4* __restrict__ g, const float2* __restrict__ bias,
+                      const int* __restrict__ flags, float b1, float b2, float eps, long long V)
+{
+    const int b = blockIdx.y;
+    if (flags && flags[b]) return;
+    const float2 bf = bias[b];
+    const size_t off = (size_t)b * 3 * V;
+    const float4* gb = g + (size_t)b * V;
+    if ((V & 3) == 0) {
+        const long long V4 = V / 4;
+        for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < V4; e += (long long)gridDim.x * RT) {
+            float gv[3][4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 q = __ldg(gb + 4 * e + k);
+                gv[0][k] = q.x;
+                gv[1][k] = q.y;
+                gv[2][k] = q.z;
+            }
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float4* th4 = reinterpret_cast<float4*>(th + off + (size_t)ch * V);
+                float4* m4 = reinterpret_cast<float4*>(m + off + (size_t)ch * V);
+                float4* s4 = reinterpret_cast<float4*>(s + off + (size_t)ch * V);
+                float4 t = th4[e], mm = m4[e], ss = s4[e];
+                adam1(t.x, mm.x, ss.x, gv[ch][0], b1, b2, bf.x, bf.y, eps);
+                adam1(t.y, mm.y, ss.y, gv[ch][1], b1, b2, bf.x, bf.y, eps);
+                adam1(t.z, mm.z, ss.z, gv[ch][2], b1, b2, bf.x, bf.y, eps);
+                adam1(t.w, mm.w, ss.w, gv[ch][3], b1, b2, bf.x, bf.y, eps);
+                th4[e] = t;
+                m4[e] = mm;
+                s4[e] = ss;
+            }
+        }
+    } else {
+        for (long long e = blockIdx.x * (long long)RT + threadIdx.x; e < V; e += (long long)gridDim.x * RT) {
+            const float4 q = __ldg(gb + e);
+            const float gq[3] = {q.x, q.y, q.z};
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const size_t i = off + (size_t)ch * V + e;
+                float t = th[i], mm = m[i], ss = s[i];
+                adam1(t, mm, ss, gq[ch], b1, b2, bf.x, bf.y, eps);
+                th[i] = t;
+                m[i] = mm;
+                s[i] = ss;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(RT)
 adam_flat_kernel(float* __restrict__ th, float* __restrict__ m, float* __restrict__ s,
                  const float* __restrict__ g, size_t N, float lr_c1, float isc2, float b1, float b2,
@@ -321,6 +377,15 @@ cudaError_t adam_fields(float* theta, float* m, float* s_, const float* g, float
     const int gx = (int)std::max<long long>(1, std::min<long long>((work + RT - 1) / RT, 152LL * 8));
     adam_fields_kernel<<<dim3(gx, B), RT, 0, st>>>(theta, m, s_, g, g_scale, bias, flags, beta1,
                                                    beta2, eps, N);
+    return cudaGetLastError();
+}
+
+cudaError_t adam_fields_g4(float* theta, float* m, float* s_, const float4* g, const float2* bias, const int* flags,
+                           float beta1, float beta2, float eps, int B, long long V, cudaStream_t st)
+{
+    const long long work = (V % 4 == 0) ? V / 4 : V;
+    const int gx = (int)std::max<long long>(1, std::min<long long>((work + RT - 1) / RT, 152LL * 8));
+    adam_fields_g4_kernel<<<dim3(gx, B), RT, 0, st>>>(theta, m, s_, g, bias, flags, beta1, beta2, eps, V);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,11 @@ cudaError_t exp_square(const float* src, float scale, float* dst, int B, const V
 // gout must hold zeros (or a sum to add to) before the call.
 cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, float* gout,
                                float out_scale, int B, const Vol& v, cudaStream_t s);
+// The same adjoint onto interleaved gradients: gout [B][V] float4 (z, y, x,
+// 0), 16-byte aligned and cleared (or holding a sum to add to); gin is
+// interleaved the same way (gin_interleaved != 0) or planar [B][3][V].
+cudaError_t exp_square_adjoint4(const float* src, float scale, const float* gin, int gin_interleaved,
+                                float4* gout, float out_scale, int B, const Vol& v, cudaStream_t s);
 
 // ---- images (k_image.cu) ----
 cudaError_t warp(const float* I, size_t I_bstride, const float* u, float* out, int B, const Vol& v,
@@ -85,6 +90,10 @@ cudaError_t finish_step(const double* pL, int nblkL, int strideL, const double* 
 cudaError_t adam_fields(float* theta, float* m, float* s_, const float* g, float g_scale,
                         const float2* bias, const int* flags, float beta1, float beta2, float eps,
                         int B, long long N, cudaStream_t st);
+// The same for B fields [3][V] (B x V voxels) with interleaved gradients g
+// [B][V] float4 (z, y, x, 0), scale 1
+cudaError_t adam_fields_g4(float* theta, float* m, float* s_, const float4* g, const float2* bias, const int* flags,
+                           float beta1, float beta2, float eps, int B, long long V, cudaStream_t st);
 cudaError_t adam_flat(float* theta, float* m, float* s_, const float* g, size_t N, float lr_c1,
                       float inv_sqrt_c2, float beta1, float beta2, float eps, cudaStream_t st);
 int centrality_blocks(const Vol& v);

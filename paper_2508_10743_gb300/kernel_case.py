@@ -6,9 +6,11 @@ runs `--warmup` untimed launches then `--reps` launches of the chosen
 operator on one or a few brain-shaped subjects (160x192x224 by default) and
 prints the mean CUDA-event time.  Inputs are seeded synthetic fields and
 images; the velocities reach the workload's 6-voxel displacement scale.
-`unet_step` times training steps of the warm-start network instead (pass
-`--shape 80 96 112`), `unet_forward` its forward pass; the timed launches
-sit inside an NVTX range named "step".
+`cohort_step` runs whole subject updates of a cohort (the squarings, the
+local NCC terms, the interleaved adjoint chain and Adam).  `unet_step`
+times training steps of the warm-start network instead (pass `--shape 80
+96 112`), `unet_forward` its forward pass; the timed launches sit inside an
+NVTX range named "step".
 """
 from __future__ import annotations
 
@@ -23,8 +25,8 @@ from . import configs, darc, synth
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", required=True,
-                    choices=["exp_square", "exp_adjoint", "lncc", "subject_grad", "warp", "unet_step",
-                             "unet_forward"])
+                    choices=["exp_square", "exp_adjoint", "lncc", "subject_grad", "warp", "cohort_step",
+                             "unet_step", "unet_forward"])
     ap.add_argument("--shape", type=int, nargs=3, default=[160, 192, 224])
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--window", type=int, default=9)
@@ -57,6 +59,11 @@ def main():
     u = darc.exp_forward(v, a.T)
     g = torch.randn_like(v) * 1e-3
     cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=a.window, n_squarings=a.T, lam=1.0)
+    cohort = None
+    if a.kernel == "cohort_step":
+        cohort = darc.Cohort(I, cfg)
+        for b in range(B):
+            cohort.set_velocity(b, v[b].contiguous())
 
     def run():
         if a.kernel == "exp_square":
@@ -67,6 +74,8 @@ def main():
             darc.lncc(I, A, a.window, grad_J=True)
         elif a.kernel == "warp":
             darc.warp(I, u[-1])
+        elif a.kernel == "cohort_step":
+            cohort.subject_step(0, B, 1)
         else:
             darc.subject_grad(cfg, I, A, v)
 

@@ -7,7 +7,8 @@ oracle or against what the method fixes exactly.
   identity).  (With local NCC the eps of the denominator leaves a small
   atlas gradient at A = I, which Adam turns into lr-sized steps.)
 * The smallest volume the library takes (2 x 2 x 2) through a whole sweep.
-* One squaring (T = 1) and the largest local-NCC window (17^3).
+* One squaring (T = 1), through the subject gradient and through the
+  cohort's sweep, and the largest local-NCC window (17^3).
 """
 import numpy as np
 import pytest
@@ -64,6 +65,25 @@ def test_smallest_volume_sweep_matches_the_oracle():
         os_ = oracle.sweep(st, ocfg)
         assert abs(gs["loss_data"] - os_["loss_data"]) <= 1e-4 * os_["loss_data"] + 1e-9
     assert np.abs(np64(c.atlas()) - st.A).max() <= 1e-4 * np.abs(st.A).max()
+
+
+def test_one_squaring_cohort_sweeps_match_the_oracle():
+    """T = 1 through the cohort's step: the adjoint chain is a single launch
+    whose input is the planar image-term gradient."""
+    shape, n = (9, 11, 13), 3
+    r = np.random.Generator(np.random.PCG64(48))
+    imgs = torch.from_numpy(r.uniform(size=(n,) + shape)).float()
+    cfg = configs.DarcConfig(dissim=configs.MSE, n_squarings=1, lam=0.2, inner_steps=3)
+    c = darc.Cohort(imgs.to(DEV).contiguous(), cfg)
+    st = oracle.State(np64(imgs))
+    ocfg = oracle.make_cfg(dissim=cfg.dissim, window=cfg.ncc_window, T=cfg.n_squarings,
+                           inner_steps=cfg.inner_steps, lam=cfg.lam, lr=cfg.lr)
+    for _ in range(2):
+        gs = c.sweep()
+        os_ = oracle.sweep(st, ocfg)
+        assert abs(gs["loss_data"] - os_["loss_data"]) <= 1e-3 * os_["loss_data"]
+    v = np.stack([np64(c.velocity(i)) for i in range(n)])
+    assert np.mean(np.abs(v - st.v) <= 1e-3) > 0.99
 
 
 def test_one_squaring_subject_gradient_matches_the_oracle():
