@@ -395,7 +395,9 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
 {
     const Vol& vol = c->vol;
     const int T = c->cfg.n_squarings;
-    const size_t fb = (size_t)cnt * 3 * vol.V;
+    // u_1..u_T are packed, one float4 (z, y, x, 0) a voxel: a trilinear gather
+    // of a corner's three channels is one 16-byte load; v stays planar
+    const size_t fb = (size_t)cnt * 4 * vol.V;
     const double nv = (double)cnt * (double)vol.V;     // voxels of the chunk
     const float* vb = c->v + (size_t)f * 3 * vol.V;
     const float* Ib = c->images + (size_t)f * vol.V;
@@ -405,7 +407,7 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     auto sq = [&](const float* src, float scale, float* dst) {
         Prof p(c, s, DARC_K_EXP_SQUARE, 24.0 * nv);
         c->launches += 1;
-        return exp_square(src, scale, dst, cnt, vol, s);
+        return exp_square_packed(src, src != vb, scale, reinterpret_cast<float4*>(dst), cnt, vol, s);
     };
     e = exp_forward_plan(plan, vb, c->u_all, fb, s0, sq);
     if (e != cudaSuccess) return e;
@@ -414,14 +416,14 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     int nL, nR, sL, sR;
     if (pointwise(c->cfg.dissim)) {
         Prof p(c, s, DARC_K_MSE_WARP_REG, 32.0 * nv);
-        e = mse_warp_reg(Ib, vol.V, c->A, uT, c->cfg.lambda, c->gT, c->pL, cnt, vol, c->cfg.dissim == DARC_L1, s);
+        e = mse_warp_reg(Ib, vol.V, c->A, uT, c->cfg.lambda, c->gT, c->pL, cnt, vol, c->cfg.dissim == DARC_L1, s, 1);
         pLp = c->pL; pRp = c->pL + 1; nL = nR = voxel_blocks(vol); sL = sR = 2;
         c->launches += 1;
     } else {
         const int r = c->cfg.ncc_window / 2;
         {
             Prof p(c, s, DARC_K_WARP, 20.0 * nv);
-            e = warp(Ib, vol.V, uT, c->Wimg, cnt, vol, s);
+            e = warp_packed(Ib, vol.V, reinterpret_cast<const float4*>(uT), c->Wimg, cnt, vol, s);
         }
         if (e == cudaSuccess) {
             Prof p(c, s, DARC_K_LNCC_FWD, 28.0 * nv);
@@ -431,7 +433,7 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
         if (e == cudaSuccess) {
             Prof p(c, s, DARC_K_LNCC_BWD_WARP_REG, 48.0 * nv);
             e = lncc_backward_warp_reg(c->Wimg, c->A, c->coef, r, Ib, vol.V, uT, c->cfg.lambda, c->gT,
-                                       c->pR, cnt, vol, c->boxbuf, s);
+                                       c->pR, cnt, vol, c->boxbuf, s, 1);
         }
         pLp = c->pL; pRp = c->pR; nL = nR = box_blocks(vol); sL = sR = 1;
         c->launches += 5;           // warp, two box passes of two kernels each
@@ -454,7 +456,7 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
             if (err != cudaSuccess) return err;
             Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
             c->launches += 1;
-            err = exp_square_adjoint4(src, scale, gin, interleaved, gout, scale, cnt, vol, s);
+            err = exp_square_adjoint4(src, t != 0, scale, gin, interleaved, gout, scale, cnt, vol, s);
             gin = reinterpret_cast<const float*>(gout);
             interleaved = 1;
             gv = gout;
@@ -795,7 +797,9 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     ALLOC(c->nonfinite, 1);
     ALLOC(c->loss, 2 * (size_t)n);
     ALLOC(c->A, v.V);
-    ALLOC(c->u_all, F * c->bmax * std::max(CkPlan(T, cfg->checkpoint_stride).fields(), 2));
+    // packed squaring fields of the subject step (4V floats each); also two
+    // planar slots for the atlas's Exp
+    ALLOC(c->u_all, 4 * (size_t)v.V * c->bmax * std::max(CkPlan(T, cfg->checkpoint_stride).fields(), 2));
     ALLOC(c->gT, F * c->bmax);
     ALLOC(c->gbuf, 2 * 4 * (size_t)v.V * c->bmax);   // two interleaved float4 gradient sets
     ALLOC(c->pL, 2 * (size_t)nb * bsub);

@@ -62,15 +62,11 @@ __device__ __forceinline__ Cell make_cell(int z, int y, int x, float uz, float u
     return c;
 }
 
-// S(f, p): trilinear value at the cell.
-__device__ __forceinline__ float tri(const float* __restrict__ f, const Cell& c, const Vol& v)
+// Trilinear value at the cell from its 8 corner values (corner order
+// (dz, dy, dx) = 000, 001, 010, ...).
+__device__ __forceinline__ float tri_corners(const Cell& c, float f000, float f001, float f010, float f011,
+                                             float f100, float f101, float f110, float f111)
 {
-    const int sy = v.W, sz = v.H * v.W;
-    const float* p = f + c.base;
-    const float f000 = __ldg(p), f001 = __ldg(p + 1);
-    const float f010 = __ldg(p + sy), f011 = __ldg(p + sy + 1);
-    const float f100 = __ldg(p + sz), f101 = __ldg(p + sz + 1);
-    const float f110 = __ldg(p + sz + sy), f111 = __ldg(p + sz + sy + 1);
     const float a00 = fmaf(c.tx, f001 - f000, f000);
     const float a01 = fmaf(c.tx, f011 - f010, f010);
     const float a10 = fmaf(c.tx, f101 - f100, f100);
@@ -80,16 +76,11 @@ __device__ __forceinline__ float tri(const float* __restrict__ f, const Cell& c,
     return fmaf(c.tz, b1 - b0, b0);
 }
 
-// S(f, p) and dS/dp (0 along clamped axes).
-__device__ __forceinline__ float tri_grad(const float* __restrict__ f, const Cell& c, const Vol& v,
-                                          float& gz, float& gy, float& gx)
+// The same value and dS/dp (0 along clamped axes) from the 8 corner values.
+__device__ __forceinline__ float tri_grad_corners(const Cell& c, float f000, float f001, float f010, float f011,
+                                                  float f100, float f101, float f110, float f111,
+                                                  float& gz, float& gy, float& gx)
 {
-    const int sy = v.W, sz = v.H * v.W;
-    const float* p = f + c.base;
-    const float f000 = __ldg(p), f001 = __ldg(p + 1);
-    const float f010 = __ldg(p + sy), f011 = __ldg(p + sy + 1);
-    const float f100 = __ldg(p + sz), f101 = __ldg(p + sz + 1);
-    const float f110 = __ldg(p + sz + sy), f111 = __ldg(p + sz + sy + 1);
     const float d00 = f001 - f000, d01 = f011 - f010, d10 = f101 - f100, d11 = f111 - f110;
     const float a00 = fmaf(c.tx, d00, f000);
     const float a01 = fmaf(c.tx, d01, f010);
@@ -105,6 +96,87 @@ __device__ __forceinline__ float tri_grad(const float* __restrict__ f, const Cel
     return fmaf(c.tz, b1 - b0, b0);
 }
 
+// S(f, p): trilinear value at the cell.
+__device__ __forceinline__ float tri(const float* __restrict__ f, const Cell& c, const Vol& v)
+{
+    const int sy = v.W, sz = v.H * v.W;
+    const float* p = f + c.base;
+    return tri_corners(c, __ldg(p), __ldg(p + 1), __ldg(p + sy), __ldg(p + sy + 1), __ldg(p + sz),
+                       __ldg(p + sz + 1), __ldg(p + sz + sy), __ldg(p + sz + sy + 1));
+}
+
+// S(f, p) and dS/dp (0 along clamped axes).
+__device__ __forceinline__ float tri_grad(const float* __restrict__ f, const Cell& c, const Vol& v,
+                                          float& gz, float& gy, float& gx)
+{
+    const int sy = v.W, sz = v.H * v.W;
+    const float* p = f + c.base;
+    return tri_grad_corners(c, __ldg(p), __ldg(p + 1), __ldg(p + sy), __ldg(p + sy + 1), __ldg(p + sz),
+                            __ldg(p + sz + 1), __ldg(p + sz + sy), __ldg(p + sz + sy + 1), gz, gy, gx);
+}
+
+// A displacement field in one of two layouts: planar [3][V] (channel a =
+// axis a) or packed, one float4 (z, y, x, 0) per voxel.  own() reads the
+// three channels at a voxel; sample() the trilinear values at a cell;
+// grad() also the 3 x 3 derivatives d[channel][axis].  Both layouts give
+// the same floats.
+struct PlanarField {
+    const float* p;
+    long long V;
+    __device__ PlanarField subject(int b) const { return PlanarField{p + (size_t)b * 3 * V, V}; }
+    __device__ float3 own(int l) const { return make_float3(__ldg(p + l), __ldg(p + V + l), __ldg(p + 2 * V + l)); }
+    __device__ float3 sample(const Cell& c, const Vol& v) const
+    {
+        return make_float3(tri(p, c, v), tri(p + V, c, v), tri(p + 2 * V, c, v));
+    }
+    __device__ void grad(const Cell& c, const Vol& v, float d[3][3]) const
+    {
+        tri_grad(p, c, v, d[0][0], d[0][1], d[0][2]);
+        tri_grad(p + V, c, v, d[1][0], d[1][1], d[1][2]);
+        tri_grad(p + 2 * V, c, v, d[2][0], d[2][1], d[2][2]);
+    }
+};
+
+struct PackedField {
+    const float4* p;
+    long long V;
+    __device__ PackedField subject(int b) const { return PackedField{p + (size_t)b * V, V}; }
+    __device__ float3 own(int l) const
+    {
+        const float4 q = __ldg(p + l);
+        return make_float3(q.x, q.y, q.z);
+    }
+    __device__ void corners(const Cell& c, const Vol& v, float4 f[8]) const
+    {
+        const int sy = v.W, sz = v.H * v.W;
+        const float4* q = p + c.base;
+        f[0] = __ldg(q);
+        f[1] = __ldg(q + 1);
+        f[2] = __ldg(q + sy);
+        f[3] = __ldg(q + sy + 1);
+        f[4] = __ldg(q + sz);
+        f[5] = __ldg(q + sz + 1);
+        f[6] = __ldg(q + sz + sy);
+        f[7] = __ldg(q + sz + sy + 1);
+    }
+    __device__ float3 sample(const Cell& c, const Vol& v) const
+    {
+        float4 f[8];
+        corners(c, v, f);
+        return make_float3(tri_corners(c, f[0].x, f[1].x, f[2].x, f[3].x, f[4].x, f[5].x, f[6].x, f[7].x),
+                           tri_corners(c, f[0].y, f[1].y, f[2].y, f[3].y, f[4].y, f[5].y, f[6].y, f[7].y),
+                           tri_corners(c, f[0].z, f[1].z, f[2].z, f[3].z, f[4].z, f[5].z, f[6].z, f[7].z));
+    }
+    __device__ void grad(const Cell& c, const Vol& v, float d[3][3]) const
+    {
+        float4 f[8];
+        corners(c, v, f);
+        tri_grad_corners(c, f[0].x, f[1].x, f[2].x, f[3].x, f[4].x, f[5].x, f[6].x, f[7].x, d[0][0], d[0][1], d[0][2]);
+        tri_grad_corners(c, f[0].y, f[1].y, f[2].y, f[3].y, f[4].y, f[5].y, f[6].y, f[7].y, d[1][0], d[1][1], d[1][2]);
+        tri_grad_corners(c, f[0].z, f[1].z, f[2].z, f[3].z, f[4].z, f[5].z, f[6].z, f[7].z, d[2][0], d[2][1], d[2][2]);
+    }
+};
+
 // The 8 trilinear weights in corner order (dz, dy, dx) = 000, 001, 010, ...
 __device__ __forceinline__ void tri_weights(const Cell& c, float w[8])
 {
@@ -114,6 +186,44 @@ __device__ __forceinline__ void tri_weights(const Cell& c, float w[8])
     w[2] = zy01 * x0; w[3] = zy01 * c.tx;
     w[4] = zy10 * x0; w[5] = zy10 * c.tx;
     w[6] = zy11 * x0; w[7] = zy11 * c.tx;
+}
+
+// Diffusion regulariser weights per axis: 1 / (3 P_a), P_a = V (n_a - 1) /
+// n_a voxel pairs along axis a.
+struct RegW {
+    float z, y, x;
+};
+
+// Value share of voxel x (pairs counted at their lower voxel) and gradient
+// dR/du_c(x) of the diffusion regulariser, for a field in either layout.
+template <class F>
+__device__ __forceinline__ float reg_at_field(const F& f, const Vol& v, int z, int y, int x, int l, const RegW& rw,
+                                              float g[3])
+{
+    const int st[3] = {v.H * v.W, v.W, 1};
+    const int q[3] = {z, y, x};
+    const int n[3] = {v.D, v.H, v.W};
+    const float ca[3] = {rw.z, rw.y, rw.x};
+    const float3 c3 = f.own(l);
+    const float cur[3] = {c3.x, c3.y, c3.z};
+    float val = 0.f;
+    g[0] = g[1] = g[2] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool up = q[a] + 1 < n[a];
+        const bool dn = q[a] > 0;
+        const float3 u3 = up ? f.own(l + st[a]) : c3;
+        const float3 d3 = dn ? f.own(l - st[a]) : c3;
+        const float uv[3] = {u3.x, u3.y, u3.z}, dv[3] = {d3.x, d3.y, d3.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float dup = up ? uv[c] - cur[c] : 0.f;
+            const float ddn = dn ? cur[c] - dv[c] : 0.f;
+            val = fmaf(ca[a] * dup, dup, val);
+            g[c] = fmaf(2.f * ca[a], ddn - dup, g[c]);
+        }
+    }
+    return val;
 }
 
 template <typename T>

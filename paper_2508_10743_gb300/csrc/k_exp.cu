@@ -35,29 +35,36 @@ namespace {
 #endif
 constexpr int SQ_Z = DARC_SQ_Z;
 
+// Src: PlanarField or PackedField; PACKED_OUT: u_{t+1} written packed
+// (float4 a voxel) instead of planar.
+template <class Src, bool PACKED_OUT>
 __global__ void __launch_bounds__(VT_THREADS)
-exp_square_kernel(const float* __restrict__ src, float scale, float* __restrict__ dst, Vol v,
-                  int nzt)
+exp_square_kernel(Src src_all, float scale, float* __restrict__ dst, Vol v, int nzt)
 {
     const int x = blockIdx.x * VT_X + threadIdx.x;
     const int y = blockIdx.y * VT_Y + threadIdx.y;
     const int zt = blockIdx.z % nzt;
     const int b = blockIdx.z / nzt;
     if (x >= v.W || y >= v.H) return;
-    const float* s0 = src + (size_t)b * 3 * v.V;
-    const float* s1 = s0 + v.V;
-    const float* s2 = s1 + v.V;
-    float* d0 = dst + (size_t)b * 3 * v.V;
+    const Src f = src_all.subject(b);
+    float* d0 = dst + (size_t)b * (PACKED_OUT ? 4 : 3) * v.V;
     DARC_UNROLL(DARC_SQ_UNROLL)
     for (int k = 0; k < SQ_Z; ++k) {
         const int z = zt * SQ_Z + k;
         if (z >= v.D) break;
-        const long long l = ((long long)z * v.H + y) * v.W + x;
-        const float uz = scale * __ldg(s0 + l), uy = scale * __ldg(s1 + l), ux = scale * __ldg(s2 + l);
+        const int l = (z * v.H + y) * v.W + x;
+        const float3 o = f.own(l);
+        const float uz = scale * o.x, uy = scale * o.y, ux = scale * o.z;
         const Cell c = make_cell(z, y, x, uz, uy, ux, v);
-        d0[l] = fmaf(scale, tri(s0, c, v), uz);
-        d0[l + v.V] = fmaf(scale, tri(s1, c, v), uy);
-        d0[l + 2 * v.V] = fmaf(scale, tri(s2, c, v), ux);
+        const float3 sm = f.sample(c, v);
+        const float rz = fmaf(scale, sm.x, uz), ry = fmaf(scale, sm.y, uy), rx = fmaf(scale, sm.z, ux);
+        if (PACKED_OUT) {
+            reinterpret_cast<float4*>(d0)[l] = make_float4(rz, ry, rx, 0.f);
+        } else {
+            d0[l] = rz;
+            d0[l + v.V] = ry;
+            d0[l + 2 * v.V] = rx;
+        }
     }
 }
 
@@ -245,9 +252,9 @@ __device__ __forceinline__ void emit4_xpair(float4* o, int a, bool act, float4 l
 
 // IN4: the incoming gradient is interleaved too (else planar [3][V]); the
 // outgoing one is always interleaved [V] float4 per field.
-template <bool IN4>
+template <bool IN4, class Src>
 __global__ void __launch_bounds__(VT_THREADS)
-exp_square_adjoint4_kernel(const float* __restrict__ src, float scale, const float* __restrict__ gin,
+exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ gin,
                            float4* __restrict__ gout, float out_scale, Vol v, int nzt)
 {
     const int lane = threadIdx.x;
@@ -256,9 +263,7 @@ exp_square_adjoint4_kernel(const float* __restrict__ src, float scale, const flo
     const int zt = blockIdx.z % nzt;
     const int b = blockIdx.z / nzt;
     const bool xy_ok = (x < v.W) && (y < v.H);
-    const float* s0 = src + (size_t)b * 3 * v.V;
-    const float* s1 = s0 + v.V;
-    const float* s2 = s1 + v.V;
+    const Src f = src_all.subject(b);
     const float* g0 = gin + (size_t)b * (IN4 ? 4 : 3) * v.V;
     float4* o = gout + (size_t)b * v.V;
     const int plane = v.H * v.W;
@@ -272,8 +277,8 @@ exp_square_adjoint4_kernel(const float* __restrict__ src, float scale, const flo
         int cb = -4;
         if (active) {
             const int l = z * plane + y * v.W + x;
-            const Cell c = make_cell(z, y, x, scale * __ldg(s0 + l), scale * __ldg(s1 + l),
-                                     scale * __ldg(s2 + l), v);
+            const float3 u = f.own(l);
+            const Cell c = make_cell(z, y, x, scale * u.x, scale * u.y, scale * u.z, v);
             float gz, gy, gx;
             if (IN4) {
                 const float4 g4 = __ldg(reinterpret_cast<const float4*>(g0) + l);
@@ -285,10 +290,11 @@ exp_square_adjoint4_kernel(const float* __restrict__ src, float scale, const flo
                 gy = __ldg(g0 + v.V + l);
                 gx = __ldg(g0 + 2 * v.V + l);
             }
-            float dz0, dy0, dx0, dz1, dy1, dx1, dz2, dy2, dx2;
-            tri_grad(s0, c, v, dz0, dy0, dx0);
-            tri_grad(s1, c, v, dz1, dy1, dx1);
-            tri_grad(s2, c, v, dz2, dy2, dx2);
+            float d[3][3];
+            f.grad(c, v, d);
+            const float dz0 = d[0][0], dy0 = d[0][1], dx0 = d[0][2];
+            const float dz1 = d[1][0], dy1 = d[1][1], dx1 = d[1][2];
+            const float dz2 = d[2][0], dy2 = d[2][1], dx2 = d[2][2];
             // identity + Jacobian term at the source voxel itself (scale: du_t = scale d src)
             atomicAdd(o + l, make_float4((gz + scale * (gz * dz0 + gy * dz1 + gx * dz2)) * out_scale,
                                          (gy + scale * (gz * dy0 + gy * dy1 + gx * dy2)) * out_scale,
@@ -345,7 +351,25 @@ cudaError_t exp_square(const float* src, float scale, float* dst, int B, const V
 {
     int nzt;
     const dim3 grid = voxel_grid(B, v, nzt, SQ_Z);
-    exp_square_kernel<<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, dst, v, nzt);
+    exp_square_kernel<PlanarField, false><<<grid, dim3(VT_X, VT_Y), 0, s>>>(PlanarField{src, v.V}, scale, dst, v,
+                                                                            nzt);
+    return cudaGetLastError();
+}
+
+cudaError_t exp_square_packed(const float* src, int src_packed, float scale, float4* dst, int B, const Vol& v,
+                              cudaStream_t s)
+{
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) || (src_packed && (reinterpret_cast<uintptr_t>(src) & 15)))
+        return cudaErrorMisalignedAddress;
+    int nzt;
+    const dim3 grid = voxel_grid(B, v, nzt, SQ_Z);
+    float* d = reinterpret_cast<float*>(dst);
+    if (src_packed)
+        exp_square_kernel<PackedField, true><<<grid, dim3(VT_X, VT_Y), 0, s>>>(
+            PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, d, v, nzt);
+    else
+        exp_square_kernel<PlanarField, true><<<grid, dim3(VT_X, VT_Y), 0, s>>>(PlanarField{src, v.V}, scale, d, v,
+                                                                               nzt);
     return cudaGetLastError();
 }
 
@@ -361,17 +385,29 @@ cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, 
     return cudaGetLastError();
 }
 
-cudaError_t exp_square_adjoint4(const float* src, float scale, const float* gin, int gin_interleaved,
+template <class Src>
+void launch_adjoint4(Src f, float scale, const float* gin, int gin_interleaved, float4* gout, float out_scale,
+                     dim3 grid, const Vol& v, int nzt, cudaStream_t s)
+{
+    if (gin_interleaved)
+        exp_square_adjoint4_kernel<true, Src><<<grid, dim3(VT_X, VT_Y), 0, s>>>(f, scale, gin, gout, out_scale, v, nzt);
+    else
+        exp_square_adjoint4_kernel<false, Src><<<grid, dim3(VT_X, VT_Y), 0, s>>>(f, scale, gin, gout, out_scale, v, nzt);
+}
+
+cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
                                 float4* gout, float out_scale, int B, const Vol& v, cudaStream_t s)
 {
-    if ((reinterpret_cast<uintptr_t>(gout) & 15) || (gin_interleaved && (reinterpret_cast<uintptr_t>(gin) & 15)))
+    if ((reinterpret_cast<uintptr_t>(gout) & 15) || (gin_interleaved && (reinterpret_cast<uintptr_t>(gin) & 15)) ||
+        (src_packed && (reinterpret_cast<uintptr_t>(src) & 15)))
         return cudaErrorMisalignedAddress;
     int nzt;
     const dim3 grid = voxel_grid(B, v, nzt, ADJ_Z);
-    if (gin_interleaved)
-        exp_square_adjoint4_kernel<true><<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, gin, gout, out_scale, v, nzt);
+    if (src_packed)
+        launch_adjoint4(PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, gin, gin_interleaved, gout,
+                        out_scale, grid, v, nzt, s);
     else
-        exp_square_adjoint4_kernel<false><<<grid, dim3(VT_X, VT_Y), 0, s>>>(src, scale, gin, gout, out_scale, v, nzt);
+        launch_adjoint4(PlanarField{src, v.V}, scale, gin, gin_interleaved, gout, out_scale, grid, v, nzt, s);
     return cudaGetLastError();
 }
 

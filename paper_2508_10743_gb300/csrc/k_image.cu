@@ -16,42 +16,17 @@
 namespace darc_impl {
 namespace {
 
-struct RegW {
-    float z, y, x;   // 1 / (3 P_a), P_a = V (n_a - 1) / n_a voxel pairs along axis a
-};
-
 RegW reg_weights(const Vol& v)
 {
     auto w = [&](int n) { return (float)(1.0 / (3.0 * (double)v.V * (double)(n - 1) / (double)n)); };
     return RegW{w(v.D), w(v.H), w(v.W)};
 }
 
-// Value share of voxel x (pairs counted at their lower voxel) and gradient
-// dR/du_c(x) of the regulariser.
+// Value share of voxel x and dR/du_c(x) for a planar field.
 __device__ __forceinline__ float reg_at(const float* __restrict__ u, const Vol& v, int z, int y,
                                         int x, long long l, const RegW& rw, float g[3])
 {
-    const long long st[3] = {(long long)v.H * v.W, (long long)v.W, 1};
-    const int q[3] = {z, y, x};
-    const int n[3] = {v.D, v.H, v.W};
-    const float ca[3] = {rw.z, rw.y, rw.x};
-    float val = 0.f;
-    g[0] = g[1] = g[2] = 0.f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const bool up = q[a] + 1 < n[a];
-        const bool dn = q[a] > 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float* uc = u + c * v.V;
-            const float cur = __ldg(uc + l);
-            const float dup = up ? __ldg(uc + l + st[a]) - cur : 0.f;
-            const float ddn = dn ? cur - __ldg(uc + l - st[a]) : 0.f;
-            val = fmaf(ca[a] * dup, dup, val);
-            g[c] = fmaf(2.f * ca[a], ddn - dup, g[c]);
-        }
-    }
-    return val;
+    return reg_at_field(PlanarField{u, v.V}, v, z, y, x, (int)l, rw, g);
 }
 
 __device__ __forceinline__ int block_index_in_subject(int zt)
@@ -59,22 +34,24 @@ __device__ __forceinline__ int block_index_in_subject(int zt)
     return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zt);
 }
 
+// U: PlanarField or PackedField (the displacement's layout)
+template <class U>
 __global__ void __launch_bounds__(VT_THREADS)
-warp_kernel(const float* __restrict__ I, size_t I_bstride, const float* __restrict__ u,
-            float* __restrict__ out, Vol v, int nzt)
+warp_kernel(const float* __restrict__ I, size_t I_bstride, U u, float* __restrict__ out, Vol v, int nzt)
 {
     const int x = blockIdx.x * VT_X + threadIdx.x;
     const int y = blockIdx.y * VT_Y + threadIdx.y;
     const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
     if (x >= v.W || y >= v.H) return;
     const float* Ib = I + (size_t)b * I_bstride;
-    const float* ub = u + (size_t)b * 3 * v.V;
+    const U ub = u.subject(b);
     float* ob = out + (size_t)b * v.V;
     for (int k = 0; k < VT_Z; ++k) {
         const int z = zt * VT_Z + k;
         if (z >= v.D) break;
-        const long long l = ((long long)z * v.H + y) * v.W + x;
-        const Cell c = make_cell(z, y, x, __ldg(ub + l), __ldg(ub + v.V + l), __ldg(ub + 2 * v.V + l), v);
+        const int l = (z * v.H + y) * v.W + x;
+        const float3 d = ub.own(l);
+        const Cell c = make_cell(z, y, x, d.x, d.y, d.z, v);
         ob[l] = tri(Ib, c, v);
     }
 }
@@ -171,9 +148,10 @@ reg_kernel(const float* __restrict__ u, float* __restrict__ gu, double* __restri
 // Point-wise subject step, fused: W = S(I, x + u_T), L = mean l(W - A)
 // (MSE or L1), gT = (l'(W - A)/V) dS(I)/dp + lambda dR/du_T; partials {L, R}
 // per block.
+template <class U>
 __global__ void __launch_bounds__(VT_THREADS)
 mse_warp_reg_kernel(const float* __restrict__ I, size_t I_bstride, const float* __restrict__ A,
-                    const float* __restrict__ uT, float lambda, float* __restrict__ gT,
+                    U uT, float lambda, float* __restrict__ gT,
                     double* __restrict__ partials, Vol v, int nzt, float invV, RegW rw, int l1)
 {
     __shared__ double sh[32];
@@ -181,22 +159,23 @@ mse_warp_reg_kernel(const float* __restrict__ I, size_t I_bstride, const float* 
     const int y = blockIdx.y * VT_Y + threadIdx.y;
     const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
     const float* Ib = I + (size_t)b * I_bstride;
-    const float* ub = uT + (size_t)b * 3 * v.V;
+    const U ub = uT.subject(b);
     float* gb = gT + (size_t)b * 3 * v.V;
     float accL = 0.f, accR = 0.f;
     if (x < v.W && y < v.H) {
         for (int k = 0; k < VT_Z; ++k) {
             const int z = zt * VT_Z + k;
             if (z >= v.D) break;
-            const long long l = ((long long)z * v.H + y) * v.W + x;
-            const Cell c = make_cell(z, y, x, __ldg(ub + l), __ldg(ub + v.V + l), __ldg(ub + 2 * v.V + l), v);
+            const int l = (z * v.H + y) * v.W + x;
+            const float3 d3 = ub.own(l);
+            const Cell c = make_cell(z, y, x, d3.x, d3.y, d3.z, v);
             float dz, dy, dx;
             const float Wv = tri_grad(Ib, c, v, dz, dy, dx);
             const float d = Wv - __ldg(A + l);
             accL = fmaf(invV, pw_loss(d, l1), accL);
             const float gW = invV * pw_grad(d, l1);
             float g[3];
-            accR += reg_at(ub, v, z, y, x, l, rw, g);
+            accR += reg_at_field(ub, v, z, y, x, l, rw, g);
             gb[l] = fmaf(gW, dz, lambda * g[0]);
             gb[l + v.V] = fmaf(gW, dy, lambda * g[1]);
             gb[l + 2 * v.V] = fmaf(gW, dx, lambda * g[2]);
@@ -418,7 +397,17 @@ cudaError_t warp(const float* I, size_t I_bstride, const float* u, float* out, i
 {
     int nzt;
     const dim3 g = vgrid(B, v, nzt);
-    warp_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, u, out, v, nzt);
+    warp_kernel<PlanarField><<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, PlanarField{u, v.V}, out, v, nzt);
+    return cudaGetLastError();
+}
+
+cudaError_t warp_packed(const float* I, size_t I_bstride, const float4* u, float* out, int B, const Vol& v,
+                        cudaStream_t s)
+{
+    if (reinterpret_cast<uintptr_t>(u) & 15) return cudaErrorMisalignedAddress;
+    int nzt;
+    const dim3 g = vgrid(B, v, nzt);
+    warp_kernel<PackedField><<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, PackedField{u, v.V}, out, v, nzt);
     return cudaGetLastError();
 }
 
@@ -451,13 +440,20 @@ cudaError_t reg_partials(const float* u, float* gu, double* partials, int B, con
 
 cudaError_t mse_warp_reg(const float* I, size_t I_bstride, const float* A, const float* uT,
                          float lambda, float* gT, double* partials, int B, const Vol& v,
-                         int l1, cudaStream_t s)
+                         int l1, cudaStream_t s, int uT_packed)
 {
     int nzt;
     const dim3 g = vgrid(B, v, nzt);
-    mse_warp_reg_kernel<<<g, dim3(VT_X, VT_Y), 0, s>>>(I, I_bstride, A, uT, lambda, gT, partials, v,
-                                                      nzt, (float)(1.0 / (double)v.V),
-                                                      reg_weights(v), l1);
+    const float invV = (float)(1.0 / (double)v.V);
+    if (uT_packed) {
+        if (reinterpret_cast<uintptr_t>(uT) & 15) return cudaErrorMisalignedAddress;
+        mse_warp_reg_kernel<PackedField><<<g, dim3(VT_X, VT_Y), 0, s>>>(
+            I, I_bstride, A, PackedField{reinterpret_cast<const float4*>(uT), v.V}, lambda, gT, partials, v, nzt,
+            invV, reg_weights(v), l1);
+    } else {
+        mse_warp_reg_kernel<PlanarField><<<g, dim3(VT_X, VT_Y), 0, s>>>(
+            I, I_bstride, A, PlanarField{uT, v.V}, lambda, gT, partials, v, nzt, invV, reg_weights(v), l1);
+    }
     return cudaGetLastError();
 }
 

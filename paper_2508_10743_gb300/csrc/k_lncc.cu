@@ -343,10 +343,8 @@ struct BwdOp {
     __device__ void partial(int, int, double) const {}
 };
 
-struct RegW {
-    float z, y, x;
-};
-
+// U: the layout of u_T (PlanarField or PackedField)
+template <class U>
 struct BwdWarpRegOp {
     static constexpr bool kReduces = true;
     const float* J;
@@ -354,7 +352,7 @@ struct BwdWarpRegOp {
     const float* coef;
     const float* I;
     size_t I_bstride;
-    const float* uT;
+    U uT;
     float* gT;
     double* partials;
     int nblk;
@@ -372,30 +370,14 @@ struct BwdWarpRegOp {
     {
         const float j = __ldg(J + (size_t)b * v.V + l), a = __ldg(A + l);
         const float gJ = negInvV * (S[0] + 2.f * j * S[1] + a * S[2]);
-        const float* ub = uT + (size_t)b * 3 * v.V;
-        const Cell c = make_cell(z, y, x, __ldg(ub + l), __ldg(ub + v.V + l), __ldg(ub + 2 * v.V + l), v);
+        const U ub = uT.subject(b);
+        const float3 d3 = ub.own((int)l);
+        const Cell c = make_cell(z, y, x, d3.x, d3.y, d3.z, v);
         float dz, dy, dx;
         tri_grad(I + (size_t)b * I_bstride, c, v, dz, dy, dx);
         // diffusion regulariser at x (pairs counted at their lower voxel)
-        const long long st[3] = {(long long)v.H * v.W, (long long)v.W, 1};
-        const int q[3] = {z, y, x};
-        const int n[3] = {v.D, v.H, v.W};
-        const float ca[3] = {rw.z, rw.y, rw.x};
-        float val = 0.f, g[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int a2 = 0; a2 < 3; ++a2) {
-            const bool up = q[a2] + 1 < n[a2];
-            const bool dn = q[a2] > 0;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const float* uc = ub + ch * v.V;
-                const float cur = __ldg(uc + l);
-                const float dup = up ? __ldg(uc + l + st[a2]) - cur : 0.f;
-                const float ddn = dn ? cur - __ldg(uc + l - st[a2]) : 0.f;
-                val = fmaf(ca[a2] * dup, dup, val);
-                g[ch] = fmaf(2.f * ca[a2], ddn - dup, g[ch]);
-            }
-        }
+        float g[3];
+        const float val = reg_at_field(ub, v, z, y, x, (int)l, rw, g);
         float* gb = gT + (size_t)b * 3 * v.V;
         gb[l] = fmaf(gJ, dz, lambda * g[0]);
         gb[v.V + l] = fmaf(gJ, dy, lambda * g[1]);
@@ -725,11 +707,19 @@ cudaError_t lncc_backward(const float* J, const int* subj, const float* A, const
 cudaError_t lncc_backward_warp_reg(const float* J, const float* A, const float* coef, int r,
                                    const float* I, size_t I_bstride, const float* uT,
                                    float lambda, float* gT, double* partials, int B, const Vol& v,
-                                   float* P, cudaStream_t s)
+                                   float* P, cudaStream_t s, int uT_packed)
 {
     auto w = [&](int n) { return (float)(1.0 / (3.0 * (double)v.V * (double)(n - 1) / (double)n)); };
-    BwdWarpRegOp op{J, A, coef, I, I_bstride, uT, gT, partials, box_blocks(v), v,
-                    (float)(-1.0 / (double)v.V), lambda, RegW{w(v.D), w(v.H), w(v.W)}};
+    const RegW rw{w(v.D), w(v.H), w(v.W)};
+    const float negInvV = (float)(-1.0 / (double)v.V);
+    if (uT_packed) {
+        if (reinterpret_cast<uintptr_t>(uT) & 15) return cudaErrorMisalignedAddress;
+        BwdWarpRegOp<PackedField> op{J, A, coef, I, I_bstride, PackedField{reinterpret_cast<const float4*>(uT), v.V},
+                                     gT, partials, box_blocks(v), v, negInvV, lambda, rw};
+        return launch_box<3>(op, B, v, r, P, s);
+    }
+    BwdWarpRegOp<PlanarField> op{J, A, coef, I, I_bstride, PlanarField{uT, v.V}, gT, partials, box_blocks(v), v,
+                                 negInvV, lambda, rw};
     return launch_box<3>(op, B, v, r, P, s);
 }
 

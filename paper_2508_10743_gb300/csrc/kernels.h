@@ -25,13 +25,21 @@ cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, 
                                float out_scale, int B, const Vol& v, cudaStream_t s);
 // The same adjoint onto interleaved gradients: gout [B][V] float4 (z, y, x,
 // 0), 16-byte aligned and cleared (or holding a sum to add to); gin is
-// interleaved the same way (gin_interleaved != 0) or planar [B][3][V].
-cudaError_t exp_square_adjoint4(const float* src, float scale, const float* gin, int gin_interleaved,
+// interleaved the same way (gin_interleaved != 0) or planar [B][3][V]; the
+// field src likewise packed (src_packed != 0) or planar.
+cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
                                 float4* gout, float out_scale, int B, const Vol& v, cudaStream_t s);
+// One squaring written packed: dst [B][V] float4 (z, y, x, 0), 16-byte
+// aligned; src planar [B][3][V] or packed the same way (src_packed != 0).
+cudaError_t exp_square_packed(const float* src, int src_packed, float scale, float4* dst, int B, const Vol& v,
+                              cudaStream_t s);
 
 // ---- images (k_image.cu) ----
 cudaError_t warp(const float* I, size_t I_bstride, const float* u, float* out, int B, const Vol& v,
                  cudaStream_t s);
+// the same with u packed, [B][V] float4 (z, y, x, 0), 16-byte aligned
+cudaError_t warp_packed(const float* I, size_t I_bstride, const float4* u, float* out, int B, const Vol& v,
+                        cudaStream_t s);
 cudaError_t warp_backward(const float* I, size_t I_bstride, const float* u, const float* gW,
                           float* gu, int B, const Vol& v, cudaStream_t s);
 // partials: double [B][nblk] laid out per subject, nblk = voxel_blocks(v)
@@ -46,7 +54,7 @@ cudaError_t reg_partials(const float* u, float* gu, double* partials, int B, con
 // gradient -> gT; partials [B][nblk][2]
 cudaError_t mse_warp_reg(const float* I, size_t I_bstride, const float* A, const float* uT,
                          float lambda, float* gT, double* partials, int B, const Vol& v,
-                         int l1, cudaStream_t s);
+                         int l1, cudaStream_t s, int uT_packed = 0);
 // out[l] = lower median over the n rows of X [n][V]; median_threads(n) == 0:
 // n too large for the shared-memory columns (cudaErrorInvalidValue)
 int median_threads(int n);
@@ -197,10 +205,11 @@ cudaError_t lncc_backward(const float* J, const int* subj, const float* A, const
                           int r, int wrt_atlas, float* g, int B, const Vol& v, float* P, cudaStream_t s);
 // backward fused with the warp adjoint and the regulariser:
 // gT = gJ * dS(I, x + uT)/dp + lambda dR/du_T; reg partials [B][nblk]
+// (uT_packed != 0: uT is packed, [B][V] float4 (z, y, x, 0), 16-byte aligned)
 cudaError_t lncc_backward_warp_reg(const float* J, const float* A, const float* coef, int r,
                                    const float* I, size_t I_bstride, const float* uT,
                                    float lambda, float* gT, double* partials, int B, const Vol& v,
-                                   float* P, cudaStream_t s);
+                                   float* P, cudaStream_t s, int uT_packed = 0);
 cudaError_t sum_images(const float* g, int B, float* out, const Vol& v, cudaStream_t s);
 // Box(J_b), Box(J_b^2) of B images: stats [B][2][V]
 cudaError_t image_stats(const float* J, float* stats, int B, int r, const Vol& v, float* P, cudaStream_t s);
