@@ -404,12 +404,22 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     cudaError_t e = cudaSuccess;
     const float s0 = std::ldexp(1.0f, -T);
     const CkPlan plan(T, c->cfg.checkpoint_stride);
+    // adjoint outputs: one cleared [cnt][V] float4 buffer per squaring (gbuf
+    // slot t for step t), cleared by the forward squaring t on its way
+    float4* const g4 = reinterpret_cast<float4*>(c->gbuf);
+    auto gslot = [&](int t) { return g4 + (size_t)t * cnt * vol.V; };
     auto sq = [&](const float* src, float scale, float* dst) {
         Prof p(c, s, DARC_K_EXP_SQUARE, 24.0 * nv);
         c->launches += 1;
         return exp_square_packed(src, src != vb, scale, reinterpret_cast<float4*>(dst), cnt, vol, s);
     };
-    e = exp_forward_plan(plan, vb, c->u_all, fb, s0, sq);
+    int tf = 0;
+    auto sq_clear = [&](const float* src, float scale, float* dst) {
+        Prof p(c, s, DARC_K_EXP_SQUARE, 24.0 * nv);
+        c->launches += 1;
+        return exp_square_packed(src, src != vb, scale, reinterpret_cast<float4*>(dst), cnt, vol, s, gslot(tf++));
+    };
+    e = exp_forward_plan(plan, vb, c->u_all, fb, s0, sq_clear);
     if (e != cudaSuccess) return e;
     const float* uT = c->u_all + (size_t)plan.slot(T - 1) * fb;
     const double *pLp, *pRp;
@@ -443,17 +453,16 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
                     c->nonfinite, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, cnt, s);
     if (e != cudaSuccess) return e;
     // the adjoint chain runs on interleaved gradients (one float4 a voxel, so a
-    // scattered corner is one 16-byte atomic), ping-ponging between the two
-    // halves of gbuf; gT (planar) is its input, the last output feeds Adam
-    float4* g4[2] = {reinterpret_cast<float4*>(c->gbuf), reinterpret_cast<float4*>(c->gbuf) + (size_t)cnt * vol.V};
+    // scattered corner is one 16-byte atomic): step t adds into gbuf slot t,
+    // which the forward cleared; gT (planar) is its input, the last output
+    // feeds Adam
     const float4* gv = nullptr;
     {
         const float* gin = c->gT;
         int interleaved = 0;
         auto adj = [&](int t, const float* src, float scale) {
-            float4* gout = g4[(T - 1 - t) % 2];
-            cudaError_t err = cudaMemsetAsync(gout, 0, (size_t)cnt * vol.V * sizeof(float4), s);
-            if (err != cudaSuccess) return err;
+            float4* gout = gslot(t);
+            cudaError_t err = cudaSuccess;
             Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
             c->launches += 1;
             err = exp_square_adjoint4(src, t != 0, scale, gin, interleaved, gout, scale, cnt, vol, s);
@@ -801,7 +810,9 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     // planar slots for the atlas's Exp
     ALLOC(c->u_all, 4 * (size_t)v.V * c->bmax * std::max(CkPlan(T, cfg->checkpoint_stride).fields(), 2));
     ALLOC(c->gT, F * c->bmax);
-    ALLOC(c->gbuf, 2 * 4 * (size_t)v.V * c->bmax);   // two interleaved float4 gradient sets
+    // one interleaved float4 gradient set per squaring (at least two planar
+    // field slots for the inverse-map scratch of the diffeomorphism report)
+    ALLOC(c->gbuf, 4 * (size_t)v.V * c->bmax * std::max(T, 2));
     ALLOC(c->pL, 2 * (size_t)nb * bsub);
     ALLOC(c->pR, (size_t)nb * bsub);
     ALLOC(c->acc, v.V);

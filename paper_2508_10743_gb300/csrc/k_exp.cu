@@ -36,10 +36,12 @@ namespace {
 constexpr int SQ_Z = DARC_SQ_Z;
 
 // Src: PlanarField or PackedField; PACKED_OUT: u_{t+1} written packed
-// (float4 a voxel) instead of planar.
+// (float4 a voxel) instead of planar.  zero (packed only, may be null): a
+// packed buffer of the same shape cleared on the way.
 template <class Src, bool PACKED_OUT>
 __global__ void __launch_bounds__(VT_THREADS)
-exp_square_kernel(Src src_all, float scale, float* __restrict__ dst, Vol v, int nzt)
+exp_square_kernel(Src src_all, float scale, float* __restrict__ dst, Vol v, int nzt,
+                  float4* __restrict__ zero = nullptr)
 {
     const int x = blockIdx.x * VT_X + threadIdx.x;
     const int y = blockIdx.y * VT_Y + threadIdx.y;
@@ -60,6 +62,7 @@ exp_square_kernel(Src src_all, float scale, float* __restrict__ dst, Vol v, int 
         const float rz = fmaf(scale, sm.x, uz), ry = fmaf(scale, sm.y, uy), rx = fmaf(scale, sm.z, ux);
         if (PACKED_OUT) {
             reinterpret_cast<float4*>(d0)[l] = make_float4(rz, ry, rx, 0.f);
+            if (zero) zero[(size_t)b * v.V + l] = make_float4(0.f, 0.f, 0.f, 0.f);
         } else {
             d0[l] = rz;
             d0[l + v.V] = ry;
@@ -357,19 +360,20 @@ cudaError_t exp_square(const float* src, float scale, float* dst, int B, const V
 }
 
 cudaError_t exp_square_packed(const float* src, int src_packed, float scale, float4* dst, int B, const Vol& v,
-                              cudaStream_t s)
+                              cudaStream_t s, float4* zero)
 {
-    if ((reinterpret_cast<uintptr_t>(dst) & 15) || (src_packed && (reinterpret_cast<uintptr_t>(src) & 15)))
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) || (src_packed && (reinterpret_cast<uintptr_t>(src) & 15)) ||
+        (reinterpret_cast<uintptr_t>(zero) & 15))
         return cudaErrorMisalignedAddress;
     int nzt;
     const dim3 grid = voxel_grid(B, v, nzt, SQ_Z);
     float* d = reinterpret_cast<float*>(dst);
     if (src_packed)
         exp_square_kernel<PackedField, true><<<grid, dim3(VT_X, VT_Y), 0, s>>>(
-            PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, d, v, nzt);
+            PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, d, v, nzt, zero);
     else
         exp_square_kernel<PlanarField, true><<<grid, dim3(VT_X, VT_Y), 0, s>>>(PlanarField{src, v.V}, scale, d, v,
-                                                                               nzt);
+                                                                               nzt, zero);
     return cudaGetLastError();
 }
 

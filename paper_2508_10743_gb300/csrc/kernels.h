@@ -31,8 +31,9 @@ cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, c
                                 float4* gout, float out_scale, int B, const Vol& v, cudaStream_t s);
 // One squaring written packed: dst [B][V] float4 (z, y, x, 0), 16-byte
 // aligned; src planar [B][3][V] or packed the same way (src_packed != 0).
+// zero (may be null): another [B][V] float4 buffer set to zero on the way.
 cudaError_t exp_square_packed(const float* src, int src_packed, float scale, float4* dst, int B, const Vol& v,
-                              cudaStream_t s);
+                              cudaStream_t s, float4* zero = nullptr);
 
 // ---- images (k_image.cu) ----
 cudaError_t warp(const float* I, size_t I_bstride, const float* u, float* out, int B, const Vol& v,
