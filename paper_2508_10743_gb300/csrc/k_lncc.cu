@@ -136,8 +136,18 @@ struct NRed<Op, std::void_t<decltype(Op::kNRed)>> {
 };
 
 // 3-D window sums along z from the 2-D sums, then the Op's epilogue
+// Resident blocks per SM an Op asks of its Z pass (a register cap), else ZMINB.
+template <class Op, class = void>
+struct ZMinBlocks {
+    static constexpr int value = DARC_BOX_ZMINB;
+};
+template <class Op>
+struct ZMinBlocks<Op, std::void_t<decltype(Op::kZMinBlocks)>> {
+    static constexpr int value = Op::kZMinBlocks;
+};
+
 template <int NCH, class Op>
-__global__ void __launch_bounds__(ZX * ZY, DARC_BOX_ZMINB) box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc)
+__global__ void __launch_bounds__(ZX * ZY, ZMinBlocks<Op>::value) box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc)
 {
     __shared__ double red[32];
     const int x = blockIdx.x * ZX + threadIdx.x;
@@ -344,9 +354,15 @@ struct BwdOp {
 };
 
 // U: the layout of u_T (PlanarField or PackedField)
+// three resident blocks per SM for its Z pass (at most 85 registers): the
+// epilogue's gathers and neighbour loads want occupancy more than registers
+#ifndef DARC_WR_MINB
+#define DARC_WR_MINB 3
+#endif
 template <class U>
 struct BwdWarpRegOp {
     static constexpr bool kReduces = true;
+    static constexpr int kZMinBlocks = DARC_WR_MINB;
     const float* J;
     const float* A;
     const float* coef;
