@@ -94,6 +94,39 @@ def test_full_size_ncc_gradient_on_sampled_blocks(brain):
         assert np.linalg.norm(got - ref) <= GRAD_TOL * np.linalg.norm(ref)
 
 
+def test_full_size_cohort_step_matches_the_oracle_gradient_on_sampled_blocks(brain):
+    """The cohort's own subject step at full size (packed squaring fields,
+    interleaved adjoint chain, Adam): from m = s = 0 its first Adam step is
+    dv = -lr g / (|g| + eps) with g the NCC gradient, so the velocity change
+    on a sampled block is checked against that step of the oracle's gradient
+    on a crop (lambda = 0, as above)."""
+    images, template, v = brain
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=9, n_squarings=7, lam=0.0, inner_steps=1)
+    c = darc.Cohort(images, cfg)
+    c.set_atlas(template)
+    for i in range(2):
+        c.set_velocity(i, v[i].contiguous())
+    c.subject_step(0, 2, 1)
+    dv = torch.stack([c.velocity(i) for i in range(2)]) - v
+    Vfull = float(np.prod(SHAPE))
+    max_u = float(torch.linalg.vector_norm(darc.exp_forward(v, 7)[-1], dim=1).max())
+    cone = int(np.ceil(2 * max_u + 7))
+    k = 6
+    m = 2 * cone + 8 + k + 3
+    ocfg = oracle.make_cfg(dissim=1, window=9, T=7, lam=0.0)
+    for b in range(2):
+        cc = SAMPLES[1 - b]
+        Ic, Ac, vc = crop(np64(images[b]), cc, m), crop(np64(template), cc, m), crop(np64(v[b]), cc, m)
+        _, _, g = oracle.subject_energy(Ic, Ac, vc, ocfg)
+        g *= Ic.size / Vfull
+        inner = (slice(None),) + tuple(slice(m - k, m + k + 1) for _ in range(3))
+        ref = -cfg.lr * g[inner] / (np.abs(g[inner]) + cfg.adam_eps)
+        got = crop(np64(dv[b]), cc, m)[inner]
+        assert np.linalg.norm(got - ref) <= 2e-2 * np.linalg.norm(ref)
+        assert np.mean(np.abs(got - ref) <= 2e-2 * cfg.lr) > 0.99
+    c.close()
+
+
 def test_full_size_centrality_and_subject_steps_in_the_bench_configuration(brain):
     """The cohort at the bench's size: a subject step keeps every loss finite
     and the centrality activation leaves a zero-mean velocity set."""
