@@ -29,7 +29,13 @@ namespace {
 
 // XY pass: a block of XW warps covers a 32-column strip, YC output rows and
 // XW consecutive planes (one plane per warp).
-constexpr int XW = 8, YC = 32;
+#ifndef DARC_BOX_XW
+#define DARC_BOX_XW 8
+#endif
+#ifndef DARC_BOX_YC
+#define DARC_BOX_YC 64
+#endif
+constexpr int XW = DARC_BOX_XW, YC = DARC_BOX_YC;
 // Z pass: 32 x 8 columns per block, ZC output planes per thread; the
 // entering and leaving values of ZU planes are loaded ahead of their sums:
 // four planes for one or two channels, two for three or more (whose wider
