@@ -35,7 +35,13 @@ namespace {
 #ifndef DARC_BOX_YC
 #define DARC_BOX_YC 64
 #endif
+#ifndef DARC_BOX_YC_WIDE_BATCH
+#define DARC_BOX_YC_WIDE_BATCH 192
+#endif
 constexpr int XW = DARC_BOX_XW, YC = DARC_BOX_YC;
+// strip height for launches of eight or more images (enough blocks without
+// splitting the columns as finely)
+constexpr int YC_WIDE = DARC_BOX_YC_WIDE_BATCH;
 // Z pass: 32 x 8 columns per block, ZC output planes per thread; the
 // entering and leaving values of ZU planes are loaded ahead of their sums:
 // four planes for one or two channels, two for three or more (whose wider
@@ -63,7 +69,8 @@ size_t xy_smem_bytes(int nch, int r)
 
 // P[b][c] = 2-D window sums (x, y) of the input channels of every plane
 template <int NCH, class Op>
-__global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, float* __restrict__ P, int nzb)
+__global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, float* __restrict__ P, int nzb,
+                                                         int yc)
 {
     extern __shared__ float sm[];
     const int w = 2 * r + 1, LXW = 32 + 2 * r, NR = w + 1;
@@ -71,11 +78,11 @@ __global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, fl
     const int b = blockIdx.z / nzb;
     const int z = (blockIdx.z % nzb) * XW + wp;
     if (z >= v.D) return;                          // whole warp; no block-level barrier below
-    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * YC;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * yc;
     const int x = x0 + lane;
     float* row = sm + (size_t)wp * (NCH * LXW + NR * NCH * 32);
     float* ring = row + NCH * LXW;
-    const int yend = min(y0 + YC, v.H);
+    const int yend = min(y0 + yc, v.H);
     float ys[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) ys[c] = 0.f;
@@ -582,8 +589,9 @@ cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, float* P, cudaS
         attr_set = true;
     }
     const int nzb = div_up(v.D, XW);
-    box_xy_kernel<NCH, Op><<<dim3(div_up(v.W, 32), div_up(v.H, YC), nzb * B), XW * 32, xy_smem_bytes(NCH, r), s>>>(
-        op, v, r, P, nzb);
+    const int yc = B >= 8 ? YC_WIDE : YC;
+    box_xy_kernel<NCH, Op><<<dim3(div_up(v.W, 32), div_up(v.H, yc), nzb * B), XW * 32, xy_smem_bytes(NCH, r), s>>>(
+        op, v, r, P, nzb, yc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nzc = div_up(v.D, ZC);
