@@ -224,30 +224,31 @@ cudaError_t exp_forward_pingpong(const float* v, float* u2, int cnt, const Vol& 
     return cudaSuccess;
 }
 
-// Adjoint of Exp: gin = gT; two ping-pong buffers gbuf [2][cnt][3V]; gv may
-// be gT when T >= 2.  u holds u_1..u_T (cnt fields per slot).
-cudaError_t exp_backward_all(const float* v, const float* u, const float* gT, float* gv, float* gbuf,
+// Adjoint of Exp: gin = gT (planar); the chain runs on interleaved
+// gradients in two ping-pong buffers gbuf [2][cnt][V] float4 (one 16-byte
+// atomic per scattered corner), cleared before each step; the result is
+// unpacked into gv [cnt][3][V], which may be gT.  u holds u_1..u_T (planar,
+// cnt fields per slot).
+cudaError_t exp_backward_all(const float* v, const float* u, const float* gT, float* gv, float4* gbuf,
                              int cnt, const Vol& vol, int T, float sign, cudaStream_t s)
 {
     const float s0 = sign * std::ldexp(1.0f, -T);
     const size_t fb = (size_t)cnt * 3 * vol.V;
+    float4* g4[2] = {gbuf, gbuf + (size_t)cnt * vol.V};
     const float* gin = gT;
+    int interleaved = 0;
     for (int t = T - 1; t >= 0; --t) {
         const float* src = (t == 0) ? v : u + (size_t)(t - 1) * fb;
         const float scale = (t == 0) ? s0 : 1.f;
-        float* gout;
-        if (t == 0)
-            gout = (gv == gT && T == 1) ? gbuf : gv;
-        else
-            gout = gbuf + (size_t)((T - 1 - t) % 2) * fb;
-        cudaError_t e = cudaMemsetAsync(gout, 0, fb * sizeof(float), s);
+        float4* gout = g4[(T - 1 - t) % 2];
+        cudaError_t e = cudaMemsetAsync(gout, 0, (size_t)cnt * vol.V * sizeof(float4), s);
         if (e != cudaSuccess) return e;
-        e = exp_square_adjoint(src, scale, gin, gout, (t == 0) ? s0 : 1.f, cnt, vol, s);
+        e = exp_square_adjoint4(src, 0, scale, gin, interleaved, gout, scale, cnt, vol, s);
         if (e != cudaSuccess) return e;
-        gin = gout;
+        gin = reinterpret_cast<const float*>(gout);
+        interleaved = 1;
     }
-    if (gv == gT && T == 1) return cudaMemcpyAsync(gv, gbuf, fb * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    return cudaSuccess;
+    return unpack_field(g4[(T - 1) % 2], gv, cnt, vol, s);
 }
 
 }  // namespace
@@ -1425,7 +1426,7 @@ int darc_exp_forward(const float* v_dev, float* u_dev, int B, int D, int H, int 
 
 size_t darc_exp_backward_workspace(int B, int D, int H, int W)
 {
-    return 2 * align256(sizeof(float) * 3 * (size_t)B * D * H * W);
+    return 2 * align256(sizeof(float4) * (size_t)B * D * H * W);
 }
 
 int darc_exp_backward(const float* v_dev, const float* u_dev, const float* gT_dev, float* gv_dev, void* work_dev,
@@ -1437,7 +1438,7 @@ int darc_exp_backward(const float* v_dev, const float* u_dev, const float* gT_de
     if (T < 1 || T > 20) return fail(DARC_ERR_ARG, "T must be 1..20");
     const Vol v = make_vol(D, H, W);
     Carve cv(work_dev);
-    float* gbuf = cv.take<float>(2 * 3 * (size_t)B * v.V);
+    float4* gbuf = reinterpret_cast<float4*>(cv.take<float>(2 * 4 * (size_t)B * v.V));
     CK(exp_backward_all(v_dev, u_dev, gT_dev, gv_dev, gbuf, B, v, T, sign, (cudaStream_t)stream));
     return DARC_OK;
 }
@@ -1585,10 +1586,10 @@ int darc_diffusion_reg(const float* u_dev, float* loss_dev, float* gu_dev, void*
 size_t darc_subject_grad_workspace(const darc_config* cfg, int B, int D, int H, int W)
 {
     if (!cfg) return 0;
-    const size_t V = (size_t)D * H * W, F = 3 * V * B;
+    const size_t V = (size_t)D * H * W, F = 3 * V * B, F4 = 4 * V * B;
     const int T = std::max(cfg->n_squarings, 1);
     const size_t fields = (size_t)CkPlan(T, cfg->checkpoint_stride).fields();
-    return align256(sizeof(float) * F * fields) + align256(sizeof(float) * F) + 2 * align256(sizeof(float) * F) +
+    return align256(sizeof(float) * F4 * fields) + align256(sizeof(float) * F) + align256(sizeof(float) * 2 * F4) +
            align256(sizeof(float) * V * B) + align256(sizeof(float) * 3 * V * B) + align256(sizeof(float) * 2 * V) +
            2 * darc_loss_workspace(B, D, H, W) + align256(sizeof(float) * 3 * V * B);
 }
@@ -1604,12 +1605,14 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     const Vol v = make_vol(D, H, W);
     cudaStream_t s = (cudaStream_t)stream;
     const int T = cfg->n_squarings;
-    const size_t F = 3 * (size_t)v.V * B;
+    const size_t F = 3 * (size_t)v.V * B, F4 = 4 * (size_t)v.V * B;
     Carve cv(work_dev);
     const CkPlan plan(T, cfg->checkpoint_stride);
-    float* u_all = cv.take<float>(F * plan.fields());
+    // packed squaring fields and interleaved adjoint gradients, as in the
+    // cohort's step; the result is unpacked into the planar gv
+    float* u_all = cv.take<float>(F4 * plan.fields());
     float* gT = cv.take<float>(F);
-    float* gbuf = cv.take<float>(2 * F);
+    float4* gbuf = reinterpret_cast<float4*>(cv.take<float>(2 * F4));
     float* Wimg = cv.take<float>((size_t)v.V * B);
     float* coef = cv.take<float>(3 * (size_t)v.V * B);
     float* stats = cv.take<float>(2 * (size_t)v.V);
@@ -1617,32 +1620,40 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     double* pR = cv.take<double>(2 * (size_t)B * nblk_max(v));
     float* P = cv.take<float>(3 * (size_t)B * v.V);
     const float s0 = std::ldexp(1.0f, -T);
-    auto sq = [&](const float* src, float scale, float* dst) { return exp_square(src, scale, dst, B, v, s); };
-    CK(exp_forward_plan(plan, v_dev, u_all, F, s0, sq));
-    const float* uT = u_all + (size_t)plan.slot(T - 1) * F;
+    auto sq = [&](const float* src, float scale, float* dst) {
+        return exp_square_packed(src, src != v_dev, scale, reinterpret_cast<float4*>(dst), B, v, s);
+    };
+    CK(exp_forward_plan(plan, v_dev, u_all, F4, s0, sq));
+    const float* uT = u_all + (size_t)plan.slot(T - 1) * F4;
     if (pointwise(cfg->dissim)) {
-        CK(mse_warp_reg(I_dev, v.V, A_dev, uT, cfg->lambda, gT, pL, B, v, cfg->dissim == DARC_L1, s));
+        CK(mse_warp_reg(I_dev, v.V, A_dev, uT, cfg->lambda, gT, pL, B, v, cfg->dissim == DARC_L1, s, 1));
         CK(reduce_partials(pL, voxel_blocks(v), 2, 1.0, energy_dev, 2, B, s));
     } else {
         const int r = cfg->ncc_window / 2;
         CK(atlas_stats(A_dev, stats, r, v, P, s));
-        CK(warp(I_dev, v.V, uT, Wimg, B, v, s));
+        CK(warp_packed(I_dev, v.V, reinterpret_cast<const float4*>(uT), Wimg, B, v, s));
         CK(lncc_forward(Wimg, nullptr, A_dev, stats, r, cfg->ncc_eps, 0, patch_metric(cfg->dissim), coef, pL, B,
                         v, P, s));
-        CK(lncc_backward_warp_reg(Wimg, A_dev, coef, r, I_dev, v.V, uT, cfg->lambda, gT, pR, B, v, P, s));
+        CK(lncc_backward_warp_reg(Wimg, A_dev, coef, r, I_dev, v.V, uT, cfg->lambda, gT, pR, B, v, P, s, 1));
         CK(reduce_partials(pL, box_blocks(v), 1, 1.0, energy_dev, 2, B, s));
         CK(reduce_partials(pR, box_blocks(v), 1, 1.0, energy_dev + 1, 2, B, s));
     }
+    float4* g4[2] = {gbuf, gbuf + (size_t)B * v.V};
     const float* gin = gT;
+    int interleaved = 0;
+    const float4* last = nullptr;
     auto adj = [&](int t, const float* src, float scale) {
-        float* gout = (t == 0) ? gv_dev : gbuf + (size_t)((T - 1 - t) % 2) * F;
-        cudaError_t e = cudaMemsetAsync(gout, 0, F * sizeof(float), s);
+        float4* gout = g4[(T - 1 - t) % 2];
+        cudaError_t e = cudaMemsetAsync(gout, 0, (size_t)B * v.V * sizeof(float4), s);
         if (e != cudaSuccess) return e;
-        e = exp_square_adjoint(src, scale, gin, gout, scale, B, v, s);
-        gin = gout;
+        e = exp_square_adjoint4(src, t != 0, scale, gin, interleaved, gout, scale, B, v, s);
+        gin = reinterpret_cast<const float*>(gout);
+        interleaved = 1;
+        last = gout;
         return e;
     };
-    CK(exp_backward_plan(plan, v_dev, u_all, F, s0, sq, adj));
+    CK(exp_backward_plan(plan, v_dev, u_all, F4, s0, sq, adj));
+    CK(unpack_field(last, gv_dev, B, v, s));
     return DARC_OK;
 }
 

@@ -23,6 +23,7 @@
 // corner arithmetic, so they give the same floats.
 #include "kernels.h"
 
+#include <algorithm>
 #include <climits>
 
 namespace darc_impl {
@@ -347,6 +348,20 @@ exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ g
     for (int dy = 0; dy < 2; ++dy) emit4_xpair(o, ca + dy * v.W, ca >= 0, cl[dy], cu[dy], lane);
 }
 
+// g[b][c][l] = g4[b][l].c: an interleaved gradient back to planar fields
+__global__ void __launch_bounds__(256)
+unpack_field_kernel(const float4* __restrict__ g4, float* __restrict__ g, long long V, long long n)
+{
+    for (long long e = blockIdx.x * 256LL + threadIdx.x; e < n; e += (long long)gridDim.x * 256) {
+        const long long b = e / V, l = e - b * V;
+        const float4 q = __ldg(g4 + e);
+        float* gb = g + (size_t)b * 3 * V;
+        gb[l] = q.x;
+        gb[V + l] = q.y;
+        gb[2 * V + l] = q.z;
+    }
+}
+
 dim3 voxel_grid(int B, const Vol& v, int& nzt, int zt)
 {
     nzt = div_up(v.D, zt);
@@ -418,6 +433,14 @@ cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, c
                         out_scale, grid, v, nzt, s);
     else
         launch_adjoint4(PlanarField{src, v.V}, scale, gin, gin_interleaved, gout, out_scale, grid, v, nzt, s);
+    return cudaGetLastError();
+}
+
+cudaError_t unpack_field(const float4* g4, float* g, int B, const Vol& v, cudaStream_t s)
+{
+    const long long n = (long long)B * v.V;
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    unpack_field_kernel<<<blocks, 256, 0, s>>>(g4, g, v.V, n);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,8 @@ cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, 
 // field src likewise packed (src_packed != 0) or planar.
 cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
                                 float4* gout, float out_scale, int B, const Vol& v, cudaStream_t s);
+// g [B][3][V] from an interleaved gradient g4 [B][V] float4 (z, y, x, 0)
+cudaError_t unpack_field(const float4* g4, float* g, int B, const Vol& v, cudaStream_t s);
 // One squaring written packed: dst [B][V] float4 (z, y, x, 0), 16-byte
 // aligned; src planar [B][3][V] or packed the same way (src_packed != 0).
 // zero (may be null): another [B][V] float4 buffer set to zero on the way.

@@ -75,8 +75,9 @@ extern "C" int darc_exp_backward_noalloc(const float* v_dev, const float* u_dev,
     cudaStream_t s = (cudaStream_t)stream;
     const size_t fb = (size_t)B * 3 * vol.V;
     const float s0 = sign * std::ldexp(1.0f, -T);
-    // same sequence as darc_exp_backward: g_T -> ... -> g_0, each buffer
-    // cleared before the squaring's adjoint adds into it
+    // the steps of darc_exp_backward (g_T -> ... -> g_0) on planar gradients,
+    // which fit the scratch array: each buffer cleared before the
+    // squaring's adjoint adds into it
     const float* gin = gT_dev;
     for (int t = T - 1; t >= 0; --t) {
         const float* src = (t == 0) ? v_dev : u_dev + (size_t)(t - 1) * fb;

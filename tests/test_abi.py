@@ -77,7 +77,8 @@ def test_host_argument_checks(darc):
 
 def test_workspace_queries_are_host_only(darc):
     L = darc.lib()
-    assert L.darc_exp_backward_workspace(2, 8, 8, 8) == 2 * (2 * 3 * 512 * 4)
+    # two interleaved gradient buffers, one float4 a voxel
+    assert L.darc_exp_backward_workspace(2, 8, 8, 8) == 2 * (2 * 512 * 16)
     assert L.darc_lncc_workspace(1, 16, 16, 16) > 4 * 16 ** 3 * 6
     cfg = darc.default_config()
     assert L.darc_subject_grad_workspace(ctypes.byref(cfg), 1, 16, 16, 16) > 4 * 3 * 16 ** 3 * 7
