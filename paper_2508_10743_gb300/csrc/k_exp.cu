@@ -16,10 +16,10 @@
 // Along z, each thread walks consecutive planes and merges the upper-z
 // corners of one source with the lower-z corners of the next in registers.
 //
-// Two field layouts: planar [3][V] (the public Exp entry points, and v) and
-// packed, one float4 (z, y, x, 0) a voxel (the cohort's subject update: a
-// corner's three channels are one 16-byte gather, and on interleaved
-// gradients one 16-byte atomic).  Both read through the same trilinear
+// Two field layouts: planar [3][V] (v, the public Exp forward, the
+// allocation-free adjoint) and packed, one float4 (z, y, x, 0) a voxel (the
+// subject update's squaring fields: a corner's three channels are one
+// 16-byte gather; the adjoint chains' gradients: one 16-byte atomic).  Both read through the same trilinear
 // corner arithmetic, so they give the same floats.
 #include "kernels.h"
 
