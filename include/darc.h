@@ -72,7 +72,19 @@ typedef struct {
     int subject_batch;     /* subjects per launch in darc_subject_step (0 = all)  */
     int reset_each_sweep;  /* 1: restart v and Adam each sweep (literal Algorithm 1) */
     unsigned long long seed; /* atlas mini-batch shuffle                           */
+    int adjoint;           /* darc_adjoint: how the squarings' adjoint forms the
+                              transpose of the interpolation                      */
 } darc_config;
+
+/* The transpose of trilinear sampling in the adjoint of each squaring
+ * (Sec. "Diffeomorphisms", the backward of Exp).  SCATTER: every source adds
+ * its 8 corner weights with float atomics into a buffer its forward squaring
+ * cleared.  GATHER: every voxel collects the sources whose displacement is
+ * below one voxel on each axis from its 27 neighbours and is written once;
+ * the others are scattered afterwards, so the result is bitwise
+ * reproducible where all displacements are sub-voxel.  Both give the same
+ * gradient up to float rounding order. */
+typedef enum { DARC_ADJOINT_SCATTER = 0, DARC_ADJOINT_GATHER = 1 } darc_adjoint;
 
 /* Per-sweep statistics (Sec. "Evaluation metrics"; Table 1's centrality). */
 typedef struct {
@@ -231,14 +243,17 @@ int darc_atlas_batches(darc_cohort* c);
 /* Kernel families timed by the profiling switch. */
 typedef enum {
     DARC_K_EXP_SQUARE = 0,      /* one squaring of Exp (24 B/voxel/subject)            */
-    DARC_K_EXP_ADJOINT = 1,     /* adjoint of one squaring (36 B/voxel/subject)        */
+    DARC_K_EXP_ADJOINT = 1,     /* adjoint of one squaring: the gather (36 B/voxel)    */
     DARC_K_WARP = 2,            /* warp (20 B/voxel/subject)                           */
     DARC_K_LNCC_FWD = 3,        /* local-NCC forward (28 B/voxel/subject)              */
     DARC_K_LNCC_BWD_WARP_REG = 4,/* NCC adjoint + warp adjoint + regulariser (48 B)    */
     DARC_K_MSE_WARP_REG = 5,    /* fused MSE step (32 B/voxel/subject)                 */
     DARC_K_ADAM = 6,            /* Adam on the velocities (84 B/voxel/subject)         */
     DARC_K_ATLAS = 7,           /* everything of the atlas re-estimate                 */
-    DARC_K_COUNT = 8
+    DARC_K_EXP_FAR = 8,         /* far-source scatter after the gather adjoint (no
+                                 * algorithmic bytes of its own: the step's 36 B
+                                 * are counted on DARC_K_EXP_ADJOINT)                 */
+    DARC_K_COUNT = 9
 } darc_kernel_id;
 
 /* on != 0: later calls on the cohort launch every kernel directly (no graph
@@ -524,7 +539,14 @@ int darc_unet_load(darc_unet* u, const char* path);
  *    returns DARC_ERR_ARG and a message naming the limit.
  *  - The first call on a device looks up the array's device address (one
  *    cudaGetSymbolAddress with that device current); make that first call
- *    before any stream capture on the device.
+ *    before any stream capture on the device.  Under CUDA's default lazy
+ *    module loading the driver also commits the 64 MiB only then (at load
+ *    time with CUDA_MODULE_LOADING=EAGER), so that first call can fail
+ *    with DARC_ERR_CUDA when the device is full: a caller on a fixed budget
+ *    should make one call at start-up.
+ *  - gv_dev may equal gT_dev (the result replaces the incoming gradient);
+ *    any other overlap of gv_dev with v_dev, u_dev or gT_dev returns
+ *    DARC_ERR_ARG.
  *  - All calls share the one array, which keeps the last call's contents;
  *    each call clears what it accumulates into before using it.  Calls
  *    whose work overlaps on the GPU (other streams, unordered threads) race

@@ -1,13 +1,15 @@
 """One kernel family on a small seeded case, for focused profiler captures.
 
-    python -m paper_2508_10743_gb300.kernel_case --kernel exp_adjoint --batch 1
+    python kernel_case.py --kernel exp_adjoint --batch 1
 
 runs `--warmup` untimed launches then `--reps` launches of the chosen
 operator on one or a few brain-shaped subjects (160x192x224 by default) and
 prints the mean CUDA-event time.  Inputs are seeded synthetic fields and
 images; the velocities reach the workload's 6-voxel displacement scale.
+`exp_adjoint` runs one squaring's adjoint (T = 1, so u_0 = v / 2: pass
+`--max-disp 1` for a chain of near sources only, 6 for mostly far ones).
 `cohort_step` runs whole subject updates of a cohort (the squarings, the
-local NCC terms, the interleaved adjoint chain and Adam).  `unet_step`
+local NCC terms, the gather adjoint chain and Adam).  `unet_step`
 times training steps of the warm-start network instead (pass `--shape 80
 96 112`), `unet_forward` its forward pass; the timed launches sit inside an
 NVTX range named "step".
@@ -19,7 +21,14 @@ import json
 
 import torch
 
-from . import configs, darc, synth
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2508_10743_gb300 import configs, darc, synth  # noqa: E402
 
 
 def main():
@@ -34,6 +43,7 @@ def main():
     ap.add_argument("--max-disp", type=float, default=6.0)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--adjoint", choices=["scatter", "gather"], default="scatter")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     shape = tuple(a.shape)
@@ -58,7 +68,8 @@ def main():
     A = synth.random_image(shape, 30, n_ell=12, radii=(4.0, 20.0), device=dev).contiguous()
     u = darc.exp_forward(v, a.T)
     g = torch.randn_like(v) * 1e-3
-    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=a.window, n_squarings=a.T, lam=1.0)
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=a.window, n_squarings=a.T, lam=1.0,
+                             adjoint=0 if a.adjoint == "scatter" else 1)
     cohort = None
     if a.kernel == "cohort_step":
         cohort = darc.Cohort(I, cfg)

@@ -36,6 +36,7 @@ class DarcConfig:
     subject_batch: int = 0      # subjects per launch (0 = all of them)
     reset_each_sweep: int = 0   # 1 = restart v and Adam each sweep (literal Algorithm 1)
     seed: int = 0               # atlas mini-batch shuffling
+    adjoint: int = 0            # squaring adjoint: 0 = scatter (atomics), 1 = gather (+ scatter of moves >= 1 voxel)
 
 
 @dataclasses.dataclass

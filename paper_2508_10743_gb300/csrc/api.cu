@@ -61,6 +61,8 @@ int patch_metric(int d) { return d == DARC_SSIM ? 1 : 0; }
 
 int check_config(const darc_config* c, int D, int H, int W)
 {
+    if (c && c->adjoint != DARC_ADJOINT_SCATTER && c->adjoint != DARC_ADJOINT_GATHER)
+        return fail(DARC_ERR_ARG, "adjoint must be DARC_ADJOINT_SCATTER or DARC_ADJOINT_GATHER");
     if (!c) return fail(DARC_ERR_ARG, "null config");
     if (!pointwise(c->dissim) && !patchwise(c->dissim)) return fail(DARC_ERR_ARG, "unknown dissimilarity");
     if (patchwise(c->dissim)) {
@@ -224,31 +226,45 @@ cudaError_t exp_forward_pingpong(const float* v, float* u2, int cnt, const Vol& 
     return cudaSuccess;
 }
 
-// Adjoint of Exp: gin = gT (planar); the chain runs on interleaved
-// gradients in two ping-pong buffers gbuf [2][cnt][V] float4 (one 16-byte
-// atomic per scattered corner), cleared before each step; the result is
-// unpacked into gv [cnt][3][V], which may be gT.  u holds u_1..u_T (planar,
-// cnt fields per slot).
-cudaError_t exp_backward_all(const float* v, const float* u, const float* gT, float* gv, float4* gbuf,
+// Layout of the adjoint chain's gradient after step t: the last two
+// squarings (the largest displacements, so most far sources) write
+// interleaved float4 gradients for the far scatter's 16-byte atomics; the
+// others and the result (t = 0) are planar, 12 bytes a voxel instead of 16.
+bool adj_out4(int t, int T) { return t > 0 && t >= T - 2; }
+
+// One adjoint step: the gather writes gout, the far scatter adds onto it.
+cudaError_t exp_adjoint_step(const float* src, int src_packed, float scale, const float* gin, int in4, float* gout,
+                             int out4, float out_scale, int* flags, int B, const Vol& v, cudaStream_t s)
+{
+    cudaError_t e = exp_adjoint_gather(src, src_packed, scale, gin, in4, gout, out4, out_scale, flags, B, v, s);
+    if (e != cudaSuccess) return e;
+    return exp_adjoint_far(src, src_packed, scale, gin, in4, gout, out4, out_scale, flags, B, v, s);
+}
+
+// Adjoint of Exp: gin = gT (planar); steps alternate between two
+// [cnt][V] float4-sized buffers gbuf, the last one writes gv [cnt][3][V]
+// (which may be gT: then a one-squaring chain goes through gbuf).  u holds
+// u_1..u_T (planar, cnt fields per slot); flags: exp_far_flags ints.
+cudaError_t exp_backward_all(const float* v, const float* u, const float* gT, float* gv, float4* gbuf, int* flags,
                              int cnt, const Vol& vol, int T, float sign, cudaStream_t s)
 {
     const float s0 = sign * std::ldexp(1.0f, -T);
     const size_t fb = (size_t)cnt * 3 * vol.V;
-    float4* g4[2] = {gbuf, gbuf + (size_t)cnt * vol.V};
+    float* g4[2] = {reinterpret_cast<float*>(gbuf), reinterpret_cast<float*>(gbuf + (size_t)cnt * vol.V)};
     const float* gin = gT;
-    int interleaved = 0;
+    int in4 = 0;
     for (int t = T - 1; t >= 0; --t) {
         const float* src = (t == 0) ? v : u + (size_t)(t - 1) * fb;
         const float scale = (t == 0) ? s0 : 1.f;
-        float4* gout = g4[(T - 1 - t) % 2];
-        cudaError_t e = cudaMemsetAsync(gout, 0, (size_t)cnt * vol.V * sizeof(float4), s);
+        const int out4 = adj_out4(t, T);
+        float* gout = (t == 0 && (gv != gT || T > 1)) ? gv : g4[(T - 1 - t) % 2];
+        cudaError_t e = exp_adjoint_step(src, 0, scale, gin, in4, gout, out4, scale, flags, cnt, vol, s);
         if (e != cudaSuccess) return e;
-        e = exp_square_adjoint4(src, 0, scale, gin, interleaved, gout, scale, cnt, vol, s);
-        if (e != cudaSuccess) return e;
-        gin = reinterpret_cast<const float*>(gout);
-        interleaved = 1;
+        gin = gout;
+        in4 = out4;
     }
-    return unpack_field(g4[(T - 1) % 2], gv, cnt, vol, s);
+    if (gin != gv) return cudaMemcpyAsync(gv, gin, sizeof(float) * fb, cudaMemcpyDeviceToDevice, s);
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -279,6 +295,7 @@ struct darc_cohort {
     float* astats = nullptr;     // [2][V]
     // scratch
     float *u_all = nullptr, *gT = nullptr, *gbuf = nullptr, *Wimg = nullptr, *coef = nullptr;
+    int* eflags = nullptr;       // far-source tile marks of the Exp adjoint (exp_far_flags)
     double *pL = nullptr, *pR = nullptr, *acc = nullptr, *cpart = nullptr, *cmetrics = nullptr;
     float *Wcache = nullptr, *Am = nullptr, *As = nullptr, *gA = nullptr, *aloss = nullptr;
     float *jstats = nullptr, *gsh = nullptr;   // [n][2][V] window stats of W_i; [V] shared gradient
@@ -405,8 +422,10 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     cudaError_t e = cudaSuccess;
     const float s0 = std::ldexp(1.0f, -T);
     const CkPlan plan(T, c->cfg.checkpoint_stride);
-    // adjoint outputs: one cleared [cnt][V] float4 buffer per squaring (gbuf
-    // slot t for step t), cleared by the forward squaring t on its way
+    // adjoint outputs: one [cnt][V] float4-sized buffer per squaring (gbuf
+    // slot t for step t).  The gather adjoint writes every voxel; the
+    // scatter adjoint adds into a slot that its forward squaring cleared.
+    const bool gather = c->cfg.adjoint == DARC_ADJOINT_GATHER;
     float4* const g4 = reinterpret_cast<float4*>(c->gbuf);
     auto gslot = [&](int t) { return g4 + (size_t)t * cnt * vol.V; };
     auto sq = [&](const float* src, float scale, float* dst) {
@@ -420,7 +439,7 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
         c->launches += 1;
         return exp_square_packed(src, src != vb, scale, reinterpret_cast<float4*>(dst), cnt, vol, s, gslot(tf++));
     };
-    e = exp_forward_plan(plan, vb, c->u_all, fb, s0, sq_clear);
+    e = gather ? exp_forward_plan(plan, vb, c->u_all, fb, s0, sq) : exp_forward_plan(plan, vb, c->u_all, fb, s0, sq_clear);
     if (e != cudaSuccess) return e;
     const float* uT = c->u_all + (size_t)plan.slot(T - 1) * fb;
     const double *pLp, *pRp;
@@ -453,23 +472,41 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     e = finish_step(pLp, nL, sL, pRp, nR, sR, c->loss + 2 * f, c->flags + f, c->k + f, c->bias + f,
                     c->nonfinite, c->cfg.lr, c->cfg.beta1, c->cfg.beta2, cnt, s);
     if (e != cudaSuccess) return e;
-    // the adjoint chain runs on interleaved gradients (one float4 a voxel, so a
-    // scattered corner is one 16-byte atomic): step t adds into gbuf slot t,
-    // which the forward cleared; gT (planar) is its input, the last output
-    // feeds Adam
-    const float4* gv = nullptr;
+    // the adjoint chain: gT (planar) is its input; step t writes gbuf slot t
+    // (interleaved or planar, adj_out4), the last one (planar) feeds Adam
+    const float* gv = nullptr;
+    int gv4 = 0;
     {
         const float* gin = c->gT;
-        int interleaved = 0;
+        int in4 = 0;
         auto adj = [&](int t, const float* src, float scale) {
-            float4* gout = gslot(t);
-            cudaError_t err = cudaSuccess;
-            Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
-            c->launches += 1;
-            err = exp_square_adjoint4(src, t != 0, scale, gin, interleaved, gout, scale, cnt, vol, s);
-            gin = reinterpret_cast<const float*>(gout);
-            interleaved = 1;
+            float* gout = reinterpret_cast<float*>(gslot(t));
+            cudaError_t err;
+            if (!gather) {
+                // interleaved gradients, one 16-byte atomic per scattered corner
+                Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
+                c->launches += 1;
+                err = exp_square_adjoint4(src, t != 0, scale, gin, in4, gslot(t), scale, cnt, vol, s);
+                gin = gout;
+                in4 = 1;
+                gv = gout;
+                gv4 = 1;
+                return err;
+            }
+            const int out4 = adj_out4(t, T);
+            {
+                Prof p(c, s, DARC_K_EXP_ADJOINT, 36.0 * nv);
+                err = exp_adjoint_gather(src, t != 0, scale, gin, in4, gout, out4, scale, c->eflags, cnt, vol, s);
+            }
+            if (err == cudaSuccess) {
+                Prof p(c, s, DARC_K_EXP_FAR, 0.0);
+                err = exp_adjoint_far(src, t != 0, scale, gin, in4, gout, out4, scale, c->eflags, cnt, vol, s);
+            }
+            c->launches += 2;
+            gin = gout;
+            in4 = out4;
             gv = gout;
+            gv4 = out4;
             return err;
         };
         e = exp_backward_plan(plan, vb, c->u_all, fb, s0, sq, adj);
@@ -477,8 +514,14 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
     if (e != cudaSuccess) return e;
     Prof p(c, s, DARC_K_ADAM, 84.0 * nv);
     c->launches += 2;
-    return adam_fields_g4(c->v + (size_t)f * 3 * vol.V, c->m + (size_t)f * 3 * vol.V, c->s + (size_t)f * 3 * vol.V,
-                          gv, c->bias + f, c->flags + f, c->cfg.beta1, c->cfg.beta2, c->cfg.adam_eps, cnt, vol.V, s);
+    float* vf = c->v + (size_t)f * 3 * vol.V;
+    float* mf = c->m + (size_t)f * 3 * vol.V;
+    float* sf = c->s + (size_t)f * 3 * vol.V;
+    if (gv4)
+        return adam_fields_g4(vf, mf, sf, reinterpret_cast<const float4*>(gv), c->bias + f, c->flags + f,
+                              c->cfg.beta1, c->cfg.beta2, c->cfg.adam_eps, cnt, vol.V, s);
+    return adam_fields(vf, mf, sf, gv, 1.f, c->bias + f, c->flags + f, c->cfg.beta1, c->cfg.beta2, c->cfg.adam_eps,
+                       cnt, 3 * vol.V, s);
 }
 
 int run_steps(darc_cohort* c, int first, int count, int steps)
@@ -814,6 +857,7 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
     // one interleaved float4 gradient set per squaring (at least two planar
     // field slots for the inverse-map scratch of the diffeomorphism report)
     ALLOC(c->gbuf, 4 * (size_t)v.V * c->bmax * std::max(T, 2));
+    ALLOC(c->eflags, exp_far_flags(c->bmax, v));
     ALLOC(c->pL, 2 * (size_t)nb * bsub);
     ALLOC(c->pR, (size_t)nb * bsub);
     ALLOC(c->acc, v.V);
@@ -854,6 +898,7 @@ int darc_init_cohort(darc_cohort** out, const darc_config* cfg, int n, int D, in
         cudaMemsetAsync(c->s, 0, sizeof(float) * F * n, s) == cudaSuccess &&
         cudaMemsetAsync(c->k, 0, sizeof(int) * n, s) == cudaSuccess &&
         cudaMemsetAsync(c->flags, 0, sizeof(int) * n, s) == cudaSuccess &&
+        cudaMemsetAsync(c->eflags, 0, sizeof(int) * exp_far_flags(c->bmax, v), s) == cudaSuccess &&
         cudaMemsetAsync(c->nonfinite, 0, sizeof(int), s) == cudaSuccess &&
         cudaMemsetAsync(c->loss, 0, sizeof(float) * 2 * n, s) == cudaSuccess &&
         cudaMemsetAsync(c->cmetrics, 0, sizeof(double) * 2, s) == cudaSuccess &&
@@ -1426,7 +1471,8 @@ int darc_exp_forward(const float* v_dev, float* u_dev, int B, int D, int H, int 
 
 size_t darc_exp_backward_workspace(int B, int D, int H, int W)
 {
-    return 2 * align256(sizeof(float4) * (size_t)B * D * H * W);
+    return 2 * align256(sizeof(float4) * (size_t)B * D * H * W) +
+           align256(sizeof(int) * exp_far_flags(B, make_vol(D, H, W)));
 }
 
 int darc_exp_backward(const float* v_dev, const float* u_dev, const float* gT_dev, float* gv_dev, void* work_dev,
@@ -1439,7 +1485,11 @@ int darc_exp_backward(const float* v_dev, const float* u_dev, const float* gT_de
     const Vol v = make_vol(D, H, W);
     Carve cv(work_dev);
     float4* gbuf = reinterpret_cast<float4*>(cv.take<float>(2 * 4 * (size_t)B * v.V));
-    CK(exp_backward_all(v_dev, u_dev, gT_dev, gv_dev, gbuf, B, v, T, sign, (cudaStream_t)stream));
+    int* flags = cv.take<int>(exp_far_flags(B, v));
+    // the marks only steer which tiles the far scatter visits; clearing them
+    // keeps the first step from visiting every tile of a reused workspace
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * exp_far_flags(B, v), (cudaStream_t)stream));
+    CK(exp_backward_all(v_dev, u_dev, gT_dev, gv_dev, gbuf, flags, B, v, T, sign, (cudaStream_t)stream));
     return DARC_OK;
 }
 
@@ -1591,7 +1641,8 @@ size_t darc_subject_grad_workspace(const darc_config* cfg, int B, int D, int H, 
     const size_t fields = (size_t)CkPlan(T, cfg->checkpoint_stride).fields();
     return align256(sizeof(float) * F4 * fields) + align256(sizeof(float) * F) + align256(sizeof(float) * 2 * F4) +
            align256(sizeof(float) * V * B) + align256(sizeof(float) * 3 * V * B) + align256(sizeof(float) * 2 * V) +
-           2 * darc_loss_workspace(B, D, H, W) + align256(sizeof(float) * 3 * V * B);
+           2 * darc_loss_workspace(B, D, H, W) + align256(sizeof(float) * 3 * V * B) +
+           align256(sizeof(int) * exp_far_flags(B, make_vol(D, H, W)));
 }
 
 int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A_dev, const float* v_dev,
@@ -1608,8 +1659,8 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     const size_t F = 3 * (size_t)v.V * B, F4 = 4 * (size_t)v.V * B;
     Carve cv(work_dev);
     const CkPlan plan(T, cfg->checkpoint_stride);
-    // packed squaring fields and interleaved adjoint gradients, as in the
-    // cohort's step; the result is unpacked into the planar gv
+    // packed squaring fields and the gather adjoint chain, as in the cohort's
+    // step; the last adjoint step writes the planar gv
     float* u_all = cv.take<float>(F4 * plan.fields());
     float* gT = cv.take<float>(F);
     float4* gbuf = reinterpret_cast<float4*>(cv.take<float>(2 * F4));
@@ -1619,6 +1670,8 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
     double* pL = cv.take<double>(2 * (size_t)B * nblk_max(v));
     double* pR = cv.take<double>(2 * (size_t)B * nblk_max(v));
     float* P = cv.take<float>(3 * (size_t)B * v.V);
+    int* flags = cv.take<int>(exp_far_flags(B, v));
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * exp_far_flags(B, v), s));
     const float s0 = std::ldexp(1.0f, -T);
     auto sq = [&](const float* src, float scale, float* dst) {
         return exp_square_packed(src, src != v_dev, scale, reinterpret_cast<float4*>(dst), B, v, s);
@@ -1638,22 +1691,32 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
         CK(reduce_partials(pL, box_blocks(v), 1, 1.0, energy_dev, 2, B, s));
         CK(reduce_partials(pR, box_blocks(v), 1, 1.0, energy_dev + 1, 2, B, s));
     }
-    float4* g4[2] = {gbuf, gbuf + (size_t)B * v.V};
+    // gradients alternate between the two gbuf halves; the last step writes gv
+    // (the scatter adjoint: into a cleared interleaved buffer, then unpacked)
+    const bool gather = cfg->adjoint == DARC_ADJOINT_GATHER;
+    float* g4[2] = {reinterpret_cast<float*>(gbuf), reinterpret_cast<float*>(gbuf + (size_t)B * v.V)};
     const float* gin = gT;
-    int interleaved = 0;
-    const float4* last = nullptr;
+    int in4 = 0;
+    const float* last = nullptr;
     auto adj = [&](int t, const float* src, float scale) {
-        float4* gout = g4[(T - 1 - t) % 2];
-        cudaError_t e = cudaMemsetAsync(gout, 0, (size_t)B * v.V * sizeof(float4), s);
-        if (e != cudaSuccess) return e;
-        e = exp_square_adjoint4(src, t != 0, scale, gin, interleaved, gout, scale, B, v, s);
-        gin = reinterpret_cast<const float*>(gout);
-        interleaved = 1;
-        last = gout;
+        cudaError_t e;
+        if (!gather) {
+            float4* gout = reinterpret_cast<float4*>(g4[(T - 1 - t) % 2]);
+            e = cudaMemsetAsync(gout, 0, (size_t)B * v.V * sizeof(float4), s);
+            if (e == cudaSuccess) e = exp_square_adjoint4(src, t != 0, scale, gin, in4, gout, scale, B, v, s);
+            gin = last = reinterpret_cast<const float*>(gout);
+            in4 = 1;
+            return e;
+        }
+        const int out4 = adj_out4(t, T);
+        float* gout = t == 0 ? gv_dev : g4[(T - 1 - t) % 2];
+        e = exp_adjoint_step(src, t != 0, scale, gin, in4, gout, out4, scale, flags, B, v, s);
+        gin = gout;
+        in4 = out4;
         return e;
     };
     CK(exp_backward_plan(plan, v_dev, u_all, F4, s0, sq, adj));
-    CK(unpack_field(last, gv_dev, B, v, s));
+    if (!gather) CK(unpack_field(reinterpret_cast<const float4*>(last), gv_dev, B, v, s));
     return DARC_OK;
 }
 

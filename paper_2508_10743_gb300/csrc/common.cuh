@@ -62,6 +62,40 @@ __device__ __forceinline__ Cell make_cell(int z, int y, int x, float uz, float u
     return c;
 }
 
+// Whether make_cell reduces to its unclamped case at this voxel: every
+// coordinate at least one voxel inside the faces and every |u_a| < 1, so
+// x_a + u_a lies strictly inside (0, n_a - 1) and no axis clamps.
+__device__ __forceinline__ bool interior_near(int z, int y, int x, float uz, float uy, float ux, const Vol& v)
+{
+    return z >= 1 && z <= v.D - 2 && y >= 1 && y <= v.H - 2 && x >= 1 && x <= v.W - 2 && fabsf(uz) < 1.f &&
+           fabsf(uy) < 1.f && fabsf(ux) < 1.f;
+}
+
+// make_cell where interior_near holds (the same floats, without the clamps)
+__device__ __forceinline__ Cell make_cell_inner(int z, int y, int x, float uz, float uy, float ux, const Vol& v)
+{
+    Cell c;
+    const float fz = floorf(uz), fy = floorf(uy), fx = floorf(ux);
+    c.iz = z + (int)fz;
+    c.iy = y + (int)fy;
+    c.ix = x + (int)fx;
+    c.tz = uz - fz;
+    c.ty = uy - fy;
+    c.tx = ux - fx;
+    c.cz = c.cy = c.cx = false;
+    c.base = (c.iz * v.H + c.iy) * v.W + c.ix;
+    return c;
+}
+
+// make_cell, in the short form when every lane running it together
+// qualifies (both forms give the same cell where interior_near holds)
+__device__ __forceinline__ Cell make_cell_warp(int z, int y, int x, float uz, float uy, float ux, const Vol& v)
+{
+    if (__all_sync(__activemask(), interior_near(z, y, x, uz, uy, ux, v)))
+        return make_cell_inner(z, y, x, uz, uy, ux, v);
+    return make_cell(z, y, x, uz, uy, ux, v);
+}
+
 // Trilinear value at the cell from its 8 corner values (corner order
 // (dz, dy, dx) = 000, 001, 010, ...).
 __device__ __forceinline__ float tri_corners(const Cell& c, float f000, float f001, float f010, float f011,
@@ -176,6 +210,41 @@ struct PackedField {
         tri_grad_corners(c, f[0].z, f[1].z, f[2].z, f[3].z, f[4].z, f[5].z, f[6].z, f[7].z, d[2][0], d[2][1], d[2][2]);
     }
 };
+
+// J^T g for a packed field: with J = dS(u, p)/dp at the cell (3 x 3,
+// channel by axis) and g a 3-vector, (J^T g)_a = d/dp_a of the trilinear
+// interpolation of the corner dot products g . u(corner) (S is linear in the
+// corner values), zero along clamped axes.
+__device__ __forceinline__ float3 packed_jac_t(const PackedField& f, const Cell& c, const Vol& v, float3 g)
+{
+    float4 q[8];
+    f.corners(c, v, q);
+    float d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = fmaf(g.x, q[k].x, fmaf(g.y, q[k].y, g.z * q[k].z));
+    float jz, jy, jx;
+    tri_grad_corners(c, d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], jz, jy, jx);
+    return make_float3(jz, jy, jx);
+}
+
+// J^T g of a planar field: the 3 x 3 derivatives, then the product
+__device__ __forceinline__ float3 planar_jac_t(const PlanarField& f, const Cell& c, const Vol& v, float3 g)
+{
+    float d[3][3];
+    f.grad(c, v, d);
+    return make_float3(g.x * d[0][0] + g.y * d[1][0] + g.z * d[2][0], g.x * d[0][1] + g.y * d[1][1] + g.z * d[2][1],
+                       g.x * d[0][2] + g.y * d[1][2] + g.z * d[2][2]);
+}
+
+__device__ __forceinline__ float3 field_jac_t(const PackedField& f, const Cell& c, const Vol& v, float3 g)
+{
+    return packed_jac_t(f, c, v, g);
+}
+
+__device__ __forceinline__ float3 field_jac_t(const PlanarField& f, const Cell& c, const Vol& v, float3 g)
+{
+    return planar_jac_t(f, c, v, g);
+}
 
 // The 8 trilinear weights in corner order (dz, dy, dx) = 000, 001, 010, ...
 __device__ __forceinline__ void tri_weights(const Cell& c, float w[8])

@@ -260,13 +260,35 @@ __device__ __forceinline__ void emit4_xpair(float4* o, int a, bool act, float4 l
     if (!given) atomicAdd(o + a + 1, hi);
 }
 
+// Far-source scatter after the gather adjoint (k_exp_gather.cu): a block
+// runs only if the gather marked its tile (the mark is cleared here), and
+// only sources with |u_a| >= 1 on some axis (or not finite) scatter.
+__device__ __forceinline__ bool far_tile(int* flags)
+{
+    __shared__ int mark;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const size_t bid = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        mark = flags[bid];
+        if (mark) flags[bid] = 0;
+    }
+    __syncthreads();
+    return mark != 0;
+}
+
+__device__ __forceinline__ bool near_source(float uz, float uy, float ux)
+{
+    return fabsf(uz) < 1.f && fabsf(uy) < 1.f && fabsf(ux) < 1.f;
+}
+
 // IN4: the incoming gradient is interleaved too (else planar [3][V]); the
-// outgoing one is always interleaved [V] float4 per field.
-template <bool IN4, class Src>
+// outgoing one is always interleaved [V] float4 per field.  FAR: only the
+// transpose terms of far sources, in marked tiles (flags).
+template <bool IN4, class Src, bool FAR = false>
 __global__ void __launch_bounds__(VT_THREADS)
 exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ gin,
-                           float4* __restrict__ gout, float out_scale, Vol v, int nzt)
+                           float4* __restrict__ gout, float out_scale, Vol v, int nzt, int* flags = nullptr)
 {
+    if (FAR && !far_tile(flags)) return;
     const int lane = threadIdx.x;
     const int x = blockIdx.x * VT_X + threadIdx.x;
     const int y = blockIdx.y * VT_Y + threadIdx.y;
@@ -281,14 +303,18 @@ exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ g
     int ca = -1;                     // base index of the carried pairs (-1: none)
     for (int k = 0; k < ADJ_Z; ++k) {
         const int z = zt * ADJ_Z + k;
-        const bool active = xy_ok && z < v.D;
+        bool active = xy_ok && z < v.D;
         float w[8];
         float4 gs = make_float4(0.f, 0.f, 0.f, 0.f);
         int cb = -4;
+        float3 u = make_float3(0.f, 0.f, 0.f);
+        const int l = z * plane + y * v.W + x;
         if (active) {
-            const int l = z * plane + y * v.W + x;
-            const float3 u = f.own(l);
-            const Cell c = make_cell(z, y, x, scale * u.x, scale * u.y, scale * u.z, v);
+            u = f.own(l);
+            if (FAR && near_source(scale * u.x, scale * u.y, scale * u.z)) active = false;
+        }
+        if (active) {
+            const Cell c = make_cell_warp(z, y, x, scale * u.x, scale * u.y, scale * u.z, v);
             float gz, gy, gx;
             if (IN4) {
                 const float4 g4 = __ldg(reinterpret_cast<const float4*>(g0) + l);
@@ -300,15 +326,12 @@ exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ g
                 gy = __ldg(g0 + v.V + l);
                 gx = __ldg(g0 + 2 * v.V + l);
             }
-            float d[3][3];
-            f.grad(c, v, d);
-            const float dz0 = d[0][0], dy0 = d[0][1], dx0 = d[0][2];
-            const float dz1 = d[1][0], dy1 = d[1][1], dx1 = d[1][2];
-            const float dz2 = d[2][0], dy2 = d[2][1], dx2 = d[2][2];
-            // identity + Jacobian term at the source voxel itself (scale: du_t = scale d src)
-            atomicAdd(o + l, make_float4((gz + scale * (gz * dz0 + gy * dz1 + gx * dz2)) * out_scale,
-                                         (gy + scale * (gz * dy0 + gy * dy1 + gx * dy2)) * out_scale,
-                                         (gx + scale * (gz * dx0 + gy * dx1 + gx * dx2)) * out_scale, 0.f));
+            if (!FAR) {
+                // identity + Jacobian term at the source voxel itself (scale: du_t = scale d src)
+                const float3 jt = field_jac_t(f, c, v, make_float3(gz, gy, gx));
+                atomicAdd(o + l, make_float4(fmaf(scale, jt.x, gz) * out_scale, fmaf(scale, jt.y, gy) * out_scale,
+                                             fmaf(scale, jt.z, gx) * out_scale, 0.f));
+            }
             tri_weights(c, w);
             gs = make_float4(gz * out_scale, gy * out_scale, gx * out_scale, 0.f);
             cb = c.base;
@@ -346,6 +369,55 @@ exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ g
     }
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) emit4_xpair(o, ca + dy * v.W, ca >= 0, cl[dy], cu[dy], lane);
+}
+
+// Far-source transpose terms onto planar gradients [B][3][V]: one atomic per
+// corner and channel (far sources are few where this layout is used).
+template <bool IN4, class Src>
+__global__ void __launch_bounds__(VT_THREADS)
+exp_far_planar_kernel(Src src_all, float scale, const float* __restrict__ gin, float* __restrict__ gout,
+                      float out_scale, Vol v, int nzt, int* flags)
+{
+    if (!far_tile(flags)) return;
+    const int x = blockIdx.x * VT_X + threadIdx.x;
+    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int zt = blockIdx.z % nzt;
+    const int b = blockIdx.z / nzt;
+    if (x >= v.W || y >= v.H) return;
+    const Src f = src_all.subject(b);
+    const float* g0 = gin + (size_t)b * (IN4 ? 4 : 3) * v.V;
+    float* o = gout + (size_t)b * 3 * v.V;
+    const int plane = v.H * v.W;
+    for (int k = 0; k < ADJ_Z; ++k) {
+        const int z = zt * ADJ_Z + k;
+        if (z >= v.D) break;
+        const int l = z * plane + y * v.W + x;
+        const float3 u = f.own(l);
+        const float uz = scale * u.x, uy = scale * u.y, ux = scale * u.z;
+        if (near_source(uz, uy, ux)) continue;
+        const Cell c = make_cell(z, y, x, uz, uy, ux, v);
+        float gz, gy, gx;
+        if (IN4) {
+            const float4 g4 = __ldg(reinterpret_cast<const float4*>(g0) + l);
+            gz = g4.x;
+            gy = g4.y;
+            gx = g4.z;
+        } else {
+            gz = __ldg(g0 + l);
+            gy = __ldg(g0 + v.V + l);
+            gx = __ldg(g0 + 2 * v.V + l);
+        }
+        float w[8];
+        tri_weights(c, w);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int a = c.base + ((q >> 2) & 1) * plane + ((q >> 1) & 1) * v.W + (q & 1);
+            const float s = w[q] * out_scale;
+            atomicAdd(o + a, s * gz);
+            atomicAdd(o + v.V + a, s * gy);
+            atomicAdd(o + 2 * v.V + a, s * gx);
+        }
+    }
 }
 
 // g[b][c][l] = g4[b][l].c: an interleaved gradient back to planar fields
@@ -433,6 +505,42 @@ cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, c
                         out_scale, grid, v, nzt, s);
     else
         launch_adjoint4(PlanarField{src, v.V}, scale, gin, gin_interleaved, gout, out_scale, grid, v, nzt, s);
+    return cudaGetLastError();
+}
+
+template <class Src>
+void launch_far(Src f, float scale, const float* gin, int in4, float* gout, int out4, float out_scale, int* flags,
+                dim3 grid, const Vol& v, int nzt, cudaStream_t s)
+{
+    const dim3 block(VT_X, VT_Y);
+    float4* g4 = reinterpret_cast<float4*>(gout);
+    if (out4 && in4)
+        exp_square_adjoint4_kernel<true, Src, true><<<grid, block, 0, s>>>(f, scale, gin, g4, out_scale, v, nzt, flags);
+    else if (out4)
+        exp_square_adjoint4_kernel<false, Src, true><<<grid, block, 0, s>>>(f, scale, gin, g4, out_scale, v, nzt, flags);
+    else if (in4)
+        exp_far_planar_kernel<true, Src><<<grid, block, 0, s>>>(f, scale, gin, gout, out_scale, v, nzt, flags);
+    else
+        exp_far_planar_kernel<false, Src><<<grid, block, 0, s>>>(f, scale, gin, gout, out_scale, v, nzt, flags);
+}
+
+cudaError_t exp_adjoint_far(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
+                            float* gout, int gout_interleaved, float out_scale, int* flags, int B, const Vol& v,
+                            cudaStream_t s)
+{
+    static_assert(ADJ_Z == 8 && VT_X == 32 && VT_Y == 8, "far-scatter blocks are the gather's 32 x 8 x 8 mark tiles");
+    if ((src_packed && (reinterpret_cast<uintptr_t>(src) & 15)) ||
+        (gin_interleaved && (reinterpret_cast<uintptr_t>(gin) & 15)) ||
+        (gout_interleaved && (reinterpret_cast<uintptr_t>(gout) & 15)))
+        return cudaErrorMisalignedAddress;
+    int nzt;
+    const dim3 grid = voxel_grid(B, v, nzt, ADJ_Z);
+    if (src_packed)
+        launch_far(PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, gin, gin_interleaved, gout,
+                   gout_interleaved, out_scale, flags, grid, v, nzt, s);
+    else
+        launch_far(PlanarField{src, v.V}, scale, gin, gin_interleaved, gout, gout_interleaved, out_scale, flags, grid,
+                   v, nzt, s);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,22 @@ cudaError_t exp_square_adjoint(const float* src, float scale, const float* gin, 
 // field src likewise packed (src_packed != 0) or planar.
 cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
                                 float4* gout, float out_scale, int B, const Vol& v, cudaStream_t s);
+// Scatter-free adjoint of one squaring (k_exp_gather.cu): gout = out_scale *
+// (identity + Jacobian terms + transpose terms of the near sources, |u_a| < 1
+// on every axis), written once with plain stores (no clearing needed); the
+// 32 x 8 x 8 tiles holding far sources are marked in flags
+// (exp_far_flags(B, v) ints).  exp_adjoint_far then adds the far sources'
+// transpose terms onto gout with atomics, visiting marked tiles only and
+// clearing their marks.  gin / gout: interleaved [B][V] float4 (z, y, x, 0)
+// (16-byte aligned) when *_interleaved, else planar [B][3][V]; src packed
+// likewise when src_packed; u = scale * src.
+size_t exp_far_flags(int B, const Vol& v);
+cudaError_t exp_adjoint_gather(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
+                               float* gout, int gout_interleaved, float out_scale, int* flags, int B, const Vol& v,
+                               cudaStream_t s);
+cudaError_t exp_adjoint_far(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
+                            float* gout, int gout_interleaved, float out_scale, int* flags, int B, const Vol& v,
+                            cudaStream_t s);
 // g [B][3][V] from an interleaved gradient g4 [B][V] float4 (z, y, x, 0)
 cudaError_t unpack_field(const float4* g4, float* g, int B, const Vol& v, cudaStream_t s);
 // One squaring written packed: dst [B][V] float4 (z, y, x, 0), 16-byte

@@ -7,7 +7,10 @@
 // they cannot hand over a workspace either.  darc_exp_backward_noalloc
 // therefore keeps its scratch (the two gradient buffers the adjoint
 // alternates between) in one file-scope device array of fixed size.  Every
-// GPU that loads the library holds that array until the process exits.
+// GPU that loads the library holds that array until the process exits; with
+// CUDA's default lazy module loading the driver commits it when the first
+// call on a device looks its address up (at load time when
+// CUDA_MODULE_LOADING=EAGER).
 #include "../../include/darc.h"
 #include "kernels.h"
 
@@ -49,6 +52,12 @@ int scratch_address(float** out)
     return DARC_OK;
 }
 
+bool overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
 }  // namespace
 
 extern "C" int darc_exp_backward_noalloc(const float* v_dev, const float* u_dev, const float* gT_dev,
@@ -67,6 +76,13 @@ extern "C" int darc_exp_backward_noalloc(const float* v_dev, const float* u_dev,
                               " voxels; use darc_exp_backward with a workspace");
     if ((long long)div_up(D, VT_Z) * B > 65535)
         return darc_impl::report_error(DARC_ERR_SHAPE, "batch x depth too large for one launch");
+    // the last step reads its inputs while it writes gv: gv may replace gT
+    // exactly, and must not touch v, u or only part of gT
+    const size_t field_bytes = sizeof(float) * 3 * (size_t)voxels;
+    if (overlap(gv_dev, field_bytes, v_dev, field_bytes) ||
+        overlap(gv_dev, field_bytes, u_dev, field_bytes * (size_t)T) ||
+        (gv_dev != gT_dev && overlap(gv_dev, field_bytes, gT_dev, field_bytes)))
+        return darc_impl::report_error(DARC_ERR_ARG, "darc_exp_backward_noalloc: gv overlaps v, u or part of gT");
     float* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != DARC_OK) return rc;

@@ -27,6 +27,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdarc.so")
 
 DARC_OK, DARC_ERR_ARG, DARC_ERR_SHAPE, DARC_ERR_OOM, DARC_ERR_CUDA, DARC_ERR_NONFINITE, \
     DARC_ERR_IO, DARC_ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
+# largest B*D*H*W of one darc_exp_backward_noalloc call (include/darc.h)
+DARC_NOALLOC_MAX_VOXELS = 2796202
 
 
 class DarcError(RuntimeError):
@@ -44,7 +46,7 @@ class CConfig(ctypes.Structure):
         ("inner_steps", ctypes.c_int), ("atlas_epochs", ctypes.c_int), ("atlas_batch", ctypes.c_int),
         ("center_mode", ctypes.c_int), ("checkpoint_stride", ctypes.c_int),
         ("subject_batch", ctypes.c_int), ("reset_each_sweep", ctypes.c_int),
-        ("seed", ctypes.c_ulonglong),
+        ("seed", ctypes.c_ulonglong), ("adjoint", ctypes.c_int),
     ]
 
 
@@ -140,7 +142,7 @@ _SIGS = {
 }
 
 KERNEL_IDS = {"exp_square": 0, "exp_adjoint": 1, "warp": 2, "lncc_fwd": 3, "lncc_bwd_warp_reg": 4,
-              "mse_warp_reg": 5, "adam": 6, "atlas": 7}
+              "mse_warp_reg": 5, "adam": 6, "atlas": 7, "exp_far": 8}
 
 _lib = None
 _lock = threading.Lock()
@@ -189,7 +191,7 @@ def to_cconfig(cfg: configs.DarcConfig) -> CConfig:
     return CConfig(cfg.dissim, cfg.ncc_window, cfg.n_squarings, cfg.lam, cfg.lr, cfg.beta1,
                    cfg.beta2, cfg.adam_eps, cfg.ncc_eps, cfg.inner_steps, cfg.atlas_epochs,
                    cfg.atlas_batch, cfg.center_mode, cfg.checkpoint_stride, cfg.subject_batch,
-                   cfg.reset_each_sweep, cfg.seed)
+                   cfg.reset_each_sweep, cfg.seed, cfg.adjoint)
 
 
 def version() -> str:
@@ -436,15 +438,27 @@ def exp_backward_noalloc(v: torch.Tensor, u: torch.Tensor, gT: torch.Tensor, sig
                          out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """darc_exp_backward without a workspace: for callers that cannot allocate
     device memory (the library keeps a fixed 64 MiB device array instead).
-    `out` lets such a caller pass a preallocated result buffer."""
-    for t, nm in ((v, "v"), (u, "u"), (gT, "gT")):
+    `out` lets such a caller pass a preallocated result buffer; it may be gT.
+    Shapes: v, gT, out [B, 3, D, H, W]; u [T, B, 3, D, H, W], 1 <= T <= 20;
+    all on one CUDA device (the call runs with that device current)."""
+    if v.dim() != 5 or v.shape[1] != 3:
+        raise ValueError(f"v must have shape [B, 3, D, H, W], got {tuple(v.shape)}")
+    if tuple(gT.shape) != tuple(v.shape):
+        raise ValueError(f"gT shape {tuple(gT.shape)} differs from v's {tuple(v.shape)}")
+    if u.dim() != 6 or tuple(u.shape[1:]) != tuple(v.shape) or not 1 <= u.shape[0] <= 20:
+        raise ValueError(f"u must have shape [T, *v.shape] with 1 <= T <= 20, got {tuple(u.shape)}")
+    if out is not None and tuple(out.shape) != tuple(v.shape):
+        raise ValueError(f"out shape {tuple(out.shape)} differs from v's {tuple(v.shape)}")
+    for t, nm in ((v, "v"), (u, "u"), (gT, "gT")) + (((out, "out"),) if out is not None else ()):
         _need(t, nm)
+    if len({t.device for t in (v, u, gT) + ((out,) if out is not None else ())}) != 1:
+        raise ValueError("v, u, gT and out must be on one device")
     B = v.shape[0]
     D, H, W = _dims(v)
-    gv = torch.empty_like(v) if out is None else out
-    _need(gv, "out")
-    _check(lib().darc_exp_backward_noalloc(_ptr(v), _ptr(u), _ptr(gT), _ptr(gv), B, D, H, W, u.shape[0],
-                                           sign, _stream()))
+    with torch.cuda.device(v.device):
+        gv = torch.empty_like(v) if out is None else out
+        _check(lib().darc_exp_backward_noalloc(_ptr(v), _ptr(u), _ptr(gT), _ptr(gv), B, D, H, W, u.shape[0],
+                                               sign, ctypes.c_void_p(torch.cuda.current_stream(v.device).cuda_stream)))
     return gv
 
 

@@ -45,12 +45,13 @@ def test_binding_covers_the_header(darc):
 
 
 def test_struct_layouts(darc):
-    assert ctypes.sizeof(darc.CConfig) == 72
-    assert darc.CConfig.seed.offset == 64
+    assert ctypes.sizeof(darc.CConfig) == 80
+    assert darc.CConfig.seed.offset == 64 and darc.CConfig.adjoint.offset == 72
     assert ctypes.sizeof(darc.CSweepStats) == 48
     c = darc.default_config()
     assert (c.dissim, c.ncc_window, c.n_squarings) == (1, 9, 7)
     assert c.lr == pytest.approx(1e-2) and c.atlas_epochs == 20 and c.atlas_batch == 4
+    assert c.adjoint == 0
     assert "sm_103a" in darc.version()
 
 
@@ -77,8 +78,10 @@ def test_host_argument_checks(darc):
 
 def test_workspace_queries_are_host_only(darc):
     L = darc.lib()
-    # two interleaved gradient buffers, one float4 a voxel
-    assert L.darc_exp_backward_workspace(2, 8, 8, 8) == 2 * (2 * 512 * 16)
+    # two gradient buffers of one float4 a voxel, then one int per 32 x 8 x 8
+    # tile marking far sources (256-byte aligned pieces)
+    assert L.darc_exp_backward_workspace(2, 8, 8, 8) == 2 * (2 * 512 * 16) + 256
+    assert L.darc_exp_backward_workspace(1, 20, 40, 70) == 2 * (20 * 40 * 70 * 16) + 256 * ((4 * 3 * 5 * 3 + 255) // 256)
     assert L.darc_lncc_workspace(1, 16, 16, 16) > 4 * 16 ** 3 * 6
     cfg = darc.default_config()
     assert L.darc_subject_grad_workspace(ctypes.byref(cfg), 1, 16, 16, 16) > 4 * 3 * 16 ** 3 * 7
@@ -109,3 +112,36 @@ def test_host_eigensolver_matches_numpy(darc):
     # a degenerate spectrum (identity) still gives an orthonormal basis
     mu, e = darc.sym_eigen(np.eye(4))
     assert np.allclose(mu, 1.0) and np.allclose(e @ e.T, np.eye(4))
+
+
+def test_noalloc_host_checks(darc):
+    """Host-side rejections of the allocation-free adjoint (no device work):
+    the smallest volume above the fixed-scratch limit (the limit + 1 is prime,
+    so no shape with every dimension >= 2 has exactly that many voxels), and
+    a result buffer overlapping the velocity or the squaring fields."""
+    L = darc.lib()
+    fake = ctypes.c_void_p(0x10000000)
+    over = darc.DARC_NOALLOC_MAX_VOXELS + 2            # 2 x 2 x 699,051
+    assert L.darc_exp_backward_noalloc(fake, fake, fake, fake, 1, 2, 2, over // 4, 7, 1.0, None) == darc.DARC_ERR_ARG
+    assert "exceeds" in L.darc_last_error().decode()
+    v = ctypes.c_void_p(0x10000000)
+    u = ctypes.c_void_p(0x20000000)
+    g = ctypes.c_void_p(0x30000000)
+    inside_u = ctypes.c_void_p(0x20000000 + 4 * 3 * 512 * 2)      # the third squaring field of u
+    for gv in (v, inside_u, ctypes.c_void_p(0x30000000 + 64)):
+        assert L.darc_exp_backward_noalloc(v, u, g, gv, 1, 8, 8, 8, 7, 1.0, None) == darc.DARC_ERR_ARG
+        assert "overlaps" in L.darc_last_error().decode()
+
+
+def test_noalloc_wrapper_checks_shapes_before_any_call(darc):
+    import torch
+    v = torch.zeros(1, 3, 4, 5, 6)
+    u = torch.zeros(2, 1, 3, 4, 5, 6)
+    with pytest.raises(ValueError, match="out shape"):
+        darc.exp_backward_noalloc(v, u, v.clone(), out=torch.zeros(1, 3, 4, 5, 5))
+    with pytest.raises(ValueError, match="u must have shape"):
+        darc.exp_backward_noalloc(v, torch.zeros(2, 2, 3, 4, 5, 6), v.clone())
+    with pytest.raises(ValueError, match="gT shape"):
+        darc.exp_backward_noalloc(v, u, torch.zeros(1, 3, 4, 5, 7))
+    with pytest.raises(ValueError, match="CUDA"):          # right shapes, but host tensors
+        darc.exp_backward_noalloc(v, u, v.clone())

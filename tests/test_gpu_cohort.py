@@ -51,11 +51,12 @@ def test_init_atlas_is_the_image_mean():
     assert float(c.velocity(1).abs().max()) == 0.0
 
 
+@pytest.mark.parametrize("adjoint", [0, 1])
 @pytest.mark.parametrize("dissim", [configs.MSE, configs.LNCC])
-def test_subject_step_from_identical_state(dissim):
+def test_subject_step_from_identical_state(dissim, adjoint):
     shape, n = (14, 17, 35), 3
     co = cohort_images(n, shape, 2)
-    cfg = configs.DarcConfig(dissim=dissim, ncc_window=5, n_squarings=7, lam=0.5)
+    cfg = configs.DarcConfig(dissim=dissim, ncc_window=5, n_squarings=7, lam=0.5, adjoint=adjoint)
     imgs = co.images.to(DEV).contiguous()
     c = darc.Cohort(imgs, cfg)
     v0 = [synth.random_field(shape, 3.0, 1.5, 200 + i) for i in range(n)]
@@ -301,14 +302,15 @@ def test_sweeps_around_a_diffeo_report_match_a_cohort_without_one():
         assert float(((va - vb).abs() <= 1e-4 * float(vb.abs().max())).float().mean()) > 0.99
 
 
-def test_checkpoint_stride_gives_the_same_sweep():
+@pytest.mark.parametrize("adjoint", [0, 1])
+def test_checkpoint_stride_gives_the_same_sweep(adjoint):
     shape, n = (10, 12, 14), 4
     co = cohort_images(n, shape, 9)
     imgs = co.images.to(DEV).contiguous()
     out, launches = [], []
     for stride in (0, 3):
         cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=3, n_squarings=7, checkpoint_stride=stride,
-                                 inner_steps=3, atlas_epochs=2, atlas_batch=2)
+                                 inner_steps=3, atlas_epochs=2, atlas_batch=2, adjoint=adjoint)
         c = darc.Cohort(imgs, cfg)
         before = c.launch_count()
         c.subject_step(0, n, 3)

@@ -94,14 +94,16 @@ def test_full_size_ncc_gradient_on_sampled_blocks(brain):
         assert np.linalg.norm(got - ref) <= GRAD_TOL * np.linalg.norm(ref)
 
 
-def test_full_size_cohort_step_matches_the_oracle_gradient_on_sampled_blocks(brain):
+@pytest.mark.parametrize("adjoint", [0, 1])
+def test_full_size_cohort_step_matches_the_oracle_gradient_on_sampled_blocks(brain, adjoint):
     """The cohort's own subject step at full size (packed squaring fields,
-    interleaved adjoint chain, Adam): from m = s = 0 its first Adam step is
-    dv = -lr g / (|g| + eps) with g the NCC gradient, so the velocity change
-    on a sampled block is checked against that step of the oracle's gradient
-    on a crop (lambda = 0, as above)."""
+    scatter or gather adjoint chain, Adam): from m = s = 0 its first Adam
+    step is dv = -lr g / (|g| + eps) with g the NCC gradient, so the
+    velocity change on a sampled block is checked against that step of the
+    oracle's gradient on a crop (lambda = 0, as above)."""
     images, template, v = brain
-    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=9, n_squarings=7, lam=0.0, inner_steps=1)
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=9, n_squarings=7, lam=0.0, inner_steps=1,
+                             adjoint=adjoint)
     c = darc.Cohort(images, cfg)
     c.set_atlas(template)
     for i in range(2):

@@ -73,8 +73,9 @@ def test_exp_backward(shape):
 
 
 def test_exp_backward_large_displacements_use_the_global_scatter():
-    """Rough fields with 8-voxel displacements overflow the shared-memory
-    window of a tile, so those blocks scatter straight to global memory."""
+    """Rough fields with 8-voxel displacements: most sources of the upper
+    squarings move a voxel or more, so the far-source scatter carries most
+    of their transpose terms."""
     shape = (12, 20, 40)
     v = field(shape, 40, max_disp=8.0, sigma=1.5)
     gT = field(shape, 41, max_disp=1.0, sigma=1.0)
@@ -84,6 +85,26 @@ def test_exp_backward_large_displacements_use_the_global_scatter():
     ref_u = oracle.exp(np64(v[0]), 5)
     assert rel_max(np64(u[-1, 0]), ref_u[-1]) <= FWD_TOL
     assert rel_l2(np64(gv[0]), oracle.exp_vjp(ref_u, np64(gT[0]))) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("max_disp,T", [(0.5, 3), (3.0, 7), (12.0, 4)])
+def test_exp_backward_gather_and_far_scatter(max_disp, T):
+    """Sources below one voxel are gathered, the others scattered: a chain
+    entirely below one voxel, one that crosses it in its upper squarings and
+    one mostly above it, on volumes spanning several 32 x 16 x 16 gather
+    tiles with ragged tails on every axis."""
+    shape = (37, 35, 70)
+    v = field(shape, 90, max_disp=max_disp, sigma=2.5, B=2)
+    gT = field(shape, 91, max_disp=1.0, sigma=1.0, B=2)
+    vd = v.to(DEV)
+    u = darc.exp_forward(vd, T)
+    gv = darc.exp_backward(vd, u, gT.to(DEV))
+    for b in range(2):
+        ref = oracle.exp_vjp(oracle.exp(np64(v[b]), T), np64(gT[b]))
+        assert rel_l2(np64(gv[b]), ref) <= GRAD_TOL, b
+    if max_disp < 1.0:
+        # no far source: every voxel is written once by the gather, no atomics
+        assert torch.equal(gv, darc.exp_backward(vd, u, gT.to(DEV)))
 
 
 def test_exp_backward_in_place_and_single_squaring():
@@ -182,13 +203,14 @@ def test_median_is_exact(n):
     assert np.array_equal(got.double().numpy(), ref)
 
 
+@pytest.mark.parametrize("adjoint", [0, 1])
 @pytest.mark.parametrize("dissim,w,T", [(configs.MSE, 9, 6), (configs.LNCC, 5, 7), (configs.LNCC, 9, 7),
                                         (configs.L1, 9, 6), (configs.SSIM, 5, 7)])
-def test_subject_gradient(dissim, w, T):
+def test_subject_gradient(dissim, w, T, adjoint):
     shape = (18, 21, 35)
     I, A = image(shape, 90, B=2), image(shape, 95)[0].contiguous()
     v = field(shape, 96, max_disp=2.5, B=2)
-    cfg = configs.DarcConfig(dissim=dissim, ncc_window=w, n_squarings=T, lam=0.8)
+    cfg = configs.DarcConfig(dissim=dissim, ncc_window=w, n_squarings=T, lam=0.8, adjoint=adjoint)
     energy, gv = darc.subject_grad(cfg, I.to(DEV), A.to(DEV), v.to(DEV))
     ocfg = oracle.make_cfg(dissim=dissim, window=w, T=T, lam=0.8)
     for b in range(2):
@@ -198,15 +220,17 @@ def test_subject_gradient(dissim, w, T):
         assert rel_l2(np64(gv[b]), g) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("adjoint", [0, 1])
 @pytest.mark.parametrize("stride", [2, 3, 4])
-def test_subject_gradient_with_checkpointed_squarings(stride):
+def test_subject_gradient_with_checkpointed_squarings(stride, adjoint):
     """Keeping every stride-th squaring field and recomputing the rest gives
     the oracle's gradient (the recomputed fields are bit-identical: the
     forward squaring is a pure gather)."""
     shape = (18, 21, 35)
     I, A = image(shape, 91, B=2), image(shape, 92)[0].contiguous()
     v = field(shape, 93, max_disp=2.5, B=2)
-    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=7, lam=0.8, checkpoint_stride=stride)
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=7, lam=0.8, checkpoint_stride=stride,
+                             adjoint=adjoint)
     energy, gv = darc.subject_grad(cfg, I.to(DEV), A.to(DEV), v.to(DEV))
     ocfg = oracle.make_cfg(dissim=configs.LNCC, window=5, T=7, lam=0.8)
     for b in range(2):

@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2508_10743_gb300 import darc, synth
 
 pytestmark = pytest.mark.gpu
@@ -28,6 +29,7 @@ GRAD_TOL = 1e-3
 def _lib():
     from paper_2508_10743_gb300 import build
     build.build()
+    oracle.build()
     darc.lib()
 
 
@@ -61,6 +63,30 @@ def test_noalloc_adjoint_matches_the_workspace_entry_point_on_two_calls():
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert _rel_l2(out, ref) <= GRAD_TOL, f"call {call}"
+        # and against the FP64 oracle's adjoint directly
+        for b in range(B):
+            vb = v[b].double().cpu().numpy()
+            want = oracle.exp_vjp(oracle.exp(vb, T), gT[b].double().cpu().numpy())
+            got = out[b].double().cpu().numpy()
+            assert np.linalg.norm(got - want) / np.linalg.norm(want) <= GRAD_TOL, (call, b)
+
+
+def test_noalloc_wrapper_and_a_call_at_exactly_the_limit():
+    """The Python wrapper on a volume of exactly DARC_NOALLOC_MAX_VOXELS
+    voxels (46 x 89 x 683 = 2,796,202), where the second gradient buffer ends
+    at the end of the fixed array, twice in a row."""
+    shape, T = (46, 89, 683), 7
+    assert shape[0] * shape[1] * shape[2] == darc.DARC_NOALLOC_MAX_VOXELS
+    for seed in (1000, 1100):
+        v = _field(shape, seed, 4.0, 3.0, 1)
+        gT = _field(shape, seed + 1, 1.0, 1.5, 1)
+        u = darc.exp_forward(v, T)
+        ref = darc.exp_backward(v, u, gT)
+        out = torch.full_like(v, float("nan"))
+        got = darc.exp_backward_noalloc(v, u, gT, out=out)
+        torch.cuda.synchronize()
+        assert got.data_ptr() == out.data_ptr() and torch.isfinite(out).all()
+        assert _rel_l2(out, ref) <= GRAD_TOL, seed
 
 
 def test_noalloc_adjoint_inverse_map_and_single_squaring_in_place():
