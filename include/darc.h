@@ -392,6 +392,17 @@ int darc_atlas_mean(const float* I_dev, const float* v_dev, float* A_dev, void* 
 int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* out_dev, int B,
                       int D, int H, int W, void* stream);
 
+/* Dice score of one-shot segmentation (Sec. "Evaluation metrics"; Table 3):
+ * for each of B label maps a_dev, b_dev [B][V] (uint8) and each label
+ * l = 1..n_labels-1 (0 is the background), dice_host[b][l - 1] =
+ * 2 |a = l and b = l| / (|a = l| + |b = l|), or -1 where the label occurs in
+ * neither map.  n_labels 2..256.  work_dev: darc_dice_workspace(B,
+ * n_labels) bytes (counters).  Waits for the stream (host output).
+ * Errors: ARG, CUDA. */
+size_t darc_dice_workspace(int B, int n_labels);
+int darc_dice(const uint8_t* a_dev, const uint8_t* b_dev, int B, long long V, int n_labels, void* work_dev,
+              double* dice_host, void* stream);
+
 /* Mesh vertices moved by a forward map (Sec. "Shape synthesis"): out_dev
  * [P][3] = pts_dev[p] + S(u_dev, pts_dev[p]) for points in (z, y, x) voxel
  * coordinates and a displacement u_dev [3][D][H][W] (trilinear, border

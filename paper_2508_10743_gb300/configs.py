@@ -95,4 +95,11 @@ WORKLOADS: Dict[str, Workload] = {
         sweeps=60,
         gen=dict(phantom="shells", sigma=6.0, max_disp=5.0, noise=0.02),
         seed=5000),
+    # half-resolution cardiac cohort for its learned warm start (2x2x2 block means)
+    "cardiac_half": Workload(
+        "cardiac_half", 256, (64, 64, 48),
+        DarcConfig(dissim=LNCC, ncc_window=9, n_squarings=7, lam=1.0, inner_steps=10,
+                   atlas_epochs=20, atlas_batch=10),
+        sweeps=60,
+        seed=5500),
 }

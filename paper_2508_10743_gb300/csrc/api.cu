@@ -1793,6 +1793,36 @@ int darc_label_gather(const uint8_t* labels_dev, const float* u_dev, uint8_t* ou
     return DARC_OK;
 }
 
+size_t darc_dice_workspace(int B, int n_labels)
+{
+    if (B < 1 || n_labels < 2 || n_labels > 256) return 0;
+    return sizeof(unsigned long long) * 3 * (size_t)B * n_labels;
+}
+
+int darc_dice(const uint8_t* a_dev, const uint8_t* b_dev, int B, long long V, int n_labels, void* work_dev,
+              double* dice_host, void* stream)
+{
+    if (!a_dev || !b_dev || !work_dev || !dice_host) return fail(DARC_ERR_ARG, "null argument");
+    if (B < 1 || V < 1) return fail(DARC_ERR_ARG, "B and V must be >= 1");
+    if (n_labels < 2 || n_labels > 256) return fail(DARC_ERR_ARG, "n_labels must be 2..256");
+    if (B > 65535) return fail(DARC_ERR_ARG, "at most 65535 label maps a call");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long* cnt = static_cast<unsigned long long*>(work_dev);
+    const size_t nc = 3 * (size_t)B * n_labels;
+    CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * nc, s));
+    CK(label_overlap(a_dev, b_dev, B, V, n_labels, cnt, s));
+    std::vector<unsigned long long> h(nc);
+    CK(cudaMemcpyAsync(h.data(), cnt, sizeof(unsigned long long) * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < B; ++b)
+        for (int l = 1; l < n_labels; ++l) {
+            const unsigned long long* q = h.data() + ((size_t)b * n_labels + l) * 3;
+            dice_host[(size_t)b * (n_labels - 1) + l - 1] =
+                (q[0] + q[1]) ? 2.0 * (double)q[2] / (double)(q[0] + q[1]) : -1.0;
+        }
+    return DARC_OK;
+}
+
 int darc_warp_points(const float* u_dev, int D, int H, int W, const float* pts_dev, long long P, float* out_dev,
                      void* stream)
 {

@@ -13,6 +13,8 @@
 // sums per block in float, stored as double, reduced in fixed order later.
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace darc_impl {
 namespace {
 
@@ -454,6 +456,44 @@ cudaError_t mse_warp_reg(const float* I, size_t I_bstride, const float* A, const
         mse_warp_reg_kernel<PlanarField><<<g, dim3(VT_X, VT_Y), 0, s>>>(
             I, I_bstride, A, PlanarField{uT, v.V}, lambda, gT, partials, v, nzt, invV, reg_weights(v), l1);
     }
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Per-subject label overlaps for the Dice score (Sec. "Evaluation
+// metrics"): counts[b][l] = {|a = l|, |b = l|, |a = l and b = l|}; block
+// histograms in shared memory, flushed with one atomic per label.
+__global__ void __launch_bounds__(256)
+label_overlap_kernel(const uint8_t* __restrict__ a, const uint8_t* __restrict__ bl, long long V, int nl,
+                     unsigned long long* __restrict__ counts)
+{
+    __shared__ unsigned int h[3][256];
+    for (int k = threadIdx.x; k < 3 * 256; k += 256) (&h[0][0])[k] = 0u;
+    __syncthreads();
+    const int b = blockIdx.y;
+    const uint8_t* pa = a + (size_t)b * V;
+    const uint8_t* pb = bl + (size_t)b * V;
+    for (long long l = blockIdx.x * 256LL + threadIdx.x; l < V; l += (long long)gridDim.x * 256) {
+        const int x = __ldg(pa + l), y = __ldg(pb + l);
+        atomicAdd(&h[0][x], 1u);
+        atomicAdd(&h[1][y], 1u);
+        if (x == y) atomicAdd(&h[2][x], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * nl; k += 256) {
+        const int c = k / nl, lab = k - c * nl;
+        if (h[c][lab]) atomicAdd(counts + ((size_t)b * nl + lab) * 3 + c, (unsigned long long)h[c][lab]);
+    }
+}
+
+}  // namespace
+
+cudaError_t label_overlap(const uint8_t* a, const uint8_t* b, int B, long long V, int nl,
+                          unsigned long long* counts, cudaStream_t s)
+{
+    const int gx = (int)std::max<long long>(1, std::min<long long>((V + 255) / 256, 152LL * 8 / std::max(B, 1) + 1));
+    label_overlap_kernel<<<dim3(gx, B), 256, 0, s>>>(a, b, V, nl, counts);
     return cudaGetLastError();
 }
 

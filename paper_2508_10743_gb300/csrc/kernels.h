@@ -80,6 +80,10 @@ int median_threads(int n);
 cudaError_t median(const float* X, int n, long long V, float* out, cudaStream_t s);
 cudaError_t label_gather(const uint8_t* labels, const float* u, uint8_t* out, int B, const Vol& v,
                          cudaStream_t s);
+// counts [B][nl][3] (cleared by the caller) += {|a = l|, |b = l|, |a = l and
+// b = l|} over the V voxels of each of the B label maps; nl <= 256
+cudaError_t label_overlap(const uint8_t* a, const uint8_t* b, int B, long long V, int nl,
+                          unsigned long long* counts, cudaStream_t s);
 // ---- PCA shape synthesis (k_shape.cu) ----
 // mean[l] = 1/n sum_i v[i][l], v [n][M]
 cudaError_t field_mean(const float* v, int n, long long M, float* mean, cudaStream_t s);

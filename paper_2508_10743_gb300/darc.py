@@ -98,6 +98,8 @@ _SIGS = {
     "darc_atlas_mean_workspace": (_sz, [_i, _i, _i, _i]),
     "darc_atlas_mean": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "darc_label_gather": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
+    "darc_dice_workspace": (_sz, [_i, _i]),
+    "darc_dice": (_i, [_vp, _vp, _i, ctypes.c_longlong, _i, _vp, _vp, _vp]),
     "darc_jacobian_det": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp]),
     "darc_set_profiling": (_i, [_vp, _i]),
     "darc_profile_read": (_i, [_vp, _i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
@@ -804,6 +806,26 @@ def label_gather(labels: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
     D, H, W = _dims(u)
     out = torch.empty((B, D, H, W), dtype=torch.uint8, device=u.device)
     _check(lib().darc_label_gather(_ptr(labels), _ptr(u), _ptr(out), B, D, H, W, _stream()))
+    return out
+
+
+def dice(a: torch.Tensor, b: torch.Tensor, n_labels: int):
+    """Per map and label 1..n_labels-1: the Dice score of two batches of
+    uint8 label maps [B, D, H, W] (-1 where the label is in neither), as a
+    numpy array [B, n_labels - 1] (darc_dice)."""
+    import numpy as np
+    _need(a, "a", torch.uint8)
+    _need(b, "b", torch.uint8)
+    if a.shape != b.shape:
+        raise ValueError(f"label maps differ in shape: {tuple(a.shape)} vs {tuple(b.shape)}")
+    a4 = a if a.dim() == 4 else a[None]
+    b4 = b if b.dim() == 4 else b[None]
+    B = a4.shape[0]
+    V = a4[0].numel()
+    out = np.zeros((B, n_labels - 1))
+    work = _work(lib().darc_dice_workspace(B, n_labels), a.device)
+    _check(lib().darc_dice(_ptr(a4), _ptr(b4), B, V, n_labels, _ptr(work), out.ctypes.data_as(ctypes.c_void_p),
+                           _stream()))
     return out
 
 

@@ -36,20 +36,27 @@ def half_inputs(images: torch.Tensor, atlas: torch.Tensor):
     return darc.resample_half(images), darc.resample_half(atlas[None].contiguous())[0].contiguous()
 
 
-def make_pairs(seeds: List[int], sweeps: int, gen_workload: str = "brain", run_workload: str = "unet_half",
-               device="cuda:0", log=None) -> Dict:
+def _workload(w) -> configs.Workload:
+    return configs.WORKLOADS[w] if isinstance(w, str) else w
+
+
+def make_pairs(seeds: List[int], sweeps: int, gen_workload="brain", run_workload="unet_half",
+               device="cuda:0", log=None, gen_n: Optional[int] = None) -> Dict:
     """Training pairs from the plain method at half resolution.
 
-    Each seeded cohort of `gen_workload` (full resolution) is reduced by
-    2x2x2 block means and registered from v = 0 for `sweeps` sweeps with the
-    settings of `run_workload`.  Returns subj [N, D, H, W], atlas [C, D, H, W]
-    (A^0 of each cohort), cohort [N] (index into atlas) and target
-    [N, 3, D, H, W] (the final centred velocities), all on `device`."""
-    gw, rw = configs.WORKLOADS[gen_workload], configs.WORKLOADS[run_workload]
+    Each seeded cohort of `gen_workload` (full resolution; a name of
+    configs.WORKLOADS or a Workload; `gen_n` subjects instead of its n) is
+    reduced by 2x2x2 block means and registered from v = 0 for `sweeps`
+    sweeps with the settings of `run_workload`.  Returns subj [N, D, H, W],
+    atlas [C, D, H, W] (A^0 of each cohort), cohort [N] (index into atlas)
+    and target [N, 3, D, H, W] (the final centred velocities), all on
+    `device`."""
+    gw, rw = _workload(gen_workload), _workload(run_workload)
+    gen_workload = gw.name
     subj, atlas, cohort, target = [], [], [], []
     for c, seed in enumerate(seeds):
         t0 = time.perf_counter()
-        co = synth.make_cohort(gw.n, gw.shape, seed, device=device, keep_w=False, keep_disp=False, **gw.gen)
+        co = synth.make_cohort(gen_n or gw.n, gw.shape, seed, device=device, keep_w=False, keep_disp=False, **gw.gen)
         images = darc.resample_half(co.images.contiguous())
         del co
         if tuple(images.shape[1:]) != rw.shape:

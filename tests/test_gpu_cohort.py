@@ -120,38 +120,64 @@ def test_sweeps_match_the_oracle_l1():
     assert np.mean(np.abs(np64(c.atlas()) - st.A) <= 1e-3) > 0.99
 
 
-def test_ssim_atlas_update_matches_oracle_sgd():
-    shape, n = (12, 18, 33), 5
-    co = cohort_images(n, shape, 14)
-    cfg = configs.DarcConfig(dissim=configs.SSIM, ncc_window=5, n_squarings=7, atlas_epochs=3,
-                             atlas_batch=2, seed=12)
+def _atlas_one_step(metric, n, batch, seed):
+    """Protocol (iii) for the atlas: one mini-batch Adam step of the atlas
+    from identical state (one epoch, one batch of every subject), compared on
+    the voxels whose batch gradient is above 1e-3 of its maximum, where float
+    rounding cannot flip the sign that Adam's first step takes."""
+    shape = (12, 18, 33)
+    co = cohort_images(n, shape, seed)
+    cfg = configs.DarcConfig(dissim=metric, ncc_window=5, n_squarings=7, atlas_epochs=1, atlas_batch=batch,
+                             seed=seed)
     c = darc.Cohort(co.images.to(DEV).contiguous(), cfg)
-    v = [synth.random_field(shape, 3.0, 1.5, 310 + i) for i in range(n)]
+    v = [synth.random_field(shape, 3.0, 1.5, 300 + seed + i) for i in range(n)]
     for i in range(n):
         c.set_velocity(i, v[i].to(DEV).contiguous())
     A0 = np64(c.atlas())
     stats = c.update_atlas()
+    A = np64(c.atlas())
     vv = np.ascontiguousarray(np.stack([np64(x) for x in v]))
     oracle.centrality(vv)
     A_ref, loss_ref = oracle.atlas_sgd(np64(co.images), vv, A0, _ocfg(cfg), sweep=0)
-    A = np64(c.atlas())
-    step_ref = A_ref - A0
-    agree = np.abs((A - A0) - step_ref) <= 0.05 * np.abs(step_ref).max()
-    assert agree.mean() > 0.99
-    assert abs(stats["atlas_loss"] - loss_ref) <= 1e-3 * abs(loss_ref)
-    # one subject step with SSIM from the same state
-    losses = c.subject_step(0, n, 1, want_loss=True)
-    assert all(np.isfinite(losses))
+    # the batch-mean atlas gradient at A0 (oracle)
+    I = np64(co.images)
+    loss_fn = oracle.lncc if metric == configs.LNCC else oracle.ssim
+    g = np.zeros_like(A0)
+    for i in range(n):
+        Wi = oracle.warp(I[i], oracle.exp(vv[i], 7)[-1])
+        out = loss_fn(Wi, A0, 5, with_grad=True) if metric == configs.SSIM else loss_fn(Wi, A0, 5, 1e-5, with_grad=True)
+        g += out[2] / n
+    return A0, A, A_ref, g, stats, loss_ref, cfg
 
 
-# mini-batches of 1 to 4 subjects take the two-pass step with the Adam update
-# in the adjoint's epilogue; 6 takes the unfused chain (and a last batch of 1)
-@pytest.mark.parametrize("n,batch", [(5, 2), (7, 3), (9, 4), (7, 6)])
-def test_ncc_atlas_update_matches_oracle_sgd(n, batch):
+# batches of 1 to 4 subjects take the two-pass step with the Adam update in
+# the adjoint's epilogue; 6 takes the unfused chain
+@pytest.mark.parametrize("metric,n,batch", [(configs.LNCC, 4, 4), (configs.LNCC, 3, 3), (configs.LNCC, 6, 6),
+                                            (configs.SSIM, 4, 4)])
+def test_atlas_adam_step_from_identical_state(metric, n, batch):
+    A0, A, A_ref, g, stats, loss_ref, cfg = _atlas_one_step(metric, n, batch, 40 + n)
+    mask = np.abs(g) > 1e-3 * np.abs(g).max()
+    step, step_ref = A - A0, A_ref - A0
+    ok = np.abs(step - step_ref) <= 1e-4 * cfg.lr
+    flips = int((~ok & mask).sum())
+    print(f"atlas one-step parity: {mask.sum()} voxels above 1e-3 max|g|, {flips} differ "
+          f"({flips / max(mask.sum(), 1):.2e})")
+    assert flips <= 1e-3 * mask.sum()
+    assert np.abs(step).max() <= cfg.lr * (1 + 1e-6)         # Adam's first step is at most lr
+    assert abs(stats["atlas_loss"] - loss_ref) <= 1e-4 * abs(loss_ref)
+
+
+@pytest.mark.parametrize("metric,n,batch", [(configs.LNCC, 5, 2), (configs.LNCC, 7, 3), (configs.LNCC, 9, 4),
+                                            (configs.LNCC, 7, 6), (configs.SSIM, 5, 2)])
+def test_atlas_epochs_follow_the_oracle(metric, n, batch):
+    """Several epochs of shuffled mini-batches (the last one partial): the
+    atlas loss of the last epoch matches the oracle's, and the atlas stays
+    on the oracle's trajectory (Adam steps near zero gradients may flip, so
+    per-voxel agreement is bounded on 99% of voxels)."""
     shape = (12, 18, 33)
     co = cohort_images(n, shape, 4)
-    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=7, atlas_epochs=3,
-                             atlas_batch=batch, seed=11)
+    cfg = configs.DarcConfig(dissim=metric, ncc_window=5, n_squarings=7, atlas_epochs=3, atlas_batch=batch,
+                             seed=11)
     c = darc.Cohort(co.images.to(DEV).contiguous(), cfg)
     v = [synth.random_field(shape, 3.0, 1.5, 300 + i) for i in range(n)]
     for i in range(n):
@@ -167,6 +193,9 @@ def test_ncc_atlas_update_matches_oracle_sgd(n, batch):
     assert agree.mean() > 0.99
     assert abs(stats["atlas_loss"] - loss_ref) <= 1e-3 * abs(loss_ref)
     assert stats["centrality_after"] < 1e-6
+    if metric == configs.SSIM:
+        losses = c.subject_step(0, n, 1, want_loss=True)     # one SSIM subject step from the same state
+        assert all(np.isfinite(losses))
 
 
 def test_propagate_labels_matches_oracle():

@@ -299,6 +299,24 @@ def test_label_gather_through_inverse_map():
         assert safe.mean() > 0.99
 
 
+def test_dice_matches_oracle():
+    """darc_dice against the oracle's Dice, on random maps (every label
+    present), maps with a label missing from one side and from both."""
+    rng = np.random.default_rng(11)
+    shape = (13, 17, 29)
+    a = rng.integers(0, 8, size=(3,) + shape).astype(np.uint8)
+    b = a.copy()
+    flip = rng.random(b.shape) < 0.3
+    b[flip] = rng.integers(0, 8, size=int(flip.sum())).astype(np.uint8)
+    b[1][b[1] == 5] = 0                      # label 5 only in a (dice 0)
+    a[2][a[2] == 6] = 0                      # label 6 in neither map of subject 2
+    b[2][b[2] == 6] = 0
+    got = darc.dice(torch.tensor(a).to(DEV), torch.tensor(b).to(DEV), 8)
+    for i in range(3):
+        np.testing.assert_allclose(got[i], oracle.dice(a[i], b[i], 8), rtol=1e-15, atol=0)
+    assert got[1][4] == 0.0 and got[2][5] == -1.0
+
+
 def test_jacobian_determinant():
     shape = (9, 13, 37)
     v = field(shape, 140, max_disp=3.0, sigma=1.2, B=2)

@@ -107,6 +107,72 @@ def test_atlas_sgd_decreases_ncc_loss(ora):
     assert losses[0] > losses[1] > losses[2]
 
 
+def _atlas_case(ora, n, seed, shape=(10, 11, 12), T=4):
+    """n subjects warped by Exp(v_i) with the oracle's own (pinned) Exp and
+    warp, and a start atlas."""
+    I = np.stack([synth.random_image(shape, seed + i, n_ell=4, radii=(2.0, 4.0)).double().numpy()
+                  for i in range(n)])
+    v = np.stack([synth.random_field(shape, 2.0, 1.5, seed + 10 + i).double().numpy() for i in range(n)])
+    A0 = synth.random_image(shape, seed + 20, n_ell=4, radii=(2.0, 4.0)).double().numpy()
+    W = [ora.warp(I[i], ora.exp(v[i], T)[-1]) for i in range(n)]
+    return I, v, A0, W
+
+
+def test_atlas_sgd_first_step_is_the_normalised_ncc_gradient(ora):
+    """One subject, batch 1, one epoch: one Adam step from fresh state, which
+    in closed form is A - lr g / (|g| + eps), g = dL/dA of the local NCC
+    (that gradient is pinned by finite differences).  A second call restarts
+    Adam (the optimiser is created inside SGD_for_atlas, Algorithm 1): it is
+    again one normalised step, taken at the new atlas."""
+    I, v, A0, W = _atlas_case(ora, 1, 400)
+    cfg = ora.make_cfg(dissim=ora.LNCC, window=3, T=4, atlas_epochs=1, atlas_batch=1, lr=1e-2)
+    A1, loss = ora.atlas_sgd(I, v, A0, cfg, sweep=0)
+    L0, _, g0 = ora.lncc(W[0], A0, 3, with_grad=True)
+    np.testing.assert_allclose(A1, A0 - 1e-2 * g0 / (np.abs(g0) + 1e-8), rtol=0, atol=1e-13)
+    assert loss == pytest.approx(L0, rel=1e-12)
+    A2, _ = ora.atlas_sgd(I, v, A1, cfg, sweep=1)
+    _, _, g1 = ora.lncc(W[0], A1, 3, with_grad=True)
+    np.testing.assert_allclose(A2, A1 - 1e-2 * g1 / (np.abs(g1) + 1e-8), rtol=0, atol=1e-13)
+
+
+def test_atlas_sgd_batch_gradient_is_the_mean(ora):
+    """A batch of two subjects steps along the mean of their atlas
+    gradients.  An Adam eps comparable to |g| makes the first step depend on
+    the gradient's scale, so a batch sum is told apart from the mean."""
+    I, v, A0, W = _atlas_case(ora, 2, 500)
+    (La, _, ga), (Lb, _, gb) = (ora.lncc(W[i], A0, 3, with_grad=True) for i in range(2))
+    gm = 0.5 * (ga + gb)
+    eps = float(np.median(np.abs(gm)))
+    cfg = ora.make_cfg(dissim=ora.LNCC, window=3, T=4, atlas_epochs=1, atlas_batch=2, lr=1e-2, adam_eps=eps)
+    A1, loss = ora.atlas_sgd(I, v, A0, cfg, sweep=0)
+    want = A0 - 1e-2 * gm / (np.abs(gm) + eps)
+    np.testing.assert_allclose(A1, want, rtol=0, atol=1e-13)
+    summed = A0 - 1e-2 * (2 * gm) / (np.abs(2 * gm) + eps)
+    assert np.abs(summed - want).max() > 1e-4            # the pin tells the two apart
+    assert loss == pytest.approx(0.5 * (La + Lb), rel=1e-12)
+
+
+def test_atlas_sgd_takes_the_last_partial_batch(ora):
+    """Three copies of one subject in batches of two: an epoch is two Adam
+    steps, the full batch and the partial one, whatever the shuffle.  The
+    reference is torch.optim.Adam driven by the oracle's NCC atlas gradient."""
+    I, v, A0, W = _atlas_case(ora, 1, 600)
+    I3, v3 = np.repeat(I, 3, axis=0), np.repeat(v, 3, axis=0)
+    cfg = ora.make_cfg(dissim=ora.LNCC, window=3, T=4, atlas_epochs=1, atlas_batch=2, lr=1e-2)
+    A1, _ = ora.atlas_sgd(I3, v3, A0, cfg, sweep=0)
+    p = torch.nn.Parameter(torch.tensor(A0))
+    opt = torch.optim.Adam([p], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    one_step = None
+    for k in range(2):
+        _, _, g = ora.lncc(W[0], p.detach().numpy().copy(), 3, with_grad=True)
+        p.grad = torch.tensor(g)
+        opt.step()
+        if k == 0:
+            one_step = p.detach().numpy().copy()
+    np.testing.assert_allclose(A1, p.detach().numpy(), rtol=0, atol=1e-13)
+    assert np.abs(A1 - one_step).max() > 1e-4            # the second (partial) batch moved it
+
+
 def test_labels_identity_and_integer_translation(ora):
     rng = np.random.default_rng(3)
     lab = rng.integers(0, 8, size=(6, 7, 8)).astype(np.uint8)
