@@ -227,7 +227,11 @@ int darc_atlas_set_sum(darc_cohort* c, const double* acc_dev, long long n_total)
  * dL_i/dA and loss_dev float [1] = the sum of their losses (the order of the
  * rank's subjects is its own shuffle, seeded with cfg.seed + rank_seed);
  * apply takes one Adam step with the all-reduced sum divided by the global
- * batch size; end refreshes the atlas window statistics.
+ * batch size; end refreshes the atlas window statistics.  A mini-batch of
+ * at most four subjects takes the single-GPU update's two fused box passes
+ * (the second writes g_dev instead of stepping the atlas).  All four calls
+ * only enqueue work on the cohort's stream: a driver keeps the losses on the
+ * device and synchronises once per atlas update.
  * Returns DARC_ERR_ARG for an epoch/batch outside the schedule. */
 int darc_atlas_sgd_begin(darc_cohort* c, int sweep, unsigned long long rank_seed);
 int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, float* loss_dev);

@@ -9,7 +9,10 @@ images; the velocities reach the workload's 6-voxel displacement scale.
 `exp_adjoint` runs one squaring's adjoint (T = 1, so u_0 = v / 2: pass
 `--max-disp 1` for a chain of near sources only, 6 for mostly far ones).
 `cohort_step` runs whole subject updates of a cohort (the squarings, the
-local NCC terms, the gather adjoint chain and Adam).  `unet_step`
+local NCC terms, the adjoint chain and Adam); `atlas_update` the cohort's
+atlas re-estimate (centrality, warped cohort, K3 epochs of mini-batch Adam)
+and `atlas_sharded` the same update of the cohort split into two shards in
+one process, driven through the cross-GPU exchange hooks.  `unet_step`
 times training steps of the warm-start network instead (pass `--shape 80
 96 112`), `unet_forward` its forward pass; the timed launches sit inside an
 NVTX range named "step".
@@ -35,7 +38,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", required=True,
                     choices=["exp_square", "exp_adjoint", "lncc", "subject_grad", "warp", "cohort_step",
-                             "unet_step", "unet_forward"])
+                             "atlas_update", "atlas_sharded", "unet_step", "unet_forward"])
     ap.add_argument("--shape", type=int, nargs=3, default=[160, 192, 224])
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--window", type=int, default=9)
@@ -71,10 +74,19 @@ def main():
     cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=a.window, n_squarings=a.T, lam=1.0,
                              adjoint=0 if a.adjoint == "scatter" else 1)
     cohort = None
-    if a.kernel == "cohort_step":
+    if a.kernel in ("cohort_step", "atlas_update"):
         cohort = darc.Cohort(I, cfg)
         for b in range(B):
             cohort.set_velocity(b, v[b].contiguous())
+    sharded = None
+    if a.kernel == "atlas_sharded":
+        # two shards of one cohort held in one process, driven like two ranks
+        from paper_2508_10743_gb300.distributed import ShardedSweep
+        h = B // 2
+        shards = [darc.Cohort(I[:h].contiguous(), cfg), darc.Cohort(I[h:].contiguous(), cfg)]
+        for b in range(B):
+            shards[b // h if b < 2 * h else 1].set_velocity(b - h * (b >= h), v[b].contiguous())
+        sharded = ShardedSweep(shards, cfg)
 
     def run():
         if a.kernel == "exp_square":
@@ -87,6 +99,10 @@ def main():
             darc.warp(I, u[-1])
         elif a.kernel == "cohort_step":
             cohort.subject_step(0, B, 1)
+        elif a.kernel == "atlas_update":
+            cohort.update_atlas()
+        elif a.kernel == "atlas_sharded":
+            sharded.update_atlas(0)
         else:
             darc.subject_grad(cfg, I, A, v)
 

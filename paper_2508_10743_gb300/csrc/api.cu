@@ -1372,6 +1372,23 @@ int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, floa
     const int r = c->cfg.ncc_window / 2, b0 = batch * B, nb = std::min(B, c->n - b0);
     const int* subj = c->perm_dev + (size_t)epoch * c->n + b0;
     cudaStream_t s = c->st;
+    if (nb <= ATLAS_FUSED_MAX) {
+        // the single-GPU step's two box passes (the batch's metrics with Box(A),
+        // Box(A^2); the adjoint), the second writing g instead of stepping A
+        const int* sh = c->perm_host + (size_t)epoch * c->n + b0;
+        const float* Jr[ATLAS_FUSED_MAX];
+        const float* jr[ATLAS_FUSED_MAX];
+        for (int b = 0; b < nb; ++b) {
+            Jr[b] = c->Wcache + (size_t)sh[b] * vol.V;
+            jr[b] = c->jstats + (size_t)sh[b] * 2 * vol.V;
+        }
+        CK(atlas_sgd_fused_forward(Jr, jr, nb, c->A, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim), c->coef, c->pL,
+                                   vol, c->boxbuf, s));
+        CK(reduce_partials(c->pL, nb * box_blocks(vol), 1, 1.0, loss_dev, 1, 1, s));
+        CK(atlas_sgd_fused_grad(Jr, nb, c->coef, r, c->A, (float)(-1.0 / (double)vol.V), g_dev, vol, c->boxbuf, s));
+        c->launches += 5;
+        return end(c);
+    }
     CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));
     CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim),
                          c->coef, c->pL, nb, vol,

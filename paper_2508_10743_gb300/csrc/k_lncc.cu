@@ -578,6 +578,34 @@ struct AtlasBwdAdamOp {
     __device__ void partial(int, int, double) const {}
 };
 
+// The same adjoint pass without the Adam step, for a cohort sharded across
+// GPUs (the gradient is summed over the ranks before the step):
+// g = scale [Box(sum a) + 2 A Box(sum b) + sum_b J_b Box(g_b)] written out.
+template <int NB>
+struct AtlasBwdGradOp {
+    static constexpr bool kReduces = false;
+    const float* J[NB];
+    const float* coef;     // [2 + NB][V] from AtlasFwdFusedOp
+    const float* A;
+    float* g;
+    long long V;
+    float scale;
+    __device__ void load(int, long long l, float* o) const
+    {
+#pragma unroll
+        for (int c = 0; c < 2 + NB; ++c) o[c] = __ldg(coef + (size_t)c * V + l);
+    }
+    __device__ float emit(int, int, int, int, long long l, const float* S) const
+    {
+        float t = S[0] + 2.f * __ldg(A + l) * S[1];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) t += __fmul_rn(__ldg(J[b] + l), S[2 + b]);
+        g[l] = t * scale;
+        return 0.f;
+    }
+    __device__ void partial(int, int, double) const {}
+};
+
 template <int NCH, class Op>
 cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, float* P, cudaStream_t s)
 {
@@ -689,6 +717,32 @@ cudaError_t atlas_fused_adam_nb(const float* const* Jrows, const float* coef, in
     op.b2 = b2;
     op.eps = eps;
     return launch_box<2 + NB>(op, 1, v, r, P, s);
+}
+
+template <int NB>
+cudaError_t atlas_fused_grad_nb(const float* const* Jrows, const float* coef, int r, const float* A, float scale,
+                                float* g, const Vol& v, float* P, cudaStream_t s)
+{
+    AtlasBwdGradOp<NB> op{};
+    for (int b = 0; b < NB; ++b) op.J[b] = Jrows[b];
+    op.coef = coef;
+    op.A = A;
+    op.g = g;
+    op.V = v.V;
+    op.scale = scale;
+    return launch_box<2 + NB>(op, 1, v, r, P, s);
+}
+
+cudaError_t atlas_sgd_fused_grad(const float* const* Jrows, int nb, const float* coef, int r, const float* A,
+                                 float scale, float* g, const Vol& v, float* P, cudaStream_t s)
+{
+    switch (nb) {
+    case 1: return atlas_fused_grad_nb<1>(Jrows, coef, r, A, scale, g, v, P, s);
+    case 2: return atlas_fused_grad_nb<2>(Jrows, coef, r, A, scale, g, v, P, s);
+    case 3: return atlas_fused_grad_nb<3>(Jrows, coef, r, A, scale, g, v, P, s);
+    case 4: return atlas_fused_grad_nb<4>(Jrows, coef, r, A, scale, g, v, P, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t atlas_sgd_fused_forward(const float* const* Jrows, const float* const* jsrows, int nb, const float* A,

@@ -258,5 +258,9 @@ cudaError_t atlas_sgd_fused_forward(const float* const* Jrows, const float* cons
 cudaError_t atlas_sgd_fused_adam(const float* const* Jrows, int nb, const float* coef, int r, float* A, float* m,
                                  float* s_, float scale, float lr_c1, float isc2, float b1, float b2, float eps,
                                  const Vol& v, float* P, cudaStream_t s);
+// the same adjoint pass writing g [V] = scale * the batch's summed gradient
+// instead of stepping A (a sharded cohort sums g over its ranks first)
+cudaError_t atlas_sgd_fused_grad(const float* const* Jrows, int nb, const float* coef, int r, const float* A,
+                                 float scale, float* g, const Vol& v, float* P, cudaStream_t s);
 
 }  // namespace darc_impl

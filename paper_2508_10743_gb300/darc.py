@@ -333,9 +333,16 @@ class Cohort:
     def atlas_sgd_begin(self, sweep: int, rank_seed: int = 0):
         _check(lib().darc_atlas_sgd_begin(self._h, int(sweep), int(rank_seed)))
 
-    def atlas_sgd_grad(self, epoch: int, batch: int):
-        g = torch.empty(self.shape, dtype=torch.float32, device=self.device)
-        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+    def atlas_sgd_grad(self, epoch: int, batch: int, g: Optional[torch.Tensor] = None,
+                       loss: Optional[torch.Tensor] = None):
+        """(g [D, H, W], loss [1]) of this rank's mini-batch; pass g and loss
+        to reuse buffers (nothing waits for the stream)."""
+        g = torch.empty(self.shape, dtype=torch.float32, device=self.device) if g is None else g
+        loss = torch.empty(1, dtype=torch.float32, device=self.device) if loss is None else loss
+        _need(g, "g")
+        _need(loss, "loss")
+        if tuple(g.shape) != tuple(self.shape) or loss.numel() < 1:
+            raise ValueError("g must have the volume's shape and loss at least one element")
         _check(lib().darc_atlas_sgd_grad(self._h, int(epoch), int(batch), _ptr(g), _ptr(loss)))
         return g, loss
 

@@ -80,35 +80,49 @@ class ShardedSweep:
         B = self.cfg.atlas_batch
         for j, s in enumerate(self.shards):
             s.atlas_sgd_begin(sweep, self.shard_offset + j)
-        nb_local = max(s.atlas_batches() for s in self.shards)
-        nb = int(self._allreduce(torch.tensor([float(nb_local)], dtype=torch.float64),
+        # the schedule, once per update: the number of global mini-batches and
+        # the global batch size of each (host integers, two small collectives)
+        per_shard = [s.atlas_batches() for s in self.shards]
+        nb = int(self._allreduce(torch.tensor([float(max(per_shard))], dtype=torch.float64),
                                  op=dist.ReduceOp.MAX if self.distributed else None, cpu=True).item())
-        losses = []
-        proto = None
+        counts = torch.zeros(nb, dtype=torch.float64)
+        for s, k in zip(self.shards, per_shard):
+            for bi in range(k):
+                counts[bi] += min(B, s.n - bi * B)
+        counts = [int(c) for c in self._allreduce(counts, cpu=True).tolist()]
+        # the epoch loop only enqueues work: gradients and losses stay on the
+        # device in buffers made once; the gradient all-reduce is the exchange
+        g = tmp = loss_buf = None
         for ep in range(self.cfg.atlas_epochs):
-            ep_loss = 0.0
             for bi in range(nb):
-                parts, cnt, lsum = [], 0, 0.0
-                for s in self.shards:
-                    if bi < s.atlas_batches():
+                first = True
+                for j, s in enumerate(self.shards):
+                    if bi >= per_shard[j]:
+                        continue
+                    if g is None:
                         g, loss = s.atlas_sgd_grad(ep, bi)
-                        parts.append(g)
-                        cnt += min(B, s.n - bi * B)
-                        lsum += float(loss.sum())
-                if parts:
-                    g = self._sum_local(parts)
-                    proto = g
-                else:                               # every local shard has run out of batches
-                    g = torch.zeros_like(proto)
+                        loss_buf = torch.zeros((self.cfg.atlas_epochs, nb, len(self.shards)), dtype=loss.dtype,
+                                               device=loss.device)
+                        loss_buf[ep, bi, j] = loss[0]
+                    elif first:
+                        s.atlas_sgd_grad(ep, bi, g, loss_buf[ep, bi, j:j + 1])
+                    else:
+                        tmp = torch.empty_like(g) if tmp is None else tmp
+                        s.atlas_sgd_grad(ep, bi, tmp, loss_buf[ep, bi, j:j + 1])
+                        g += tmp
+                    first = False
+                if first:                           # every local shard has run out of batches
+                    g.zero_()
                 g = self._allreduce(g)
-                stats = self._allreduce(torch.tensor([float(cnt), lsum], dtype=torch.float64), cpu=True)
                 for s in self.shards:
-                    s.atlas_sgd_apply(g, int(stats[0].item()))
-                ep_loss += float(stats[1].item())
-            losses.append(ep_loss / self.n_total)
+                    s.atlas_sgd_apply(g, counts[bi])
         for s in self.shards:
             s.atlas_sgd_end()
-        out["atlas_loss"] = losses[-1] if losses else 0.0
+        if loss_buf is not None:
+            ep_loss = self._allreduce(loss_buf.sum(dim=(1, 2)).double(), cpu=True)   # the one wait
+            out["atlas_loss"] = float(ep_loss[-1]) / self.n_total
+        else:
+            out["atlas_loss"] = 0.0
         return out
 
     def sweep(self, sweep: int) -> dict:

@@ -73,14 +73,16 @@ class OracleShard:
                      for ep in range(self.cfg.atlas_epochs)]
         self.Am, self.As, self.ak = np.zeros_like(self.A), np.zeros_like(self.A), 0
 
-    def atlas_sgd_grad(self, epoch, batch):
+    def atlas_sgd_grad(self, epoch, batch, g_out=None, loss_out=None):
         B = self.cfg.atlas_batch
         g, loss = np.zeros_like(self.A), 0.0
         for i in self.perm[epoch][batch * B:(batch + 1) * B]:
             L, _, gA = oracle.lncc(self.W[i], self.A, self.cfg.ncc_window, self.cfg.ncc_eps, with_grad=True)
             g += gA
             loss += L
-        return torch.from_numpy(g), torch.tensor([loss])
+        g_t = torch.from_numpy(g) if g_out is None else g_out.copy_(torch.from_numpy(g))
+        l_t = torch.tensor([loss], dtype=torch.float64) if loss_out is None else loss_out.fill_(loss)
+        return g_t, l_t
 
     def atlas_sgd_apply(self, g, global_batch):
         self.ak += 1
