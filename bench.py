@@ -65,12 +65,16 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-PROFILE_FILES = {"exp_adjoint": "exp_gather", "exp_square": "exp_square"}
+PROFILE_FILES = {("exp_adjoint", "scatter"): "exp_square_adjoint", ("exp_adjoint", "gather"): "exp_gather",
+                 ("exp_square", "scatter"): "exp_square_kernel"}
 
 
-def read_traffic(kernel: str, workload: str):
+def read_traffic(kernel: str, workload: str, adjoint: str):
     """dram bytes per launch from a committed ncu summary (profiles/), or None."""
-    path = os.path.join(ROOT, "profiles", f"{PROFILE_FILES.get(kernel, kernel)}_{workload}.txt")
+    name = PROFILE_FILES.get((kernel, adjoint))
+    if name is None:
+        return None
+    path = os.path.join(ROOT, "profiles", f"{name}_{workload}.txt")
     if not os.path.exists(path):
         return None
     for line in open(path):
@@ -321,7 +325,7 @@ def main():
     dom = max(fams, key=lambda k: fams[k][0])
     tot_ms, nl, by = fams[dom]
     achieved = by / (tot_ms / 1e3) / 1e9
-    traffic = read_traffic(dom, wl.name)
+    traffic = read_traffic(dom, wl.name, args.adjoint)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_kind": peak_kind,
                 "traffic": (traffic if traffic is None else traffic),
