@@ -96,7 +96,7 @@ struct Carve {
     }
 };
 
-int nblk_max(const Vol& v) { return std::max(voxel_blocks(v), box_blocks(v)); }
+int nblk_max(const Vol& v) { return std::max(voxel_blocks(v), box_blocks_max(v)); }
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the k-th output of the
 // stream seeded s0 is mix(s0 + k * golden gamma).  Mini-batch order of the
@@ -465,7 +465,7 @@ cudaError_t enqueue_step(darc_cohort* c, int f, int cnt, cudaStream_t s)
             e = lncc_backward_warp_reg(c->Wimg, c->A, c->coef, r, Ib, vol.V, uT, c->cfg.lambda, c->gT,
                                        c->pR, cnt, vol, c->boxbuf, s, 1);
         }
-        pLp = c->pL; pRp = c->pR; nL = nR = box_blocks(vol); sL = sR = 1;
+        pLp = c->pL; pRp = c->pR; nL = nR = box_blocks(vol, cnt); sL = sR = 1;
         c->launches += 5;           // warp, two box passes of two kernels each
     }
     if (e != cudaSuccess) return e;
@@ -664,7 +664,7 @@ int update_atlas_body(darc_cohort* c)
                     }
                     CK(atlas_sgd_fused_forward(Jr, jr, nb, c->A, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim),
                                                c->coef, c->pL, vol, c->boxbuf, s));
-                    CK(reduce_partials(c->pL, box_blocks(vol), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
+                    CK(reduce_partials(c->pL, box_blocks(vol, 1), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
                     ++kk;
                     const double c1 = 1.0 - std::pow((double)c->cfg.beta1, kk);
                     const double c2 = 1.0 - std::pow((double)c->cfg.beta2, kk);
@@ -679,7 +679,7 @@ int update_atlas_body(darc_cohort* c)
                 CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps,
                                      patch_metric(c->cfg.dissim), c->coef,
                                      c->pL, nb, vol, c->boxbuf, s));
-                CK(reduce_partials(c->pL, box_blocks(vol), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
+                CK(reduce_partials(c->pL, box_blocks(vol, nb), 1, 1.0, c->aloss + (size_t)ep * n + b0, 1, nb, s));
                 CK(atlas_sgd_backward(c->Wcache, subj, c->A, c->coef, r, c->gsh, c->gA, nb, vol, c->boxbuf, s));
                 ++kk;
                 const double c1 = 1.0 - std::pow((double)c->cfg.beta1, kk);
@@ -1384,7 +1384,7 @@ int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, floa
         }
         CK(atlas_sgd_fused_forward(Jr, jr, nb, c->A, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim), c->coef, c->pL,
                                    vol, c->boxbuf, s));
-        CK(reduce_partials(c->pL, nb * box_blocks(vol), 1, 1.0, loss_dev, 1, 1, s));
+        CK(reduce_partials(c->pL, nb * box_blocks(vol, 1), 1, 1.0, loss_dev, 1, 1, s));
         CK(atlas_sgd_fused_grad(Jr, nb, c->coef, r, c->A, (float)(-1.0 / (double)vol.V), g_dev, vol, c->boxbuf, s));
         c->launches += 5;
         return end(c);
@@ -1393,7 +1393,7 @@ int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, floa
     CK(atlas_sgd_forward(c->Wcache, c->jstats, subj, c->A, c->astats, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim),
                          c->coef, c->pL, nb, vol,
                          c->boxbuf, s));
-    CK(reduce_partials(c->pL, nb * box_blocks(vol), 1, 1.0, loss_dev, 1, 1, s));
+    CK(reduce_partials(c->pL, nb * box_blocks(vol, nb), 1, 1.0, loss_dev, 1, 1, s));
     CK(atlas_sgd_backward(c->Wcache, subj, c->A, c->coef, r, c->gsh, c->gA, nb, vol, c->boxbuf, s));
     CK(combine_grad(c->gsh, c->gA, nb, (float)(-1.0 / (double)vol.V), g_dev, vol, s));
     c->launches += 10;
@@ -1610,7 +1610,7 @@ int patch_op(int metric, const float* J_dev, const float* A_dev, int window, flo
     float* P = cv.take<float>(3 * (size_t)B * v.V);
     CK(atlas_stats(A_dev, stats, r, v, P, s));
     CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 0, metric, coef, part, B, v, P, s));
-    CK(reduce_partials(part, box_blocks(v), 1, 1.0, loss_dev, 1, B, s));
+    CK(reduce_partials(part, box_blocks(v, B), 1, 1.0, loss_dev, 1, B, s));
     if (gJ_dev) CK(lncc_backward(J_dev, nullptr, A_dev, coef, r, 0, gJ_dev, B, v, P, s));
     if (gA_dev) {
         CK(lncc_forward(J_dev, nullptr, A_dev, stats, r, eps, 1, metric, coef, part, B, v, P, s));
@@ -1705,8 +1705,8 @@ int darc_subject_grad(const darc_config* cfg, const float* I_dev, const float* A
         CK(lncc_forward(Wimg, nullptr, A_dev, stats, r, cfg->ncc_eps, 0, patch_metric(cfg->dissim), coef, pL, B,
                         v, P, s));
         CK(lncc_backward_warp_reg(Wimg, A_dev, coef, r, I_dev, v.V, uT, cfg->lambda, gT, pR, B, v, P, s, 1));
-        CK(reduce_partials(pL, box_blocks(v), 1, 1.0, energy_dev, 2, B, s));
-        CK(reduce_partials(pR, box_blocks(v), 1, 1.0, energy_dev + 1, 2, B, s));
+        CK(reduce_partials(pL, box_blocks(v, B), 1, 1.0, energy_dev, 2, B, s));
+        CK(reduce_partials(pR, box_blocks(v, B), 1, 1.0, energy_dev + 1, 2, B, s));
     }
     // gradients alternate between the two gbuf halves; the last step writes gv
     // (the scatter adjoint: into a cleared interleaved buffer, then unpacked)

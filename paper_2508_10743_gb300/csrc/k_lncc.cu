@@ -60,6 +60,10 @@ constexpr int YC_WIDE = DARC_BOX_YC_WIDE_BATCH;
 #define DARC_BOX_ZMINB 0
 #endif
 constexpr int ZX = 32, ZY = 8, ZC = DARC_BOX_ZC;
+// Small launches (one small image) would leave most SMs idle with these
+// tiles: the XY strip and the Z chunk shrink (down to 16 rows, 8 planes)
+// until a launch has at least two blocks per SM.
+constexpr int BOX_MIN_BLOCKS = 2 * 152, YC_MIN = 16, ZC_MIN = 8;
 
 size_t xy_smem_bytes(int nch, int r)
 {
@@ -160,13 +164,14 @@ struct ZMinBlocks<Op, std::void_t<decltype(Op::kZMinBlocks)>> {
 };
 
 template <int NCH, class Op>
-__global__ void __launch_bounds__(ZX * ZY, ZMinBlocks<Op>::value) box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc)
+__global__ void __launch_bounds__(ZX * ZY, ZMinBlocks<Op>::value)
+box_z_kernel(Op op, Vol v, int r, const float* __restrict__ P, int nzc, int zlen)
 {
     __shared__ double red[32];
     const int x = blockIdx.x * ZX + threadIdx.x;
     const int y = blockIdx.y * ZY + threadIdx.y;
     const int b = blockIdx.z / nzc, zc = blockIdx.z % nzc;
-    const int z0 = zc * ZC, z1 = min(v.D, z0 + ZC);
+    const int z0 = zc * zlen, z1 = min(v.D, z0 + zlen);
     constexpr int ZU = NCH >= 3 ? DARC_BOX_ZU_WIDE : DARC_BOX_ZU_NARROW;
     constexpr int NR = NRed<Op>::value;
     float acc[NR];
@@ -617,13 +622,14 @@ cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, float* P, cudaS
         attr_set = true;
     }
     const int nzb = div_up(v.D, XW);
-    const int yc = B >= 8 ? YC_WIDE : YC;
+    const int yc = box_yc(v, B);
     box_xy_kernel<NCH, Op><<<dim3(div_up(v.W, 32), div_up(v.H, yc), nzb * B), XW * 32, xy_smem_bytes(NCH, r), s>>>(
         op, v, r, P, nzb, yc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int nzc = div_up(v.D, ZC);
-    box_z_kernel<NCH, Op><<<dim3(div_up(v.W, ZX), div_up(v.H, ZY), nzc * B), dim3(ZX, ZY), 0, s>>>(op, v, r, P, nzc);
+    const int zlen = box_zc(v, B), nzc = div_up(v.D, zlen);
+    box_z_kernel<NCH, Op><<<dim3(div_up(v.W, ZX), div_up(v.H, ZY), nzc * B), dim3(ZX, ZY), 0, s>>>(op, v, r, P, nzc,
+                                                                                                 zlen);
     return cudaGetLastError();
 }
 
@@ -640,7 +646,24 @@ __global__ void sum_images_kernel(const float* __restrict__ g, int B, float* __r
 
 }  // namespace
 
-int box_blocks(const Vol& v) { return div_up(v.W, ZX) * div_up(v.H, ZY) * div_up(v.D, ZC); }
+int box_yc(const Vol& v, int B)
+{
+    int yc = B >= 8 ? YC_WIDE : YC;
+    while (yc > YC_MIN && (long long)div_up(v.W, 32) * div_up(v.H, yc) * div_up(v.D, XW) * B < BOX_MIN_BLOCKS)
+        yc /= 2;
+    return std::max(yc, YC_MIN);
+}
+
+int box_zc(const Vol& v, int B)
+{
+    int zc = ZC;
+    while (zc > ZC_MIN && (long long)div_up(v.W, ZX) * div_up(v.H, ZY) * div_up(v.D, zc) * B < BOX_MIN_BLOCKS) zc /= 2;
+    return std::max(zc, ZC_MIN);
+}
+
+int box_blocks(const Vol& v, int B) { return div_up(v.W, ZX) * div_up(v.H, ZY) * div_up(v.D, box_zc(v, B)); }
+
+int box_blocks_max(const Vol& v) { return div_up(v.W, ZX) * div_up(v.H, ZY) * div_up(v.D, ZC_MIN); }
 
 cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, float* P, cudaStream_t s)
 {
@@ -659,7 +682,7 @@ cudaError_t atlas_sgd_forward(const float* J, const float* jstats, const int* su
                               int nb, const Vol& v, float* P, cudaStream_t s)
 {
     const int w = 2 * r + 1;
-    AtlasFwdOp op{J, jstats, subj, A, astats, coef, partials, box_blocks(v), v.V,
+    AtlasFwdOp op{J, jstats, subj, A, astats, coef, partials, box_blocks(v, nb), v.V,
                   (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V), metric};
     return launch_box<1>(op, nb, v, r, P, s);
 }
@@ -689,7 +712,7 @@ cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* js
     op.A = A;
     op.coef = coef;
     op.partials = partials;
-    op.nblk = box_blocks(v);
+    op.nblk = box_blocks(v, 1);
     op.V = v.V;
     op.invN = (float)(1.0 / ((double)w * w * w));
     op.eps = eps;
@@ -776,7 +799,7 @@ cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const 
                          const Vol& v, float* P, cudaStream_t s)
 {
     const int w = 2 * r + 1;
-    FwdOp op{J, subj, A, stats, coef, partials, box_blocks(v), v.V,
+    FwdOp op{J, subj, A, stats, coef, partials, box_blocks(v, B), v.V,
              (float)(1.0 / ((double)w * w * w)), eps, (float)(-1.0 / (double)v.V), wrt_atlas, metric};
     return launch_box<3>(op, B, v, r, P, s);
 }
@@ -799,10 +822,10 @@ cudaError_t lncc_backward_warp_reg(const float* J, const float* A, const float* 
     if (uT_packed) {
         if (reinterpret_cast<uintptr_t>(uT) & 15) return cudaErrorMisalignedAddress;
         BwdWarpRegOp<PackedField> op{J, A, coef, I, I_bstride, PackedField{reinterpret_cast<const float4*>(uT), v.V},
-                                     gT, partials, box_blocks(v), v, negInvV, lambda, rw};
+                                     gT, partials, box_blocks(v, B), v, negInvV, lambda, rw};
         return launch_box<3>(op, B, v, r, P, s);
     }
-    BwdWarpRegOp<PlanarField> op{J, A, coef, I, I_bstride, PlanarField{uT, v.V}, gT, partials, box_blocks(v), v,
+    BwdWarpRegOp<PlanarField> op{J, A, coef, I, I_bstride, PlanarField{uT, v.V}, gT, partials, box_blocks(v, B), v,
                                  negInvV, lambda, rw};
     return launch_box<3>(op, B, v, r, P, s);
 }

@@ -212,7 +212,13 @@ cudaError_t downsample_image(const float* I, int D, int H, int W, float* Ih, int
 
 // ---- local NCC (k_lncc.cu) ----
 // Box sums need scratch P of B x (channels <= 3) x V floats for the 2-D sums.
-int box_blocks(const Vol& v);
+// Z-pass blocks per image of a box-sum launch of B images (its loss
+// partials are laid out [B][box_blocks(v, B)]); at most box_blocks_max(v)
+int box_blocks(const Vol& v, int B);
+int box_blocks_max(const Vol& v);
+// XY strip height and Z chunk of a launch of B images
+int box_yc(const Vol& v, int B);
+int box_zc(const Vol& v, int B);
 // window statistics of the atlas: stats[0] = Box(A), stats[1] = Box(A^2)
 cudaError_t atlas_stats(const float* A, float* stats, int r, const Vol& v, float* P, cudaStream_t s);
 // forward: box sums of J, J^2, J*A; the patch metric m (metric 0: local
