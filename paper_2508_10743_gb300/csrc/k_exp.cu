@@ -85,7 +85,7 @@ exp_square_kernel(Src src_all, float scale, float* __restrict__ dst, Vol v, int 
 // the lower-z corners of its next plane when the two cells coincide (the
 // usual case for a smooth field), so most corners are sent once, not twice.
 #ifndef DARC_ADJ_Z
-#define DARC_ADJ_Z 8
+#define DARC_ADJ_Z 16
 #endif
 #ifndef DARC_ADJ_PAIR
 #define DARC_ADJ_PAIR 1
@@ -97,6 +97,13 @@ exp_square_kernel(Src src_all, float scale, float* __restrict__ dst, Vol v, int 
 #define DARC_ADJ_CARRY 1
 #endif
 constexpr int ADJ_Z = DARC_ADJ_Z;
+// planes per thread of the far-source scatter: its blocks are the gather's
+// 32 x 8 x 8 mark tiles
+constexpr int FAR_Z = 8;
+// resident blocks per SM asked of the interleaved adjoint (a register cap)
+#ifndef DARC_ADJ_MINB
+#define DARC_ADJ_MINB 1
+#endif
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
 // The two x-corners (a, a + 1) of one (z, y) corner pair, three channels.
@@ -284,11 +291,12 @@ __device__ __forceinline__ bool near_source(float uz, float uy, float ux)
 // outgoing one is always interleaved [V] float4 per field.  FAR: only the
 // transpose terms of far sources, in marked tiles (flags).
 template <bool IN4, class Src, bool FAR = false>
-__global__ void __launch_bounds__(VT_THREADS)
+__global__ void __launch_bounds__(VT_THREADS, DARC_ADJ_MINB)
 exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ gin,
                            float4* __restrict__ gout, float out_scale, Vol v, int nzt, int* flags = nullptr)
 {
     if (FAR && !far_tile(flags)) return;
+    constexpr int ZT = FAR ? FAR_Z : ADJ_Z;   // planes per thread
     const int lane = threadIdx.x;
     const int x = blockIdx.x * VT_X + threadIdx.x;
     const int y = blockIdx.y * VT_Y + threadIdx.y;
@@ -301,8 +309,8 @@ exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ g
     const int plane = v.H * v.W;
     float4 cl[2], cu[2];             // carried upper-z pairs: [dy] lower / upper x-corner
     int ca = -1;                     // base index of the carried pairs (-1: none)
-    for (int k = 0; k < ADJ_Z; ++k) {
-        const int z = zt * ADJ_Z + k;
+    for (int k = 0; k < ZT; ++k) {
+        const int z = zt * ZT + k;
         bool active = xy_ok && z < v.D;
         float w[8];
         float4 gs = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -388,8 +396,8 @@ exp_far_planar_kernel(Src src_all, float scale, const float* __restrict__ gin, f
     const float* g0 = gin + (size_t)b * (IN4 ? 4 : 3) * v.V;
     float* o = gout + (size_t)b * 3 * v.V;
     const int plane = v.H * v.W;
-    for (int k = 0; k < ADJ_Z; ++k) {
-        const int z = zt * ADJ_Z + k;
+    for (int k = 0; k < FAR_Z; ++k) {
+        const int z = zt * FAR_Z + k;
         if (z >= v.D) break;
         const int l = z * plane + y * v.W + x;
         const float3 u = f.own(l);
@@ -528,13 +536,13 @@ cudaError_t exp_adjoint_far(const float* src, int src_packed, float scale, const
                             float* gout, int gout_interleaved, float out_scale, int* flags, int B, const Vol& v,
                             cudaStream_t s)
 {
-    static_assert(ADJ_Z == 8 && VT_X == 32 && VT_Y == 8, "far-scatter blocks are the gather's 32 x 8 x 8 mark tiles");
+    static_assert(FAR_Z == 8 && VT_X == 32 && VT_Y == 8, "far-scatter blocks are the gather's 32 x 8 x 8 mark tiles");
     if ((src_packed && (reinterpret_cast<uintptr_t>(src) & 15)) ||
         (gin_interleaved && (reinterpret_cast<uintptr_t>(gin) & 15)) ||
         (gout_interleaved && (reinterpret_cast<uintptr_t>(gout) & 15)))
         return cudaErrorMisalignedAddress;
     int nzt;
-    const dim3 grid = voxel_grid(B, v, nzt, ADJ_Z);
+    const dim3 grid = voxel_grid(B, v, nzt, FAR_Z);
     if (src_packed)
         launch_far(PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, gin, gin_interleaved, gout,
                    gout_interleaved, out_scale, flags, grid, v, nzt, s);
