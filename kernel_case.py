@@ -38,7 +38,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", required=True,
                     choices=["exp_square", "exp_adjoint", "lncc", "subject_grad", "warp", "cohort_step",
-                             "atlas_update", "atlas_sharded", "unet_step", "unet_forward"])
+                             "atlas_update", "atlas_sharded", "unet_step", "unet_forward", "unet_layers"])
     ap.add_argument("--shape", type=int, nargs=3, default=[160, 192, 224])
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--window", type=int, default=9)
@@ -51,6 +51,9 @@ def main():
     dev = torch.device("cuda:0")
     shape = tuple(a.shape)
     B = a.batch
+    if a.kernel == "unet_layers":
+        _unet_layers(a, dev, tuple(a.shape), a.batch)
+        return
     if a.kernel.startswith("unet"):
         g = torch.Generator(device=dev).manual_seed(0)
         subj = torch.rand(B, *shape, device=dev, generator=g)
@@ -107,6 +110,49 @@ def main():
             darc.subject_grad(cfg, I, A, v)
 
     _time(run, a, shape, B)
+
+
+# the warm-start network's 15 convolutions: (cin, cout, level)
+UNET_SPEC = [(2, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2), (64, 128, 3),
+             (128, 128, 3), (192, 64, 2), (64, 64, 2), (96, 32, 1), (32, 32, 1), (48, 16, 0), (16, 16, 0),
+             (16, 3, 0)]
+
+
+def _unet_layers(a, dev, shape, B):
+    """Each convolution of the network alone (forward with bias and leaky
+    ReLU, and weight gradient) on random data at its level's resolution:
+    CUDA-event time and TFLOP/s of the real channels (2 B V 27 cin cout)."""
+    r16 = lambda c: (c + 15) // 16 * 16                 # noqa: E731
+    g = torch.Generator(device=dev).manual_seed(0)
+    rows = []
+    for li, (cin, cout, lev) in enumerate(UNET_SPEC):
+        D, H, W = (s >> lev for s in shape)
+        cp, np_ = r16(cin), r16(cout)
+        x = torch.zeros((B, D + 2, H + 2, W + 2, cp), dtype=torch.bfloat16, device=dev)
+        x[:, 1:-1, 1:-1, 1:-1, :cin] = torch.randn((B, D, H, W, cin), generator=g, device=dev).to(torch.bfloat16)
+        w = torch.randn((np_, 27 * cp), generator=g, device=dev) * 0.05
+        bias = torch.zeros(cout, device=dev)
+        wt = darc.conv3d_pack_weights(w, cp, cout)
+        gz = torch.zeros((B, D + 2, H + 2, W + 2, cout), dtype=torch.bfloat16, device=dev)
+        gz[:, 1:-1, 1:-1, 1:-1] = torch.randn((B, D, H, W, cout), generator=g, device=dev).to(torch.bfloat16)
+        flop = 2.0 * B * D * H * W * 27 * cin * cout
+        res = {"layer": li, "cin": cin, "cout": cout, "grid": [D, H, W]}
+        for name, fn in (("fwd", lambda: darc.conv3d(x, cp, wt, cout, np_, bias=bias, act=True)),
+                         ("wgrad", lambda: darc.conv3d_wgrad(x, cp, gz, cout, np_))):
+            for _ in range(a.warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(a.reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / a.reps
+            res[name + "_ms"] = round(ms, 4)
+            res[name + "_tflops"] = round(flop / ms / 1e9, 1)
+        rows.append(res)
+        print(json.dumps(res), flush=True)
 
 
 def _time(run, a, shape, B):
