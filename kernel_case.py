@@ -133,12 +133,13 @@ def _unet_layers(a, dev, shape, B):
         w = torch.randn((np_, 27 * cp), generator=g, device=dev) * 0.05
         bias = torch.zeros(cout, device=dev)
         wt = darc.conv3d_pack_weights(w, cp, cout)
-        gz = torch.zeros((B, D + 2, H + 2, W + 2, cout), dtype=torch.bfloat16, device=dev)
-        gz[:, 1:-1, 1:-1, 1:-1] = torch.randn((B, D, H, W, cout), generator=g, device=dev).to(torch.bfloat16)
+        cw = (cout + 7) // 8 * 8                    # the weight gradient reads channel groups of 8
+        gz = torch.zeros((B, D + 2, H + 2, W + 2, cw), dtype=torch.bfloat16, device=dev)
+        gz[:, 1:-1, 1:-1, 1:-1, :cout] = torch.randn((B, D, H, W, cout), generator=g, device=dev).to(torch.bfloat16)
         flop = 2.0 * B * D * H * W * 27 * cin * cout
         res = {"layer": li, "cin": cin, "cout": cout, "grid": [D, H, W]}
         for name, fn in (("fwd", lambda: darc.conv3d(x, cp, wt, cout, np_, bias=bias, act=True)),
-                         ("wgrad", lambda: darc.conv3d_wgrad(x, cp, gz, cout, np_))):
+                         ("wgrad", lambda: darc.conv3d_wgrad(x, cp, gz, cw, np_))):
             for _ in range(a.warmup):
                 fn()
             torch.cuda.synchronize()
