@@ -439,6 +439,11 @@ conv3_wgrad_kernel(WgradArgs a)
 constexpr int WG_KC = 64;                 // rows (K) per stage
 constexpr int WG_RA = WG_KC + 2;          // input window rows per stage
 
+// With few input channels most of the 128 lanes would idle, so a CTA then
+// stacks `pairs` consecutive (dz, dy) pairs (tap pair index 3 dz + dy) in
+// the M dimension: lane row = (pair within the CTA, channel), each pair's
+// channel groups staged from its own shifted window.  The dx taps shift all
+// of them alike.
 struct WgradWinArgs {
     const bf16* in;
     int in_stride, cin;                   // cin % 16 == 0
@@ -449,6 +454,7 @@ struct WgradWinArgs {
     int B, sp;                            // splits per batch
     long long chunk;                      // rows per split (multiple of WG_KC)
     int kp, np, ns, slot_bytes;
+    int pairs;                            // (dz, dy) pairs per CTA (> 1 only when cin <= 64)
 };
 
 __global__ void __launch_bounds__(128)
@@ -459,23 +465,23 @@ conv3_wgrad_win_kernel(WgradWinArgs a)
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const PadVol g = a.g;
-    const int dz = blockIdx.x / 3, dy = blockIdx.x - 3 * dz;
+    const int pair0 = blockIdx.x * a.pairs, npair = min(a.pairs, 9 - pair0);   // tap pairs 3 dz + dy
     const int c0 = blockIdx.y * TC_M, nci = min(TC_M, a.cin - c0), ng = nci / 8;
+    const int used = npair * ng;                                  // 8-lane groups in use (<= 16)
     const int b = blockIdx.z / a.sp, spi = blockIdx.z - b * a.sp;
     const long long DP = (long long)g.D * g.P;
     const long long r0 = (long long)spi * a.chunk, r1 = min(DP, r0 + a.chunk);
     const long long base = (long long)b * g.Vp + g.P;            // padded row of interior row 0 of batch b
     const long long rows_total = (long long)a.B * g.Vp;
-    const long long off = (long long)(dz - 1) * g.P + (long long)(dy - 1) * g.Wp;
     const int steps = r1 > r0 ? (int)((r1 - r0 + WG_KC - 1) / WG_KC) : 0;
     const uint32_t strideA = (uint32_t)WG_RA * 16u, strideB = (uint32_t)WG_KC * 16u;
     const int bytesA = 16 * WG_RA * 16;                           // 16 channel groups (M = 128)
     uint32_t ncols = 32;
     while ((int)ncols < 3 * a.np) ncols <<= 1;
-    // channel groups the tile does not use stay zero in every slot
-    for (int e = tid; e < a.ns * (16 - ng) * WG_RA; e += 128) {
-        const int slot = e / ((16 - ng) * WG_RA), rest = e - slot * (16 - ng) * WG_RA;
-        const int gi = ng + rest / WG_RA, r = rest % WG_RA;
+    // lane groups the tile does not use stay zero in every slot
+    for (int e = tid; e < a.ns * (16 - used) * WG_RA; e += 128) {
+        const int slot = e / ((16 - used) * WG_RA), rest = e - slot * (16 - used) * WG_RA;
+        const int gi = used + rest / WG_RA, r = rest % WG_RA;
         *reinterpret_cast<uint4*>(smem + (size_t)slot * a.slot_bytes + gi * strideA + r * 16) = make_uint4(0u, 0u, 0u, 0u);
     }
     if (warp == 0) umma::tmem_alloc(&tslot, ncols);
@@ -489,17 +495,32 @@ conv3_wgrad_win_kernel(WgradWinArgs a)
     const uint32_t tmem = tslot;
     const uint32_t idesc = umma::idesc_bf16_f32_mn(TC_M, a.np);
 
+    // this thread's A copies of every stage (fixed over the stages but for
+    // the stage's first row): shared-memory offset, row offset of its
+    // window row from the stage's first row, channel offset
+    constexpr int WG_AMAX = (16 * WG_RA + 127) / 128;
+    int a_sm[WG_AMAX], a_row[WG_AMAX], a_ch[WG_AMAX];
+    const int na = (used * WG_RA - tid + 127) / 128;
+#pragma unroll
+    for (int i = 0; i < WG_AMAX; ++i) {
+        const int e = tid + 128 * i;
+        const int grp = e / WG_RA, r = e - grp * WG_RA;
+        const int pl = grp / ng, gi = grp - pl * ng, pr = pair0 + pl;
+        a_sm[i] = grp * (int)strideA + r * 16;
+        a_row[i] = (pr / 3 - 1) * (int)g.P + (pr % 3 - 1) * g.Wp - 1 + r;   // window row r (dx = 0 at r = 0)
+        a_ch[i] = c0 + 8 * gi;
+    }
     auto load = [&](int st, int slot) {
         uint8_t* As = smem + (size_t)slot * a.slot_bytes;
         uint8_t* Bs = As + bytesA;
         const long long k0 = r0 + (long long)st * WG_KC;
-        const long long ga = base + k0 + off - 1;                // window row 0 (dx = 0)
-        for (int e = tid; e < ng * WG_RA; e += 128) {
-            const int gi = e / WG_RA, r = e - gi * WG_RA;
-            const long long q = ga + r;
+#pragma unroll
+        for (int i = 0; i < WG_AMAX; ++i) {
+            if (i >= na) break;
+            const long long q = base + k0 + a_row[i];
             const bool ok = q >= 0 && q < rows_total;
-            const bf16* src = ok ? a.in + q * a.in_stride + c0 + 8 * gi : a.in;
-            cp_async16(As + gi * strideA + r * 16, src, ok ? 16 : 0);
+            const bf16* src = ok ? a.in + q * a.in_stride + a_ch[i] : a.in;
+            cp_async16(As + a_sm[i], src, ok ? 16 : 0);
         }
         for (int e = tid; e < (a.np / 8) * WG_KC; e += 128) {
             const int go = e / WG_KC, r = e - go * WG_KC;
@@ -542,15 +563,17 @@ conv3_wgrad_win_kernel(WgradWinArgs a)
     }
     if (steps > 0) ok = umma::mbar_wait(&mbar[(steps - 1) % a.ns], (uint32_t)(((steps - 1) / a.ns) & 1), TC_WAIT) && ok;
     umma::fence_after_sync();
-    // epilogue: lane = input channel c0 + 32 w + lane, columns dx * np + co
-    const int ci = c0 + 32 * warp + lane;
+    // epilogue: lane m = 32 w + lane is channel c0 + m % (8 ng) of the CTA's
+    // pair m / (8 ng); columns dx * np + co
+    const int m = 32 * warp + lane, pr = pair0 + m / (8 * ng);
+    const int ci = c0 + m % (8 * ng);
     for (int dx = 0; dx < 3; ++dx) {
-        const int tap = 9 * dz + 3 * dy + dx;
+        const int tap = 3 * pr + dx;                             // 9 dz + 3 dy + dx
         float* out = a.partial + ((size_t)blockIdx.z * a.kp + (size_t)tap * a.cin + ci) * a.np;
         for (int c = 0; c < a.np; c += 8) {
             float r8[8];
             umma::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(dx * a.np + c), r8);
-            if (ci < c0 + nci) {
+            if (m < 8 * used) {
 #pragma unroll
                 for (int q = 0; q < 8; ++q)
                     out[c + q] = (steps > 0 && ok) ? r8[q] : (ok ? 0.f : __int_as_float(0x7fc00000));
@@ -913,6 +936,7 @@ cudaError_t conv3_wgrad_win(const void* in, int in_stride, int cin, const void* 
     a.np = np;
     a.slot_bytes = (16 * WG_RA * 16 + np * WG_KC * 2 + 127) / 128 * 128;
     a.ns = (3 * a.slot_bytes <= 200 * 1024) ? 3 : 2;
+    a.pairs = cin <= 64 ? std::min(9, 16 / (cin / 8)) : 1;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(conv3_wgrad_win_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -920,12 +944,18 @@ cudaError_t conv3_wgrad_win(const void* in, int in_stride, int cin, const void* 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const dim3 grid(9, (cin + TC_M - 1) / TC_M, a.sp * batch);
+    const dim3 grid((9 + a.pairs - 1) / a.pairs, (cin + TC_M - 1) / TC_M, a.sp * batch);
     conv3_wgrad_win_kernel<<<grid, 128, (size_t)a.ns * a.slot_bytes, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     conv3_wgrad_reduce_kernel<<<ew_grid((long long)kp * np), 256, 0, s>>>(partial, a.sp * batch, kp, np, dw);
     return cudaGetLastError();
+}
+
+int wgrad_ctas_per_split(int cin)
+{
+    const int pairs = cin <= 64 ? std::min(9, 16 / std::max(cin / 8, 1)) : 1;
+    return (9 + pairs - 1) / pairs * ((cin + TC_M - 1) / TC_M);
 }
 
 cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout, float* partial,

@@ -190,6 +190,9 @@ cudaError_t pack_weights(const float* w, int kp, int cin, int cout, int conv_cin
 // rows of the interior planes; partial: splits x kp x np floats
 cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout, float* partial,
                         int splits, float* dw, int batch, int D, int H, int W, int kp, int np, cudaStream_t s);
+// CTAs of one split of the weight gradient's window kernel (callers size
+// their splits so a launch has about four CTAs per SM)
+int wgrad_ctas_per_split(int cin);
 // db[c] = sum over rows of gz[v][c]; (cout + 7) / 8 must divide 256; work:
 // bias_grad_work_floats(cout) floats
 int bias_grad_work_floats(int cout);

@@ -548,7 +548,7 @@ def conv3d_wgrad(x: torch.Tensor, cin: int, gz: torch.Tensor, cout: int, np_: in
     kp = 27 * cin
     dw = torch.empty((np_, kp), dtype=torch.float32, device=x.device)
     db = torch.empty(cout, dtype=torch.float32, device=x.device)
-    nbytes = 64 * kp * np_ * 4
+    nbytes = max(256 * kp * np_ * 4, 256 * 4 * ((cout + 7) // 8) * 8 * 4)   # split-K partials, bias partials
     work = _work(nbytes, x.device)
     _check(lib().darc_conv3d_wgrad(_ptr(x), S, cin, _ptr(gz), int(gz.shape[-1]), cout, _ptr(dw), _ptr(db), B,
                                    Dp - 2, Hp - 2, Wp - 2, np_, _ptr(work), nbytes, _stream()))

@@ -145,8 +145,12 @@ def test_conv3d_data_gradient_matches_oracle_adjoint(B, shape, cin, cout):
 
 @pytest.mark.parametrize("B,shape,cin,S,cout", [(2, (6, 7, 9), 16, 16, 16), (2, (16, 16, 20), 16, 16, 16),
                                                  (1, (8, 8, 12), 48, 48, 16), (1, (4, 4, 8), 128, 128, 128),
-                                                 (2, (5, 6, 8), 192, 192, 64), (3, (9, 10, 40), 32, 48, 32)])
+                                                 (2, (5, 6, 8), 192, 192, 64), (3, (9, 10, 40), 32, 48, 32),
+                                                 (1, (6, 7, 8), 64, 64, 64), (2, (10, 9, 11), 16, 16, 8)])
 def test_conv3d_weight_gradient_matches_oracle(B, shape, cin, S, cout):
+    """Every layout of the weight gradient's tiles: 16-channel inputs stack
+    eight (dz, dy) tap pairs in a CTA's 128 lanes, 32 four, 48 and 64 two;
+    128 and 192 channels take one pair and one or two channel tiles."""
     g = torch.Generator().manual_seed(cin * 7 + cout + B)
     np_ = rup(cout, 16)
     x = rand_padded(g, B, shape, S)
