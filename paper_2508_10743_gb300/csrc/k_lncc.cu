@@ -71,13 +71,14 @@ size_t xy_smem_bytes(int nch, int r)
     return sizeof(float) * (size_t)XW * ((size_t)nch * (32 + 2 * r) + (size_t)(w + 1) * nch * 32);
 }
 
-// P[b][c] = 2-D window sums (x, y) of the input channels of every plane
-template <int NCH, class Op>
+// P[b][c] = 2-D window sums (x, y) of the input channels of every plane.
+// WT: the window edge when known at compile time (the x sums unroll), or 0.
+template <int NCH, class Op, int WT>
 __global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, float* __restrict__ P, int nzb,
                                                          int yc)
 {
     extern __shared__ float sm[];
-    const int w = 2 * r + 1, LXW = 32 + 2 * r, NR = w + 1;
+    const int w = WT > 0 ? WT : 2 * r + 1, LXW = 32 + 2 * r, NR = w + 1;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int b = blockIdx.z / nzb;
     const int z = (blockIdx.z % nzb) * XW + wp;
@@ -124,7 +125,12 @@ __global__ void __launch_bounds__(XW * 32) box_xy_kernel(Op op, Vol v, int r, fl
         for (int c = 0; c < NCH; ++c) {
             const float* rr = row + c * LXW + lane;
             float xsum = 0.f;
-            for (int d = 0; d < w; ++d) xsum += rr[d];
+            if constexpr (WT > 0) {
+#pragma unroll
+                for (int d = 0; d < WT; ++d) xsum += rr[d];
+            } else {
+                for (int d = 0; d < w; ++d) xsum += rr[d];
+            }
             ys[c] += xsum;
             if (drop) ys[c] -= ring[(old * NCH + c) * 32 + lane];
             ring[(slot * NCH + c) * 32 + lane] = xsum;     // lane-private
@@ -611,21 +617,35 @@ struct AtlasBwdGradOp {
     __device__ void partial(int, int, double) const {}
 };
 
-template <int NCH, class Op>
-cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, float* P, cudaStream_t s)
+template <int NCH, class Op, int WT>
+cudaError_t launch_xy(const Op& op, int B, const Vol& v, int r, float* P, cudaStream_t s)
 {
-    static bool attr_set = false;   // once per instantiation, sized for the largest window (r = 8)
+    static bool attr_set = false;   // once per instantiation, sized for its largest window
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(box_xy_kernel<NCH, Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)xy_smem_bytes(NCH, 8));
+        cudaError_t e = cudaFuncSetAttribute(box_xy_kernel<NCH, Op, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)xy_smem_bytes(NCH, WT > 0 ? WT / 2 : 8));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int nzb = div_up(v.D, XW);
     const int yc = box_yc(v, B);
-    box_xy_kernel<NCH, Op><<<dim3(div_up(v.W, 32), div_up(v.H, yc), nzb * B), XW * 32, xy_smem_bytes(NCH, r), s>>>(
-        op, v, r, P, nzb, yc);
-    cudaError_t e = cudaGetLastError();
+    box_xy_kernel<NCH, Op, WT><<<dim3(div_up(v.W, 32), div_up(v.H, yc), nzb * B), XW * 32, xy_smem_bytes(NCH, r),
+                                 s>>>(op, v, r, P, nzb, yc);
+    return cudaGetLastError();
+}
+
+template <int NCH, class Op>
+cudaError_t launch_box(const Op& op, int B, const Vol& v, int r, float* P, cudaStream_t s)
+{
+    // windows of 3 to 9 voxels (the workloads' own) get their unrolled XY pass
+    cudaError_t e;
+    switch (r) {
+    case 1: e = launch_xy<NCH, Op, 3>(op, B, v, r, P, s); break;
+    case 2: e = launch_xy<NCH, Op, 5>(op, B, v, r, P, s); break;
+    case 3: e = launch_xy<NCH, Op, 7>(op, B, v, r, P, s); break;
+    case 4: e = launch_xy<NCH, Op, 9>(op, B, v, r, P, s); break;
+    default: e = launch_xy<NCH, Op, 0>(op, B, v, r, P, s); break;
+    }
     if (e != cudaSuccess) return e;
     const int zlen = box_zc(v, B), nzc = div_up(v.D, zlen);
     box_z_kernel<NCH, Op><<<dim3(div_up(v.W, ZX), div_up(v.H, ZY), nzc * B), dim3(ZX, ZY), 0, s>>>(op, v, r, P, nzc,
