@@ -63,7 +63,10 @@ constexpr int ZX = 32, ZY = 8, ZC = DARC_BOX_ZC;
 // Small launches (one small image) would leave most SMs idle with these
 // tiles: the XY strip and the Z chunk shrink (down to 16 rows, 8 planes)
 // until a launch has at least two blocks per SM.
-constexpr int BOX_MIN_BLOCKS = 2 * 152, YC_MIN = 16, ZC_MIN = 8;
+#ifndef DARC_BOX_MIN_BLOCKS
+#define DARC_BOX_MIN_BLOCKS (2 * 152)
+#endif
+constexpr int BOX_MIN_BLOCKS = DARC_BOX_MIN_BLOCKS, YC_MIN = 16, ZC_MIN = 8;
 
 size_t xy_smem_bytes(int nch, int r)
 {

@@ -46,6 +46,7 @@ def run_cohort(images, cfg, sweeps, net=None, batch=4, log=None, tag=""):
     torch.cuda.synchronize()
     t_init = time.perf_counter() - t0
     ncc, secs = [], []
+    st = {"centrality_after": None}
     for s in range(sweeps):
         st = co.sweep(stats=True)                     # waits for the stream
         ncc.append(-st["loss_data"])
