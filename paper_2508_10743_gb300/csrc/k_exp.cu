@@ -102,7 +102,12 @@ constexpr int ADJ_Z = DARC_ADJ_Z;
 constexpr int FAR_Z = 8;
 // resident blocks per SM asked of the interleaved adjoint (a register cap)
 #ifndef DARC_ADJ_MINB
-#define DARC_ADJ_MINB 1
+#define DARC_ADJ_MINB 4
+#endif
+// 1: the interleaved adjoint loads the next plane's displacement and
+// gradient while it works on the current one
+#ifndef DARC_ADJ_PREFETCH
+#define DARC_ADJ_PREFETCH 1
 #endif
 constexpr unsigned FULL_MASK = 0xffffffffu;
 
@@ -309,22 +314,46 @@ exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ g
     const int plane = v.H * v.W;
     float4 cl[2], cu[2];             // carried upper-z pairs: [dy] lower / upper x-corner
     int ca = -1;                     // base index of the carried pairs (-1: none)
+    constexpr bool PF = DARC_ADJ_PREFETCH && !FAR;
+    float3 u_nx = make_float3(0.f, 0.f, 0.f), g_nx = u_nx;   // the next plane's (prefetch)
+    auto fetch = [&](int kk) {
+        const int zz = zt * ZT + kk;
+        if (xy_ok && zz < v.D) {
+            const int ll = zz * plane + y * v.W + x;
+            u_nx = f.own(ll);
+            if (IN4) {
+                const float4 q = __ldg(reinterpret_cast<const float4*>(g0) + ll);
+                g_nx = make_float3(q.x, q.y, q.z);
+            } else {
+                g_nx = make_float3(__ldg(g0 + ll), __ldg(g0 + v.V + ll), __ldg(g0 + 2 * v.V + ll));
+            }
+        }
+    };
+    if (PF) fetch(0);
     for (int k = 0; k < ZT; ++k) {
         const int z = zt * ZT + k;
         bool active = xy_ok && z < v.D;
         float w[8];
         float4 gs = make_float4(0.f, 0.f, 0.f, 0.f);
         int cb = -4;
-        float3 u = make_float3(0.f, 0.f, 0.f);
+        float3 u = make_float3(0.f, 0.f, 0.f), gpf = u;
         const int l = z * plane + y * v.W + x;
-        if (active) {
+        if (PF) {
+            u = u_nx;
+            gpf = g_nx;
+            if (k + 1 < ZT) fetch(k + 1);
+        } else if (active) {
             u = f.own(l);
             if (FAR && near_source(scale * u.x, scale * u.y, scale * u.z)) active = false;
         }
         if (active) {
             const Cell c = make_cell_warp(z, y, x, scale * u.x, scale * u.y, scale * u.z, v);
             float gz, gy, gx;
-            if (IN4) {
+            if (PF) {
+                gz = gpf.x;
+                gy = gpf.y;
+                gx = gpf.z;
+            } else if (IN4) {
                 const float4 g4 = __ldg(reinterpret_cast<const float4*>(g0) + l);
                 gz = g4.x;
                 gy = g4.y;
