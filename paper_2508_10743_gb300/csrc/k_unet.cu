@@ -128,6 +128,14 @@ gemm_bf16_kernel(const bf16* __restrict__ A, const bf16* __restrict__ B, float* 
 // stages rotate; a stage's slot is refilled once the commit of the MMAs
 // that read it has arrived on the slot's mbarrier (bounded waits; a timeout
 // poisons the output with NaN instead of hanging).
+// pipeline slots of the window convolution: 2 = two (more resident blocks:
+// a block runs only 3 x cin/16 stages, and the blocks of an SM hide each
+// other's latencies better than a deeper pipeline does), 0 = three where
+// they fit in 200 KB
+#ifndef DARC_CONV_NS
+#define DARC_CONV_NS 2
+#endif
+
 struct WinArgs {
     const bf16* in;
     int in_stride, nchunk;        // channels [0, 16 nchunk) read
@@ -854,7 +862,7 @@ cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s)
     a.np = d.np;
     a.R = conv_window_rows(d.W);
     a.slot_bytes = conv_slot_bytes(d.W, d.np);
-    a.ns = (3 * a.slot_bytes <= 200 * 1024) ? 3 : 2;
+    a.ns = (DARC_CONV_NS == 2 || 3 * a.slot_bytes > 200 * 1024) ? 2 : 3;
     a.tiles_per_batch = ((long long)d.D * a.g.P + TC_M - 1) / TC_M;
     if (!conv_fits(d.W, d.np)) return cudaErrorInvalidValue;
     static bool attr = false;
@@ -956,6 +964,33 @@ int wgrad_ctas_per_split(int cin)
 {
     const int pairs = cin <= 64 ? std::min(9, 16 / std::max(cin / 8, 1)) : 1;
     return (9 + pairs - 1) / pairs * ((cin + TC_M - 1) / TC_M);
+}
+
+int wgrad_resident_ctas(int np)
+{
+    // blocks of the weight-gradient window kernel resident at once on the
+    // device: a split-K grid of at most this many runs in one wave
+    static int sms = 0, smem_sm = 0, smem_rsv = 0, regs = 0, smem_static = 0;
+    if (!sms) {
+        int dev = 0, n = 0;
+        cudaFuncAttributes fa{};
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, conv3_wgrad_win_kernel) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 4 * 152;
+        }
+        regs = fa.numRegs;
+        smem_static = (int)fa.sharedSizeBytes;
+        sms = n;
+    }
+    const int slot = (16 * WG_RA * 16 + np * WG_KC * 2 + 127) / 128 * 128;
+    const int ns = (3 * slot <= 200 * 1024) ? 3 : 2;
+    const int per_smem = smem_sm / (ns * slot + smem_static + smem_rsv);
+    const int per_regs = 65536 / (((regs + 7) & ~7) * 128);
+    return std::max(1, std::min({per_smem, per_regs, 16})) * sms;
 }
 
 cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, int gz_stride, int cout, float* partial,

@@ -193,6 +193,7 @@ cudaError_t conv3_wgrad(const void* in, int in_stride, int cin, const void* gz, 
 // CTAs of one split of the weight gradient's window kernel (callers size
 // their splits so a launch has about four CTAs per SM)
 int wgrad_ctas_per_split(int cin);
+int wgrad_resident_ctas(int np);
 // db[c] = sum over rows of gz[v][c]; (cout + 7) / 8 must divide 256; work:
 // bias_grad_work_floats(cout) floats
 int bias_grad_work_floats(int cout);

@@ -181,7 +181,7 @@ int wgrad(darc_unet* u, Layer& l, const Buf& in, int in_off, const Buf& gz, int 
     const PadVol g = make_pad(d[0], d[1], d[2]);
     const long long nrows = (long long)B * d[0] * g.P;
     const int tiles = wgrad_ctas_per_split(l.cinp);
-    int splits = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(608 / tiles, nrows / 1024), 256));
+    int splits = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(wgrad_resident_ctas(l.np) / tiles, nrows / 1024), 256));
     while ((size_t)splits * l.kp * l.np > u->partial_floats && splits > 1) splits /= 2;
     UCK(conv3_wgrad(ch(in, in_off), in.stride, l.cinp, ch(gz, gz_off), gz.stride, l.np, u->partial, splits, l.dw,
                     B, d[0], d[1], d[2], l.kp, l.np, s));
@@ -587,7 +587,7 @@ int darc_conv3d_wgrad(const void* in_dev, int in_stride, int cin, const void* gz
     const PadVol g = make_pad(D, H, W);
     const long long nrows = (long long)batch * D * g.P;
     int splits = (int)std::max<long long>(
-        batch, std::min<long long>(std::min<long long>(256, nrows / 1024), (608 + wgrad_ctas_per_split(cin) - 1) /
+        batch, std::min<long long>(std::min<long long>(256, nrows / 1024), wgrad_resident_ctas(np) /
                                                                                 wgrad_ctas_per_split(cin)));
     while (splits > 1 && (size_t)splits * kp * np * sizeof(float) > work_bytes) splits /= 2;
     if ((size_t)splits * kp * np * sizeof(float) > work_bytes ||

@@ -87,6 +87,8 @@ CONV_CASES = [
     (1, (4, 4, 8), 16, 16, 192, 192),
     (1, (4, 5, 6), 128, 128, 128, 128),
     (1, (3, 4, 112), 16, 16, 256, 256),          # a wide window: two pipeline stages
+    (2, (44, 46, 48), 16, 16, 16, 16),           # several tiles per resident CTA
+    (2, (32, 36, 40), 48, 64, 16, 16),           # and three channel chunks per tile
 ]
 
 
