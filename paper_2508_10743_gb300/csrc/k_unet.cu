@@ -649,40 +649,89 @@ __global__ void bias_grad_reduce_kernel(const float* __restrict__ partial, int n
 // 2x average pooling of padded channels-last volumes and its adjoint (fine
 // grid gf, coarse grid gc = gf / 2).  The adjoint adds (g / 8) lrelu'(x) into
 // gx at each of the 8 children (x = the pooled activation, whose
-// pre-activation gradient this is).
+// pre-activation gradient this is).  A thread takes 8 channels of one voxel
+// (16-byte loads and stores: channel counts, strides and channel offsets are
+// multiples of 8); blockIdx.y walks the (batch, plane) pairs of the grid
+// the thread's voxel is on, so the index arithmetic stays in 32 bits.
+__device__ __forceinline__ void bf8_to_f(const uint4& q, float f[8])
+{
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 f_to_bf8(const float f[8])
+{
+    uint4 q;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    return q;
+}
+
+// the voxel (b, z, y, x) and channel group c8 of this thread on grid g, or false
+__device__ __forceinline__ bool vox8(const PadVol& g, int G, int bz, int& b, int& z, int& y, int& x, int& c8)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= g.H * g.W * G) return false;
+    c8 = 8 * (e % G);
+    const int t = e / G;
+    x = t % g.W;
+    y = t / g.W;
+    b = bz / g.D;
+    z = bz - b * g.D;
+    return true;
+}
+
 __global__ void pool2_kernel(const bf16* __restrict__ x, int xs, bf16* __restrict__ y, int ys, int C, int B,
                              PadVol gf, PadVol gc)
 {
-    const long long n = (long long)B * gc.D * gc.H * gc.W * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
-        const int xo = (int)(v % gc.W), yo = (int)((v / gc.W) % gc.H), zo = (int)((v / ((long long)gc.W * gc.H)) % gc.D);
-        const long long b = v / ((long long)gc.W * gc.H * gc.D);
-        float s = 0.f;
+    const int G = C / 8;
+    for (int bz = blockIdx.y; bz < B * gc.D; bz += gridDim.y) {
+        int b, zo, yo, xo, c8;
+        if (!vox8(gc, G, bz, b, zo, yo, xo, c8)) return;
+        float s[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] = 0.f;
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const long long iv = b * gf.Vp + pad_row(gf, 2 * zo + (q >> 2), 2 * yo + ((q >> 1) & 1), 2 * xo + (q & 1));
-            s += __bfloat162float(x[iv * xs + c]);
+            const long long iv = (long long)b * gf.Vp + pad_row(gf, 2 * zo + (q >> 2), 2 * yo + ((q >> 1) & 1),
+                                                                 2 * xo + (q & 1));
+            float f[8];
+            bf8_to_f(*reinterpret_cast<const uint4*>(x + iv * xs + c8), f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += f[j];
         }
-        y[(b * gc.Vp + pad_row(gc, zo, yo, xo)) * ys + c] = __float2bfloat16(0.125f * s);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] *= 0.125f;
+        *reinterpret_cast<uint4*>(y + ((long long)b * gc.Vp + pad_row(gc, zo, yo, xo)) * ys + c8) = f_to_bf8(s);
     }
 }
 
 __global__ void pool2_adjoint_kernel(const bf16* __restrict__ gy, int gys, const bf16* __restrict__ x, int xs,
                                      bf16* __restrict__ gx, int gxs, int C, float slope, int B, PadVol gf, PadVol gc)
 {
-    const long long n = (long long)B * gf.D * gf.H * gf.W * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
-        const int xx = (int)(v % gf.W), yy = (int)((v / gf.W) % gf.H), zz = (int)((v / ((long long)gf.W * gf.H)) % gf.D);
-        const long long b = v / ((long long)gf.W * gf.H * gf.D);
-        const long long ov = b * gc.Vp + pad_row(gc, zz / 2, yy / 2, xx / 2);
-        const long long iv = b * gf.Vp + pad_row(gf, zz, yy, xx);
-        const float gv = 0.125f * __bfloat162float(gy[ov * gys + c]);
-        const float act = __bfloat162float(x[iv * xs + c]);
-        const float add = act > 0.f ? gv : slope * gv;
-        gx[iv * gxs + c] = __float2bfloat16(__bfloat162float(gx[iv * gxs + c]) + add);
+    const int G = C / 8;
+    for (int bz = blockIdx.y; bz < B * gf.D; bz += gridDim.y) {
+        int b, zz, yy, xx, c8;
+        if (!vox8(gf, G, bz, b, zz, yy, xx, c8)) return;
+        const long long ov = (long long)b * gc.Vp + pad_row(gc, zz / 2, yy / 2, xx / 2);
+        const long long iv = (long long)b * gf.Vp + pad_row(gf, zz, yy, xx);
+        float gv[8], act[8], cur[8];
+        bf8_to_f(*reinterpret_cast<const uint4*>(gy + ov * gys + c8), gv);
+        bf8_to_f(*reinterpret_cast<const uint4*>(x + iv * xs + c8), act);
+        uint4* dst = reinterpret_cast<uint4*>(gx + iv * gxs + c8);
+        bf8_to_f(*dst, cur);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float g8 = 0.125f * gv[j];
+            cur[j] += act[j] > 0.f ? g8 : slope * g8;
+        }
+        *dst = f_to_bf8(cur);
     }
 }
 
@@ -690,31 +739,35 @@ __global__ void pool2_adjoint_kernel(const bf16* __restrict__ gy, int gys, const
 __global__ void up2_kernel(const bf16* __restrict__ x, int xs, bf16* __restrict__ y, int ys, int C, int B, PadVol gf,
                            PadVol gc)
 {
-    const long long n = (long long)B * gf.D * gf.H * gf.W * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
-        const int xx = (int)(v % gf.W), yy = (int)((v / gf.W) % gf.H), zz = (int)((v / ((long long)gf.W * gf.H)) % gf.D);
-        const long long b = v / ((long long)gf.W * gf.H * gf.D);
-        y[(b * gf.Vp + pad_row(gf, zz, yy, xx)) * ys + c] = x[(b * gc.Vp + pad_row(gc, zz / 2, yy / 2, xx / 2)) * xs + c];
+    const int G = C / 8;
+    for (int bz = blockIdx.y; bz < B * gf.D; bz += gridDim.y) {
+        int b, zz, yy, xx, c8;
+        if (!vox8(gf, G, bz, b, zz, yy, xx, c8)) return;
+        *reinterpret_cast<uint4*>(y + ((long long)b * gf.Vp + pad_row(gf, zz, yy, xx)) * ys + c8) =
+            *reinterpret_cast<const uint4*>(x + ((long long)b * gc.Vp + pad_row(gc, zz / 2, yy / 2, xx / 2)) * xs + c8);
     }
 }
 
 __global__ void up2_adjoint_kernel(const bf16* __restrict__ gy, int gys, bf16* __restrict__ gx, int gxs, int C, int B,
                                    PadVol gf, PadVol gc)
 {
-    const long long n = (long long)B * gc.D * gc.H * gc.W * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        const long long v = e / C;
-        const int xo = (int)(v % gc.W), yo = (int)((v / gc.W) % gc.H), zo = (int)((v / ((long long)gc.W * gc.H)) % gc.D);
-        const long long b = v / ((long long)gc.W * gc.H * gc.D);
-        float s = 0.f;
+    const int G = C / 8;
+    for (int bz = blockIdx.y; bz < B * gc.D; bz += gridDim.y) {
+        int b, zo, yo, xo, c8;
+        if (!vox8(gc, G, bz, b, zo, yo, xo, c8)) return;
+        float s[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] = 0.f;
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const long long iv = b * gf.Vp + pad_row(gf, 2 * zo + (q >> 2), 2 * yo + ((q >> 1) & 1), 2 * xo + (q & 1));
-            s += __bfloat162float(gy[iv * gys + c]);
+            const long long iv = (long long)b * gf.Vp + pad_row(gf, 2 * zo + (q >> 2), 2 * yo + ((q >> 1) & 1),
+                                                                 2 * xo + (q & 1));
+            float f[8];
+            bf8_to_f(*reinterpret_cast<const uint4*>(gy + iv * gys + c8), f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += f[j];
         }
-        gx[(b * gc.Vp + pad_row(gc, zo, yo, xo)) * gxs + c] = __float2bfloat16(s);
+        *reinterpret_cast<uint4*>(gx + ((long long)b * gc.Vp + pad_row(gc, zo, yo, xo)) * gxs + c8) = f_to_bf8(s);
     }
 }
 
@@ -1015,37 +1068,55 @@ cudaError_t bias_grad(const void* gz, int stride, long long nvox, int cout, floa
     return cudaGetLastError();
 }
 
+namespace {
+// grid of the 8-channel resampling kernels on a grid g: x over the (y, x,
+// channel group) threads of a plane, y over (batch, plane) pairs
+dim3 vox8_grid(const PadVol& g, int C, int B)
+{
+    const int per_plane = g.H * g.W * (C / 8);
+    return dim3((unsigned)((per_plane + 255) / 256), (unsigned)std::min(B * g.D, 65535));
+}
+bool vox8_ok(const void* a, int as, const void* b, int bs, int C)
+{
+    return C % 8 == 0 && as % 8 == 0 && bs % 8 == 0 && !((uintptr_t)a & 15) && !((uintptr_t)b & 15);
+}
+}  // namespace
+
 cudaError_t pool2(const void* x, int xs, void* y, int ys, int C, int B, int D, int H, int W, cudaStream_t s)
 {
+    if (!vox8_ok(x, xs, y, ys, C)) return cudaErrorInvalidValue;
     const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
-    pool2_kernel<<<ew_grid((long long)B * gc.D * gc.H * gc.W * C), 256, 0, s>>>(
-        static_cast<const bf16*>(x), xs, static_cast<bf16*>(y), ys, C, B, gf, gc);
+    pool2_kernel<<<vox8_grid(gc, C, B), 256, 0, s>>>(static_cast<const bf16*>(x), xs, static_cast<bf16*>(y), ys, C, B,
+                                                      gf, gc);
     return cudaGetLastError();
 }
 
 cudaError_t pool2_adjoint(const void* gy, int gys, const void* x, int xs, void* gx, int gxs, int C, float slope, int B,
                           int D, int H, int W, cudaStream_t s)
 {
+    if (!vox8_ok(gy, gys, x, xs, C) || !vox8_ok(gx, gxs, gx, gxs, C)) return cudaErrorInvalidValue;
     const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
-    pool2_adjoint_kernel<<<ew_grid((long long)B * D * H * W * C), 256, 0, s>>>(
-        static_cast<const bf16*>(gy), gys, static_cast<const bf16*>(x), xs, static_cast<bf16*>(gx), gxs, C, slope, B,
-        gf, gc);
+    pool2_adjoint_kernel<<<vox8_grid(gf, C, B), 256, 0, s>>>(static_cast<const bf16*>(gy), gys,
+                                                              static_cast<const bf16*>(x), xs, static_cast<bf16*>(gx),
+                                                              gxs, C, slope, B, gf, gc);
     return cudaGetLastError();
 }
 
 cudaError_t up2(const void* x, int xs, void* y, int ys, int C, int B, int D, int H, int W, cudaStream_t s)
 {
+    if (!vox8_ok(x, xs, y, ys, C)) return cudaErrorInvalidValue;
     const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
-    up2_kernel<<<ew_grid((long long)B * D * H * W * C), 256, 0, s>>>(static_cast<const bf16*>(x), xs,
-                                                                      static_cast<bf16*>(y), ys, C, B, gf, gc);
+    up2_kernel<<<vox8_grid(gf, C, B), 256, 0, s>>>(static_cast<const bf16*>(x), xs, static_cast<bf16*>(y), ys, C, B, gf,
+                                                    gc);
     return cudaGetLastError();
 }
 
 cudaError_t up2_adjoint(const void* gy, int gys, void* gx, int gxs, int C, int B, int D, int H, int W, cudaStream_t s)
 {
+    if (!vox8_ok(gy, gys, gx, gxs, C)) return cudaErrorInvalidValue;
     const PadVol gf = make_pad(D, H, W), gc = make_pad(D / 2, H / 2, W / 2);
-    up2_adjoint_kernel<<<ew_grid((long long)B * gc.D * gc.H * gc.W * C), 256, 0, s>>>(
-        static_cast<const bf16*>(gy), gys, static_cast<bf16*>(gx), gxs, C, B, gf, gc);
+    up2_adjoint_kernel<<<vox8_grid(gc, C, B), 256, 0, s>>>(static_cast<const bf16*>(gy), gys, static_cast<bf16*>(gx),
+                                                            gxs, C, B, gf, gc);
     return cudaGetLastError();
 }
 
