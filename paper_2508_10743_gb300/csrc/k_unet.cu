@@ -635,14 +635,18 @@ bias_grad_kernel(const bf16* __restrict__ gz, int stride, long long nvox, int G,
     }
 }
 
+// one warp per channel: lane j adds rows j, j + 32, ..., then a fixed
+// shuffle tree (deterministic)
 __global__ void bias_grad_reduce_kernel(const float* __restrict__ partial, int nblk, int C, int cout,
                                         float* __restrict__ db)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (c >= cout) return;
     float s = 0.f;
-    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * C + c];
-    db[c] = s;
+    for (int b = lane; b < nblk; b += 32) s += partial[(size_t)b * C + c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) db[c] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -799,14 +803,16 @@ __global__ void velocity_loss_kernel(const float* __restrict__ pred, const float
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
         const long long b = v / V, l = v - b * V;
         const int xx = (int)(l % g.W), yy = (int)((l / g.W) % g.H), zz = (int)(l / ((long long)g.W * g.H));
-        bf16* o = gout + (b * g.Vp + pad_row(g, zz, yy, xx)) * gs;
+        uint4* o = reinterpret_cast<uint4*>(gout + (b * g.Vp + pad_row(g, zz, yy, xx)) * gs);
+        float gv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int c = 0; c < 3; ++c) {
             const size_t e = ((size_t)b * 3 + c) * V + l;
             const float d = pred[e] - target[e];
             acc += d * d * inv;
-            o[c] = __float2bfloat16(2.f * d * inv);
+            gv[c] = 2.f * d * inv;
         }
-        for (int c = 3; c < gs; ++c) o[c] = __float2bfloat16(0.f);
+        o[0] = f_to_bf8(gv);
+        for (int c = 8; c < gs; c += 8) o[c / 8] = make_uint4(0u, 0u, 0u, 0u);
     }
     const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -1064,7 +1070,7 @@ cudaError_t bias_grad(const void* gz, int stride, long long nvox, int cout, floa
     bias_grad_kernel<<<BG_BLOCKS, 256, 0, s>>>(static_cast<const bf16*>(gz), stride, nvox, G, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bias_grad_reduce_kernel<<<(cout + 127) / 128, 128, 0, s>>>(work, BG_BLOCKS, 8 * G, cout, db);
+    bias_grad_reduce_kernel<<<(cout + 3) / 4, 128, 0, s>>>(work, BG_BLOCKS, 8 * G, cout, db);
     return cudaGetLastError();
 }
 
@@ -1132,6 +1138,7 @@ int velocity_loss_blocks(long long n) { return ew_grid(n); }
 cudaError_t velocity_loss(const float* pred, const float* target, int B, int D, int H, int W, void* g, int gs,
                           double* partials, cudaStream_t s)
 {
+    if (gs % 8 || ((uintptr_t)g & 15)) return cudaErrorInvalidValue;
     const long long n = (long long)B * D * H * W;
     velocity_loss_kernel<<<ew_grid(n), 256, 0, s>>>(pred, target, B, make_pad(D, H, W), static_cast<bf16*>(g), gs,
                                                     partials, (float)(1.0 / (3.0 * (double)n)));
