@@ -15,7 +15,9 @@
 #include "kernels.h"
 #include "umma.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 
@@ -122,12 +124,16 @@ gemm_bf16_kernel(const bf16* __restrict__ A, const bf16* __restrict__ B, float* 
 //   out[q][co] = act( bias[co] + sum_{tap, ci} in[q + off(tap)][ci] W[co][tap][ci] )
 // A CTA owns 128 consecutive padded rows q (TMEM lanes) x np output channels
 // (TMEM columns).  Stage (c, dz), c = 16-channel chunk: the dz window of the
-// chunk (2 x R rows of 16 bytes) and the chunk's nine (dy, dx) weight tiles
-// are copied with cp.async; one elected thread issues nine M128 x N x K16
-// MMAs whose A descriptors start (dy (W+2) + dx) rows into the window.  ns
-// stages rotate; a stage's slot is refilled once the commit of the MMAs
-// that read it has arrived on the slot's mbarrier (bounded waits; a timeout
-// poisons the output with NaN instead of hanging).
+// chunk and the chunk's nine (dy, dx) weight tiles.  One thread runs the
+// whole main loop: it copies a stage with TMA (the window as 2 channel
+// groups x `parts` boxes of 8 channels x BR rows of a 2-D tensor map over
+// the padded rows, zero-filled outside the batch; the weight tiles with one
+// bulk copy), waits for the stage's bytes on the slot's `full` barrier,
+// issues nine M128 x N x K16 MMAs whose A descriptors start (dy (W+2) + dx)
+// rows into the window, and commits them to the slot's `empty` barrier,
+// which gates the slot's refill.  The other threads wait at a block barrier
+// and then for the last commit, and run the epilogue.  Waits are bounded: a
+// timeout poisons the output with NaN instead of hanging.
 // pipeline slots of the window convolution: 2 = two (more resident blocks:
 // a block runs only 3 x cin/16 stages, and the blocks of an SM hide each
 // other's latencies better than a deeper pipeline does), 0 = three where
@@ -151,72 +157,62 @@ struct WinArgs {
     int B;
     PadVol g;
     int np, R, ns, slot_bytes;
+    int parts, br;                // R = parts x br window rows per channel group (br <= 256, a multiple of 8)
     long long tiles_per_batch;
 };
 
 __global__ void __launch_bounds__(128)
-conv3_win_kernel(WinArgs a)
+conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ uint64_t mbar[3];
+    __shared__ uint64_t full[3], empty[3];
     __shared__ uint32_t tslot;
+    __shared__ int bad;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const PadVol g = a.g;
     const int b = (int)(blockIdx.x / a.tiles_per_batch);
     const long long q0 = g.P + (long long)(blockIdx.x % a.tiles_per_batch) * TC_M;
     const long long base_b = (long long)b * g.Vp;
-    const long long rows_total = (long long)a.B * g.Vp;
     uint32_t ncols = 32;
     while ((int)ncols < a.np) ncols <<= 1;
     if (warp == 0) umma::tmem_alloc(&tslot, ncols);
     if (tid == 0) {
-        for (int k = 0; k < a.ns; ++k) umma::mbar_init(&mbar[k], 1);
+        for (int k = 0; k < a.ns; ++k) {
+            umma::mbar_init(&full[k], 1);
+            umma::mbar_init(&empty[k], 1);
+        }
+        bad = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = tslot;
-    const uint32_t idesc = umma::idesc_bf16_f32(TC_M, a.np);
-    const uint32_t lboA = (uint32_t)a.R * 16u, lboB = (uint32_t)a.np * 16u;
     const int nst = 3 * a.nchunk;
 
-    auto load = [&](int st, int slot) {
-        const int c = st / 3, dz = st - 3 * c;
-        uint8_t* As = smem + (size_t)slot * a.slot_bytes;
-        uint8_t* Bs = As + 2 * lboA;
-        const long long r0 = base_b + q0 + (long long)(dz - 1) * g.P - g.Wp - 1;
-        for (int e = tid; e < 2 * a.R; e += 128) {
-            const int r = e >> 1, grp = e & 1;
-            const long long qg = r0 + r;
-            const bool in_buf = qg >= 0 && qg < rows_total;
-            const bf16* src = in_buf ? a.in + qg * a.in_stride + 16 * c + 8 * grp : a.in;
-            cp_async16(As + grp * lboA + r * 16, src, in_buf ? 16 : 0);
-        }
-        const bf16* w = a.wt + (size_t)(c * 3 + dz) * 18 * a.np * 8;
-        for (int e = tid; e < 18 * a.np; e += 128) cp_async16(Bs + (size_t)e * 16, w + (size_t)e * 8, 16);
-    };
-
-    for (int p = 0; p < a.ns - 1; ++p) {
-        if (p < nst) load(p, p);
-        cp_async_commit();
-    }
-    bool ok = true;
-    for (int i = 0; i < nst; ++i) {
-        const int j = i + a.ns - 1;
-        if (j < nst) {
-            const int sj = j % a.ns;
-            if (j >= a.ns) ok = umma::mbar_wait(&mbar[sj], (uint32_t)(((j - a.ns) / a.ns) & 1), TC_WAIT) && ok;
-            load(j, sj);
-        }
-        cp_async_commit();
-        if (a.ns == 3) cp_async_wait<2>();
-        else cp_async_wait<1>();
-        umma::fence_smem_async();
-        __syncthreads();
-        if (tid == 0) {
+    if (tid == 0) {
+        const uint32_t idesc = umma::idesc_bf16_f32(TC_M, a.np);
+        const uint32_t lboA = (uint32_t)a.R * 16u, lboB = (uint32_t)a.np * 16u;
+        const uint32_t wbytes = 288u * (uint32_t)a.np, tx = 32u * (uint32_t)a.R + wbytes;
+        auto issue = [&](int st, int slot) {
+            const int c = st / 3, dz = st - 3 * c;
+            uint8_t* As = smem + (size_t)slot * a.slot_bytes;
+            // first window row; negative or past the last batch at the ends (zero fill)
+            const int r0 = (int)(base_b + q0 + (long long)(dz - 1) * g.P - g.Wp - 1);
+            umma::mbar_arrive_expect_tx(&full[slot], tx);
+            for (int grp = 0; grp < 2; ++grp)
+                for (int p = 0; p < a.parts; ++p)
+                    umma::tma_load_2d(As + grp * lboA + (uint32_t)p * a.br * 16u, &tmap, 16 * c + 8 * grp,
+                                      r0 + p * a.br, &full[slot]);
+            umma::bulk_load(As + 2 * lboA, a.wt + (size_t)(c * 3 + dz) * 18 * a.np * 8, wbytes, &full[slot]);
+        };
+        bool ok = true;
+        for (int p = 0; p < a.ns && p < nst; ++p) issue(p, p);
+        for (int i = 0; i < nst; ++i) {
+            const int slot = i % a.ns;
+            ok = umma::mbar_wait(&full[slot], (uint32_t)((i / a.ns) & 1), TC_WAIT) && ok;
             umma::fence_after_sync();
-            const uint32_t As = umma::smem_u32(smem + (size_t)(i % a.ns) * a.slot_bytes);
+            const uint32_t As = umma::smem_u32(smem + (size_t)slot * a.slot_bytes);
             const uint32_t Bs = As + 2 * lboA;
             for (int t9 = 0; t9 < 9; ++t9) {
                 const int dy = t9 / 3, dx = t9 - 3 * dy;
@@ -224,10 +220,19 @@ conv3_win_kernel(WinArgs a)
                 const uint64_t db = umma::smem_desc(Bs + (uint32_t)t9 * 2u * lboB, lboB, 128);
                 umma::mma_bf16(tmem, da, db, idesc, (i > 0) || (t9 > 0));
             }
-            umma::commit(&mbar[i % a.ns]);
+            umma::commit(&empty[slot]);
+            // refill the previous stage's slot once its MMAs (queued before these) retire
+            const int k = i - 1;
+            if (k >= 0 && k + a.ns < nst) {
+                const int sk = k % a.ns;
+                ok = umma::mbar_wait(&empty[sk], (uint32_t)((k / a.ns) & 1), TC_WAIT) && ok;
+                issue(k + a.ns, sk);
+            }
         }
+        if (!ok) bad = 1;
     }
-    ok = umma::mbar_wait(&mbar[(nst - 1) % a.ns], (uint32_t)(((nst - 1) / a.ns) & 1), TC_WAIT) && ok;
+    __syncthreads();
+    const bool ok = umma::mbar_wait(&empty[(nst - 1) % a.ns], (uint32_t)(((nst - 1) / a.ns) & 1), TC_WAIT) && !bad;
     umma::fence_after_sync();
 
     // epilogue: warp w holds rows q0 + 32 w + lane
@@ -893,9 +898,39 @@ PadVol make_pad(int D, int H, int W)
     return g;
 }
 
-int conv_window_rows(int W) { return TC_M + 2 * (W + 2) + 2; }
+// window rows a stage needs, split into parts of br <= 256 rows (a TMA box
+// dimension), br a multiple of 8 (128-byte aligned boxes)
+static void conv_window_split(int W, int& parts, int& br)
+{
+    const int need = TC_M + 2 * (W + 2) + 2;
+    parts = (need + 255) / 256;
+    br = ((need + parts - 1) / parts + 7) / 8 * 8;
+}
+
+int conv_window_rows(int W)
+{
+    int parts, br;
+    conv_window_split(W, parts, br);
+    return parts * br;
+}
 
 int conv_slot_bytes(int W, int np) { return (32 * conv_window_rows(W) + 288 * np + 127) / 128 * 128; }
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+}  // namespace
 
 bool conv_fits(int W, int np) { return 2 * conv_slot_bytes(W, np) <= CONV_SMEM_MAX; }
 
@@ -919,7 +954,8 @@ cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s)
     a.B = d.batch;
     a.g = make_pad(d.D, d.H, d.W);
     a.np = d.np;
-    a.R = conv_window_rows(d.W);
+    conv_window_split(d.W, a.parts, a.br);
+    a.R = a.parts * a.br;
     a.slot_bytes = conv_slot_bytes(d.W, d.np);
     a.ns = (DARC_CONV_NS == 2 || 3 * a.slot_bytes > 200 * 1024) ? 2 : 3;
     a.tiles_per_batch = ((long long)d.D * a.g.P + TC_M - 1) / TC_M;
@@ -931,8 +967,23 @@ cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s)
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    // the input as rows x channels [0, cin): boxes of 8 channels x br rows
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    // TMA row coordinates are 32-bit
+    if ((long long)d.batch * a.g.Vp + 2 * a.g.P >= (1LL << 31)) return cudaErrorInvalidValue;
+    if (!encode || d.in_stride % 8 || (reinterpret_cast<uintptr_t>(d.in) & 15) ||
+        (reinterpret_cast<uintptr_t>(d.wt) & 15))
+        return cudaErrorInvalidValue;
+    CUtensorMap tmap;
+    const cuuint64_t gdim[2] = {(cuuint64_t)d.cin, (cuuint64_t)((long long)d.batch * a.g.Vp)};
+    const cuuint64_t gstride[1] = {(cuuint64_t)d.in_stride * sizeof(bf16)};
+    const cuuint32_t box[2] = {8u, (cuuint32_t)a.br}, estride[2] = {1u, 1u};
+    if (encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(d.in), gdim, gstride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
     const long long blocks = (long long)d.batch * a.tiles_per_batch;
-    conv3_win_kernel<<<(unsigned)blocks, 128, (size_t)a.ns * a.slot_bytes, s>>>(a);
+    conv3_win_kernel<<<(unsigned)blocks, 128, (size_t)a.ns * a.slot_bytes, s>>>(tmap, a);
     return cudaGetLastError();
 }
 

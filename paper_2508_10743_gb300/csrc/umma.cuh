@@ -115,6 +115,33 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
     return false;
 }
 
+// Arrive on the barrier (count 1) and add `bytes` to the transaction count
+// the current phase waits for (the TMA copies below complete it).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: the box of a 2-D tensor map at (c0 innermost, c1) into shared memory
+// (128-byte aligned destination); the bytes complete on `mbar`.  Elements
+// outside the tensor read as zero (c1 may be negative; c0 x element size must
+// be a multiple of 16 bytes).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int c0, int c1, uint64_t* mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(smem_u32(mbar))
+        : "memory");
+}
+
+// Plain bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+
 // 32 lanes x 8 consecutive fp32 columns of TMEM into 8 registers per thread
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8])
 {
