@@ -228,8 +228,9 @@ int darc_atlas_set_sum(darc_cohort* c, const double* acc_dev, long long n_total)
  * rank's subjects is its own shuffle, seeded with cfg.seed + rank_seed);
  * apply takes one Adam step with the all-reduced sum divided by the global
  * batch size; end refreshes the atlas window statistics.  A mini-batch of
- * at most four subjects takes the single-GPU update's two fused box passes
- * (the second writes g_dev instead of stepping the atlas).  All four calls
+ * at most 16 subjects takes the single-GPU update's fused box passes (per
+ * sub-batch of up to four subjects one forward and one adjoint pass; the
+ * last writes g_dev instead of stepping the atlas).  All four calls
  * only enqueue work on the cohort's stream: a driver keeps the losses on the
  * device and synchronises once per atlas update.
  * Returns DARC_ERR_ARG for an epoch/batch outside the schedule. */

@@ -580,8 +580,10 @@ int update_atlas_impl(darc_cohort* c)
     // algorithmic bytes: centrality 24n + 12 per voxel; warped cohort (24T + 20) n;
     // L1 median: the cached cohort read once, the atlas written; patch-wise:
     // the cohort's window statistics 12n, then per mini-batch of nb subjects
-    // either the fused pair (Adam state 24, the two shared coefficients written
-    // and read 16, per subject 24: J twice, its statistics, its coefficient
+    // either the fused passes (Adam state 24, the two shared coefficients
+    // written and read 16, per subject 24: J twice, its statistics, its
+    // coefficient written and read; per sub-batch after the first 28: A read,
+    // the shared coefficients read and written again, the running gradient
     // written and read) or the unfused chain (statistics 12, Adam 24, per
     // subject 28 + 20)
     double bytes = (24.0 * n + 12.0) + (24.0 * T + 20.0) * n;
@@ -589,14 +591,16 @@ int update_atlas_impl(darc_cohort* c)
     const long long chunks = (n + c->bmax - 1) / c->bmax;
     long long launches = 2 + chunks * (T + 1) + 1;
     if (patchwise(c->cfg.dissim)) {
-        // per mini-batch: fused 2 + 1 + 2 kernels, unfused 2 + 2 + 1 + 4 + 1
+        // per mini-batch: fused 2 per sub-batch + 1 + 2 per sub-batch kernels,
+        // unfused 2 + 2 + 1 + 4 + 1
         bytes += 12.0 * n;
         launches += 2 * chunks + 1;
         for (int b0 = 0; b0 < n; b0 += c->cfg.atlas_batch) {
             const int nb = std::min(c->cfg.atlas_batch, n - b0);
             const bool fused = nb <= ATLAS_FUSED_MAX;
-            bytes += K3 * (fused ? 40.0 + 24.0 * nb : 36.0 + 48.0 * nb);
-            launches += (long long)K3 * (fused ? 5 : 10);
+            const int K = atlas_sub_batches(nb);
+            bytes += K3 * (fused ? 40.0 + 24.0 * nb + 28.0 * (K - 1) : 36.0 + 48.0 * nb);
+            launches += (long long)K3 * (fused ? 4 * K + 1 : 10);
         }
     }
     Prof p(c, c->st, DARC_K_ATLAS, bytes * (double)vol.V);
@@ -653,8 +657,9 @@ int update_atlas_body(darc_cohort* c)
             for (int b0 = 0; b0 < n; b0 += B) {
                 const int nb = std::min(B, n - b0);
                 if (nb <= ATLAS_FUSED_MAX) {
-                    // two box passes: the batch's metrics with Box(A), Box(A^2); the
-                    // adjoint with the Adam step (subject rows from the host's order)
+                    // per sub-batch two box passes: the metrics with Box(A), Box(A^2);
+                    // the adjoint, the last with the Adam step (subject rows from the
+                    // host's order)
                     const int* sh = c->perm_host + (size_t)ep * n + b0;
                     const float* Jr[ATLAS_FUSED_MAX];
                     const float* jr[ATLAS_FUSED_MAX];
@@ -671,7 +676,7 @@ int update_atlas_body(darc_cohort* c)
                     CK(atlas_sgd_fused_adam(Jr, nb, c->coef, r, c->A, c->Am, c->As,
                                             (float)(-1.0 / ((double)vol.V * nb)), (float)(c->cfg.lr / c1),
                                             (float)(1.0 / std::sqrt(c2)), c->cfg.beta1, c->cfg.beta2,
-                                            c->cfg.adam_eps, vol, c->boxbuf, s));
+                                            c->cfg.adam_eps, c->gsh, vol, c->boxbuf, s));
                     continue;
                 }
                 const int* subj = c->perm_dev + (size_t)ep * n + b0;
@@ -1373,8 +1378,9 @@ int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, floa
     const int* subj = c->perm_dev + (size_t)epoch * c->n + b0;
     cudaStream_t s = c->st;
     if (nb <= ATLAS_FUSED_MAX) {
-        // the single-GPU step's two box passes (the batch's metrics with Box(A),
-        // Box(A^2); the adjoint), the second writing g instead of stepping A
+        // the single-GPU step's box passes (per sub-batch the metrics with
+        // Box(A), Box(A^2) and the adjoint), the last writing g instead of
+        // stepping A
         const int* sh = c->perm_host + (size_t)epoch * c->n + b0;
         const float* Jr[ATLAS_FUSED_MAX];
         const float* jr[ATLAS_FUSED_MAX];
@@ -1385,8 +1391,9 @@ int darc_atlas_sgd_grad(darc_cohort* c, int epoch, int batch, float* g_dev, floa
         CK(atlas_sgd_fused_forward(Jr, jr, nb, c->A, r, c->cfg.ncc_eps, patch_metric(c->cfg.dissim), c->coef, c->pL,
                                    vol, c->boxbuf, s));
         CK(reduce_partials(c->pL, nb * box_blocks(vol, 1), 1, 1.0, loss_dev, 1, 1, s));
-        CK(atlas_sgd_fused_grad(Jr, nb, c->coef, r, c->A, (float)(-1.0 / (double)vol.V), g_dev, vol, c->boxbuf, s));
-        c->launches += 5;
+        CK(atlas_sgd_fused_grad(Jr, nb, c->coef, r, c->A, (float)(-1.0 / (double)vol.V), g_dev, c->gsh, vol,
+                                c->boxbuf, s));
+        c->launches += 4 * atlas_sub_batches(nb) + 1;
         return end(c);
     }
     CK(atlas_stats(c->A, c->astats, r, vol, c->boxbuf, s));

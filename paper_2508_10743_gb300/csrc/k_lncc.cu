@@ -511,12 +511,13 @@ struct AtlasBwdSubjOp {
     __device__ void partial(int, int, double) const {}
 };
 
-// Atlas SGD, one box pass per mini-batch of NB subjects (rows known on the
-// host): channels Box(A), Box(A^2) and Box(J_b A) for each b.  The epilogue
-// evaluates the NB patch metrics and keeps what the adjoint needs.  Because
-// Box is linear, the two coefficients that multiply terms shared by the
-// batch are summed over b here: coef [2 + NB][V] = {sum_b dm_b/dS_A,
-// sum_b dm_b/dS_AA, dm_b/dS_JA for each b}; loss partials [NB][nblk].
+// Atlas SGD, one box pass per sub-batch of NB <= 4 subjects of a mini-batch
+// (rows known on the host): channels Box(A), Box(A^2) and Box(J_b A) for
+// each b.  The epilogue evaluates the NB patch metrics and keeps what the
+// adjoint needs.  Because Box is linear, the two coefficients that multiply
+// terms shared by the batch are summed over b here (and over the earlier
+// sub-batches when `accum`): coef [2][V] = {sum_b dm_b/dS_A, sum_b
+// dm_b/dS_AA}, coefb [NB][V] = dm_b/dS_JA; loss partials [NB][nblk].
 template <int NB>
 struct AtlasFwdFusedOp {
     static constexpr bool kReduces = true;
@@ -525,6 +526,8 @@ struct AtlasFwdFusedOp {
     const float* js[NB];   // its window statistics [2][V]
     const float* A;
     float* coef;
+    float* coefb;
+    int accum;
     double* partials;
     int nblk;
     long long V;
@@ -547,8 +550,12 @@ struct AtlasFwdFusedOp {
                                           invN, eps, true);
             s0 += t.c0;
             s1 += t.c1;
-            coef[(size_t)(2 + b) * V + l] = t.c2;
+            coefb[(size_t)b * V + l] = t.c2;
             acc[b] += t.cc * negInvV;
+        }
+        if (accum) {
+            s0 = coef[l] + s0;
+            s1 = coef[V + l] + s1;
         }
         coef[l] = s0;
         coef[V + l] = s1;
@@ -556,65 +563,52 @@ struct AtlasFwdFusedOp {
     __device__ void partial(int b, int blk, double s) const { partials[(size_t)b * nblk + blk] = s; }
 };
 
-// Atlas SGD, the adjoint of a mini-batch in one box pass with the Adam step
-// in its epilogue: g = scale [Box(sum a) + 2 A Box(sum b) + sum_b J_b Box(g_b)],
-// then A, m, s updated in place.  A is read and written only at the
-// thread's own voxel (the XY pass reads the coefficients alone).
-template <int NB>
-struct AtlasBwdAdamOp {
+// Atlas SGD, the adjoint of a mini-batch, one box pass per sub-batch:
+//   g = Box(sum a) + 2 A Box(sum b) + sum_b J_b Box(g_b)
+// SHARED (the first sub-batch) adds the terms shared by the batch, later
+// sub-batches add to the running sum `gin`.  The last pass either takes the
+// Adam step with g * scale (m != null: A, m, s updated in place, each read
+// and written only at the thread's own voxel) or writes g * gscale to gout
+// (a sharded cohort sums g over its ranks before the step); earlier passes
+// write the running sum to gout.  The XY pass reads the coefficients alone.
+template <int NB, bool SHARED>
+struct AtlasBwdStepOp {
     static constexpr bool kReduces = false;
     const float* J[NB];
-    const float* coef;     // [2 + NB][V] from AtlasFwdFusedOp
+    const float* coef;     // [2][V] shared coefficients (SHARED)
+    const float* coefb;    // [NB][V] this sub-batch's
     float* A;
     float* m;
     float* s;
+    const float* gin;
+    float* gout;
     long long V;
-    float scale, lr_c1, isc2, b1, b2, eps;
+    float gscale, scale, lr_c1, isc2, b1, b2, eps;
     __device__ void load(int, long long l, float* o) const
     {
+        if (SHARED) {
+            o[0] = __ldg(coef + l);
+            o[1] = __ldg(coef + V + l);
+        }
 #pragma unroll
-        for (int c = 0; c < 2 + NB; ++c) o[c] = __ldg(coef + (size_t)c * V + l);
+        for (int b = 0; b < NB; ++b) o[(SHARED ? 2 : 0) + b] = __ldg(coefb + (size_t)b * V + l);
     }
     __device__ float emit(int, int, int, int, long long l, const float* S) const
     {
         float a = A[l];
-        float g = S[0] + 2.f * a * S[1];
+        float g = SHARED ? S[0] + 2.f * a * S[1] : gin[l];
         // each subject's term rounded on its own, as a separate product
 #pragma unroll
-        for (int b = 0; b < NB; ++b) g += __fmul_rn(__ldg(J[b] + l), S[2 + b]);
-        float mm = m[l], ss = s[l];
-        adam1(a, mm, ss, g * scale, b1, b2, lr_c1, isc2, eps);
-        A[l] = a;
-        m[l] = mm;
-        s[l] = ss;
-        return 0.f;
-    }
-    __device__ void partial(int, int, double) const {}
-};
-
-// The same adjoint pass without the Adam step, for a cohort sharded across
-// GPUs (the gradient is summed over the ranks before the step):
-// g = scale [Box(sum a) + 2 A Box(sum b) + sum_b J_b Box(g_b)] written out.
-template <int NB>
-struct AtlasBwdGradOp {
-    static constexpr bool kReduces = false;
-    const float* J[NB];
-    const float* coef;     // [2 + NB][V] from AtlasFwdFusedOp
-    const float* A;
-    float* g;
-    long long V;
-    float scale;
-    __device__ void load(int, long long l, float* o) const
-    {
-#pragma unroll
-        for (int c = 0; c < 2 + NB; ++c) o[c] = __ldg(coef + (size_t)c * V + l);
-    }
-    __device__ float emit(int, int, int, int, long long l, const float* S) const
-    {
-        float t = S[0] + 2.f * __ldg(A + l) * S[1];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) t += __fmul_rn(__ldg(J[b] + l), S[2 + b]);
-        g[l] = t * scale;
+        for (int b = 0; b < NB; ++b) g += __fmul_rn(__ldg(J[b] + l), S[(SHARED ? 2 : 0) + b]);
+        if (m) {
+            float mm = m[l], ss = s[l];
+            adam1(a, mm, ss, g * scale, b1, b2, lr_c1, isc2, eps);
+            A[l] = a;
+            m[l] = mm;
+            s[l] = ss;
+        } else {
+            gout[l] = g * gscale;
+        }
         return 0.f;
     }
     __device__ void partial(int, int, double) const {}
@@ -721,10 +715,11 @@ cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, 
     return launch_box<1>(each, nb, v, r, P, s);
 }
 
+namespace {
 template <int NB>
 cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* jsrows, const float* A, int r,
-                               float eps, int metric, float* coef, double* partials, const Vol& v, float* P,
-                               cudaStream_t s)
+                               float eps, int metric, float* coef, float* coefb, int accum, double* partials,
+                               const Vol& v, float* P, cudaStream_t s)
 {
     const int w = 2 * r + 1;
     AtlasFwdFusedOp<NB> op{};
@@ -734,6 +729,8 @@ cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* js
     }
     op.A = A;
     op.coef = coef;
+    op.coefb = coefb;
+    op.accum = accum;
     op.partials = partials;
     op.nblk = box_blocks(v, 1);
     op.V = v.V;
@@ -744,77 +741,119 @@ cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* js
     return launch_box<2 + NB>(op, 1, v, r, P, s);
 }
 
-template <int NB>
-cudaError_t atlas_fused_adam_nb(const float* const* Jrows, const float* coef, int r, float* A, float* m, float* s_,
-                                float scale, float lr_c1, float isc2, float b1, float b2, float eps, const Vol& v,
-                                float* P, cudaStream_t s)
+template <int NB, bool SHARED>
+cudaError_t atlas_step_nb(const float* const* Jrows, const float* coef, const float* coefb, int r,
+                          const AtlasStepArgs& q, const float* gin, float* gout, float gscale, bool adam,
+                          const Vol& v, float* P, cudaStream_t s)
 {
-    AtlasBwdAdamOp<NB> op{};
+    AtlasBwdStepOp<NB, SHARED> op{};
     for (int b = 0; b < NB; ++b) op.J[b] = Jrows[b];
     op.coef = coef;
-    op.A = A;
-    op.m = m;
-    op.s = s_;
+    op.coefb = coefb;
+    op.A = q.A;
+    op.m = adam ? q.m : nullptr;
+    op.s = q.s;
+    op.gin = gin;
+    op.gout = gout;
     op.V = v.V;
-    op.scale = scale;
-    op.lr_c1 = lr_c1;
-    op.isc2 = isc2;
-    op.b1 = b1;
-    op.b2 = b2;
-    op.eps = eps;
-    return launch_box<2 + NB>(op, 1, v, r, P, s);
+    op.gscale = gscale;
+    op.scale = q.scale;
+    op.lr_c1 = q.lr_c1;
+    op.isc2 = q.isc2;
+    op.b1 = q.b1;
+    op.b2 = q.b2;
+    op.eps = q.eps;
+    return launch_box<(SHARED ? 2 : 0) + NB>(op, 1, v, r, P, s);
 }
 
-template <int NB>
-cudaError_t atlas_fused_grad_nb(const float* const* Jrows, const float* coef, int r, const float* A, float scale,
-                                float* g, const Vol& v, float* P, cudaStream_t s)
-{
-    AtlasBwdGradOp<NB> op{};
-    for (int b = 0; b < NB; ++b) op.J[b] = Jrows[b];
-    op.coef = coef;
-    op.A = A;
-    op.g = g;
-    op.V = v.V;
-    op.scale = scale;
-    return launch_box<2 + NB>(op, 1, v, r, P, s);
-}
-
-cudaError_t atlas_sgd_fused_grad(const float* const* Jrows, int nb, const float* coef, int r, const float* A,
-                                 float scale, float* g, const Vol& v, float* P, cudaStream_t s)
+template <bool SHARED>
+cudaError_t atlas_step_pass(const float* const* Jrows, int nb, const float* coef, const float* coefb, int r,
+                            const AtlasStepArgs& q, const float* gin, float* gout, float gscale, bool adam,
+                            const Vol& v, float* P, cudaStream_t s)
 {
     switch (nb) {
-    case 1: return atlas_fused_grad_nb<1>(Jrows, coef, r, A, scale, g, v, P, s);
-    case 2: return atlas_fused_grad_nb<2>(Jrows, coef, r, A, scale, g, v, P, s);
-    case 3: return atlas_fused_grad_nb<3>(Jrows, coef, r, A, scale, g, v, P, s);
-    case 4: return atlas_fused_grad_nb<4>(Jrows, coef, r, A, scale, g, v, P, s);
+    case 1: return atlas_step_nb<1, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
+    case 2: return atlas_step_nb<2, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
+    case 3: return atlas_step_nb<3, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
+    case 4: return atlas_step_nb<4, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
     default: return cudaErrorInvalidValue;
     }
 }
+
+// sub-batch k of K over nb subjects: first subject and size (sizes differ by one at most)
+void atlas_sub_batch(int nb, int k, int& off, int& cnt)
+{
+    const int K = atlas_sub_batches(nb);
+    off = (int)((long long)nb * k / K);
+    cnt = (int)((long long)nb * (k + 1) / K) - off;
+}
+
+}  // namespace
+
+int atlas_sub_batches(int nb) { return (nb + ATLAS_SUB_MAX - 1) / ATLAS_SUB_MAX; }
 
 cudaError_t atlas_sgd_fused_forward(const float* const* Jrows, const float* const* jsrows, int nb, const float* A,
                                     int r, float eps, int metric, float* coef, double* partials, const Vol& v,
                                     float* P, cudaStream_t s)
 {
-    switch (nb) {
-    case 1: return atlas_fused_fwd_nb<1>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
-    case 2: return atlas_fused_fwd_nb<2>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
-    case 3: return atlas_fused_fwd_nb<3>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
-    case 4: return atlas_fused_fwd_nb<4>(Jrows, jsrows, A, r, eps, metric, coef, partials, v, P, s);
-    default: return cudaErrorInvalidValue;
+    if (nb < 1 || nb > ATLAS_FUSED_MAX) return cudaErrorInvalidValue;
+    const int K = atlas_sub_batches(nb), nblk = box_blocks(v, 1);
+    for (int k = 0; k < K; ++k) {
+        int off, cnt;
+        atlas_sub_batch(nb, k, off, cnt);
+        float* coefb = coef + (size_t)(2 + off) * v.V;
+        double* pk = partials + (size_t)off * nblk;
+        cudaError_t e;
+        switch (cnt) {
+        case 1: e = atlas_fused_fwd_nb<1>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
+        case 2: e = atlas_fused_fwd_nb<2>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
+        case 3: e = atlas_fused_fwd_nb<3>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
+        case 4: e = atlas_fused_fwd_nb<4>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
+        default: e = cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
+
+namespace {
+cudaError_t atlas_backward_passes(const float* const* Jrows, int nb, const float* coef, int r,
+                                  const AtlasStepArgs& q, float* gacc, float* gout, float gscale, bool adam,
+                                  const Vol& v, float* P, cudaStream_t s)
+{
+    if (nb < 1 || nb > ATLAS_FUSED_MAX) return cudaErrorInvalidValue;
+    const int K = atlas_sub_batches(nb);
+    if (K > 1 && !gacc) return cudaErrorInvalidValue;
+    for (int k = 0; k < K; ++k) {
+        int off, cnt;
+        atlas_sub_batch(nb, k, off, cnt);
+        const float* coefb = coef + (size_t)(2 + off) * v.V;
+        const bool last = k == K - 1;
+        float* go = last ? gout : gacc;
+        const float gs = last ? gscale : 1.f;
+        const cudaError_t e = k == 0 ? atlas_step_pass<true>(Jrows + off, cnt, coef, coefb, r, q, nullptr, go, gs,
+                                                             adam && last, v, P, s)
+                                     : atlas_step_pass<false>(Jrows + off, cnt, coef, coefb, r, q, gacc, go, gs,
+                                                              adam && last, v, P, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+}  // namespace
 
 cudaError_t atlas_sgd_fused_adam(const float* const* Jrows, int nb, const float* coef, int r, float* A, float* m,
                                  float* s_, float scale, float lr_c1, float isc2, float b1, float b2, float eps,
-                                 const Vol& v, float* P, cudaStream_t s)
+                                 float* gacc, const Vol& v, float* P, cudaStream_t s)
 {
-    switch (nb) {
-    case 1: return atlas_fused_adam_nb<1>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
-    case 2: return atlas_fused_adam_nb<2>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
-    case 3: return atlas_fused_adam_nb<3>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
-    case 4: return atlas_fused_adam_nb<4>(Jrows, coef, r, A, m, s_, scale, lr_c1, isc2, b1, b2, eps, v, P, s);
-    default: return cudaErrorInvalidValue;
-    }
+    const AtlasStepArgs q{A, m, s_, scale, lr_c1, isc2, b1, b2, eps};
+    return atlas_backward_passes(Jrows, nb, coef, r, q, gacc, nullptr, 1.f, true, v, P, s);
+}
+
+cudaError_t atlas_sgd_fused_grad(const float* const* Jrows, int nb, const float* coef, int r, const float* A,
+                                 float scale, float* g, float* gacc, const Vol& v, float* P, cudaStream_t s)
+{
+    const AtlasStepArgs q{const_cast<float*>(A), nullptr, nullptr, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    return atlas_backward_passes(Jrows, nb, coef, r, q, gacc, g, scale, false, v, P, s);
 }
 
 cudaError_t lncc_forward(const float* J, const int* subj, const float* A, const float* stats,

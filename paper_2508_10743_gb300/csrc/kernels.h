@@ -256,21 +256,33 @@ cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, 
                                int r, float* gshared, float* gsubj, int nb, const Vol& v, float* P,
                                cudaStream_t s);
 
-// The same mini-batch step in two box passes when nb <= ATLAS_FUSED_MAX and
-// the subjects' rows are known on the host: forward with coef [2 + nb][V]
+// The same mini-batch step in box passes when the subjects' rows are known
+// on the host (nb <= ATLAS_FUSED_MAX): sub-batches of at most ATLAS_SUB_MAX
+// subjects (atlas_sub_batches(nb) of them, sizes differing by one at most),
+// each one forward pass and one adjoint pass.  Forward: coef [2 + nb][V]
 // (sum_b dm/dS_A, sum_b dm/dS_AA, dm_b/dS_JA), loss partials [nb][nblk],
-// P >= (2 + nb) V floats; then the adjoint with the Adam step of A (scale
-// multiplies the gradient, as in atlas_adam).  A, m, s are updated in place.
-constexpr int ATLAS_FUSED_MAX = 4;
+// P >= (2 + ATLAS_SUB_MAX) V floats.  Adjoint: the sub-batches' gradients
+// add up in gacc [V] (unused for one sub-batch), the last pass takes the
+// Adam step of A (scale multiplies the gradient, as in atlas_adam; A, m, s
+// updated in place).
+constexpr int ATLAS_SUB_MAX = 4;
+constexpr int ATLAS_FUSED_MAX = 16;
+int atlas_sub_batches(int nb);
+struct AtlasStepArgs {
+    float* A;
+    float* m;
+    float* s;
+    float scale, lr_c1, isc2, b1, b2, eps;
+};
 cudaError_t atlas_sgd_fused_forward(const float* const* Jrows, const float* const* jsrows, int nb, const float* A,
                                     int r, float eps, int metric, float* coef, double* partials, const Vol& v,
                                     float* P, cudaStream_t s);
 cudaError_t atlas_sgd_fused_adam(const float* const* Jrows, int nb, const float* coef, int r, float* A, float* m,
                                  float* s_, float scale, float lr_c1, float isc2, float b1, float b2, float eps,
-                                 const Vol& v, float* P, cudaStream_t s);
-// the same adjoint pass writing g [V] = scale * the batch's summed gradient
+                                 float* gacc, const Vol& v, float* P, cudaStream_t s);
+// the same adjoint passes writing g [V] = scale * the batch's summed gradient
 // instead of stepping A (a sharded cohort sums g over its ranks first)
 cudaError_t atlas_sgd_fused_grad(const float* const* Jrows, int nb, const float* coef, int r, const float* A,
-                                 float scale, float* g, const Vol& v, float* P, cudaStream_t s);
+                                 float scale, float* g, float* gacc, const Vol& v, float* P, cudaStream_t s);
 
 }  // namespace darc_impl

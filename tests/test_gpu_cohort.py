@@ -150,10 +150,13 @@ def _atlas_one_step(metric, n, batch, seed):
     return A0, A, A_ref, g, stats, loss_ref, cfg
 
 
-# batches of 1 to 4 subjects take the two-pass step with the Adam update in
-# the adjoint's epilogue; 6 takes the unfused chain
+# batches of 1 to 4 subjects take one forward and one adjoint box pass with
+# the Adam update in the adjoint's epilogue; 5 to 16 the same passes per
+# sub-batch of up to four (the shared coefficients and the gradient added
+# up across them); 17 the unfused chain
 @pytest.mark.parametrize("metric,n,batch", [(configs.LNCC, 4, 4), (configs.LNCC, 3, 3), (configs.LNCC, 6, 6),
-                                            (configs.SSIM, 4, 4)])
+                                            (configs.LNCC, 10, 10), (configs.LNCC, 17, 17), (configs.SSIM, 4, 4),
+                                            (configs.SSIM, 9, 9)])
 def test_atlas_adam_step_from_identical_state(metric, n, batch):
     A0, A, A_ref, g, stats, loss_ref, cfg = _atlas_one_step(metric, n, batch, 40 + n)
     mask = np.abs(g) > 1e-3 * np.abs(g).max()
@@ -168,7 +171,7 @@ def test_atlas_adam_step_from_identical_state(metric, n, batch):
 
 
 @pytest.mark.parametrize("metric,n,batch", [(configs.LNCC, 5, 2), (configs.LNCC, 7, 3), (configs.LNCC, 9, 4),
-                                            (configs.LNCC, 7, 6), (configs.SSIM, 5, 2)])
+                                            (configs.LNCC, 7, 6), (configs.LNCC, 13, 10), (configs.SSIM, 5, 2)])
 def test_atlas_epochs_follow_the_oracle(metric, n, batch):
     """Several epochs of shuffled mini-batches (the last one partial): the
     atlas loss of the last epoch matches the oracle's, and the atlas stays
@@ -377,6 +380,27 @@ def test_sharded_hooks_reproduce_the_fused_updates():
         assert float((whole.velocity(i) - halves[i // 2].velocity(i % 2)).abs().max()) <= 1e-5
 
     cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=6, atlas_epochs=3, atlas_batch=2, seed=4)
+    fused, split = darc.Cohort(imgs, cfg), darc.Cohort(imgs, cfg)
+    for i in range(n):
+        fused.set_velocity(i, v[i])
+        split.set_velocity(i, v[i])
+    A0 = np64(fused.atlas())
+    fused.update_atlas()
+    ShardedSweep([split], cfg).update_atlas(0)
+    step_f, step_s = np64(fused.atlas()) - A0, np64(split.atlas()) - A0
+    assert np.mean(np.abs(step_f - step_s) <= 1e-3 * np.abs(step_f).max()) > 0.99
+
+
+def test_sharded_hooks_with_sub_batches_reproduce_the_fused_update():
+    """A mini-batch of 7 subjects (sub-batches of 3 and 4): the exchange
+    hooks' gradient, stepped by the host-side Adam, follows the cohort's own
+    update, whose last adjoint pass takes the Adam step."""
+    from paper_2508_10743_gb300.distributed import ShardedSweep
+    shape, n = (12, 16, 34), 7
+    co = cohort_images(n, shape, 19)
+    imgs = co.images.to(DEV).contiguous()
+    v = [synth.random_field(shape, 3.0, 1.5, 500 + i).to(DEV).contiguous() for i in range(n)]
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=6, atlas_epochs=2, atlas_batch=7, seed=6)
     fused, split = darc.Cohort(imgs, cfg), darc.Cohort(imgs, cfg)
     for i in range(n):
         fused.set_velocity(i, v[i])
