@@ -518,7 +518,7 @@ struct AtlasBwdSubjOp {
 // terms shared by the batch are summed over b here (and over the earlier
 // sub-batches when `accum`): coef [2][V] = {sum_b dm_b/dS_A, sum_b
 // dm_b/dS_AA}, coefb [NB][V] = dm_b/dS_JA; loss partials [NB][nblk].
-template <int NB>
+template <int NB, bool ACC>
 struct AtlasFwdFusedOp {
     static constexpr bool kReduces = true;
     static constexpr int kNRed = NB;
@@ -527,7 +527,6 @@ struct AtlasFwdFusedOp {
     const float* A;
     float* coef;
     float* coefb;
-    int accum;
     double* partials;
     int nblk;
     long long V;
@@ -553,7 +552,7 @@ struct AtlasFwdFusedOp {
             coefb[(size_t)b * V + l] = t.c2;
             acc[b] += t.cc * negInvV;
         }
-        if (accum) {
+        if (ACC) {
             s0 = coef[l] + s0;
             s1 = coef[V + l] + s1;
         }
@@ -571,7 +570,7 @@ struct AtlasFwdFusedOp {
 // and written only at the thread's own voxel) or writes g * gscale to gout
 // (a sharded cohort sums g over its ranks before the step); earlier passes
 // write the running sum to gout.  The XY pass reads the coefficients alone.
-template <int NB, bool SHARED>
+template <int NB, bool SHARED, bool ADAM>
 struct AtlasBwdStepOp {
     static constexpr bool kReduces = false;
     const float* J[NB];
@@ -600,7 +599,7 @@ struct AtlasBwdStepOp {
         // each subject's term rounded on its own, as a separate product
 #pragma unroll
         for (int b = 0; b < NB; ++b) g += __fmul_rn(__ldg(J[b] + l), S[(SHARED ? 2 : 0) + b]);
-        if (m) {
+        if (ADAM) {
             float mm = m[l], ss = s[l];
             adam1(a, mm, ss, g * scale, b1, b2, lr_c1, isc2, eps);
             A[l] = a;
@@ -716,13 +715,13 @@ cudaError_t atlas_sgd_backward(const float* J, const int* subj, const float* A, 
 }
 
 namespace {
-template <int NB>
+template <int NB, bool ACC>
 cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* jsrows, const float* A, int r,
-                               float eps, int metric, float* coef, float* coefb, int accum, double* partials,
-                               const Vol& v, float* P, cudaStream_t s)
+                               float eps, int metric, float* coef, float* coefb, double* partials, const Vol& v,
+                               float* P, cudaStream_t s)
 {
     const int w = 2 * r + 1;
-    AtlasFwdFusedOp<NB> op{};
+    AtlasFwdFusedOp<NB, ACC> op{};
     for (int b = 0; b < NB; ++b) {
         op.J[b] = Jrows[b];
         op.js[b] = jsrows[b];
@@ -730,7 +729,6 @@ cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* js
     op.A = A;
     op.coef = coef;
     op.coefb = coefb;
-    op.accum = accum;
     op.partials = partials;
     op.nblk = box_blocks(v, 1);
     op.V = v.V;
@@ -741,17 +739,17 @@ cudaError_t atlas_fused_fwd_nb(const float* const* Jrows, const float* const* js
     return launch_box<2 + NB>(op, 1, v, r, P, s);
 }
 
-template <int NB, bool SHARED>
+template <int NB, bool SHARED, bool ADAM>
 cudaError_t atlas_step_nb(const float* const* Jrows, const float* coef, const float* coefb, int r,
-                          const AtlasStepArgs& q, const float* gin, float* gout, float gscale, bool adam,
-                          const Vol& v, float* P, cudaStream_t s)
+                          const AtlasStepArgs& q, const float* gin, float* gout, float gscale, const Vol& v, float* P,
+                          cudaStream_t s)
 {
-    AtlasBwdStepOp<NB, SHARED> op{};
+    AtlasBwdStepOp<NB, SHARED, ADAM> op{};
     for (int b = 0; b < NB; ++b) op.J[b] = Jrows[b];
     op.coef = coef;
     op.coefb = coefb;
     op.A = q.A;
-    op.m = adam ? q.m : nullptr;
+    op.m = q.m;
     op.s = q.s;
     op.gin = gin;
     op.gout = gout;
@@ -766,16 +764,16 @@ cudaError_t atlas_step_nb(const float* const* Jrows, const float* coef, const fl
     return launch_box<(SHARED ? 2 : 0) + NB>(op, 1, v, r, P, s);
 }
 
-template <bool SHARED>
+template <bool SHARED, bool ADAM>
 cudaError_t atlas_step_pass(const float* const* Jrows, int nb, const float* coef, const float* coefb, int r,
-                            const AtlasStepArgs& q, const float* gin, float* gout, float gscale, bool adam,
-                            const Vol& v, float* P, cudaStream_t s)
+                            const AtlasStepArgs& q, const float* gin, float* gout, float gscale, const Vol& v,
+                            float* P, cudaStream_t s)
 {
     switch (nb) {
-    case 1: return atlas_step_nb<1, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
-    case 2: return atlas_step_nb<2, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
-    case 3: return atlas_step_nb<3, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
-    case 4: return atlas_step_nb<4, SHARED>(Jrows, coef, coefb, r, q, gin, gout, gscale, adam, v, P, s);
+    case 1: return atlas_step_nb<1, SHARED, ADAM>(Jrows, coef, coefb, r, q, gin, gout, gscale, v, P, s);
+    case 2: return atlas_step_nb<2, SHARED, ADAM>(Jrows, coef, coefb, r, q, gin, gout, gscale, v, P, s);
+    case 3: return atlas_step_nb<3, SHARED, ADAM>(Jrows, coef, coefb, r, q, gin, gout, gscale, v, P, s);
+    case 4: return atlas_step_nb<4, SHARED, ADAM>(Jrows, coef, coefb, r, q, gin, gout, gscale, v, P, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -804,12 +802,24 @@ cudaError_t atlas_sgd_fused_forward(const float* const* Jrows, const float* cons
         float* coefb = coef + (size_t)(2 + off) * v.V;
         double* pk = partials + (size_t)off * nblk;
         cudaError_t e;
-        switch (cnt) {
-        case 1: e = atlas_fused_fwd_nb<1>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
-        case 2: e = atlas_fused_fwd_nb<2>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
-        case 3: e = atlas_fused_fwd_nb<3>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
-        case 4: e = atlas_fused_fwd_nb<4>(Jrows + off, jsrows + off, A, r, eps, metric, coef, coefb, k, pk, v, P, s); break;
-        default: e = cudaErrorInvalidValue;
+        const float* const* J = Jrows + off;
+        const float* const* js = jsrows + off;
+        if (k == 0) {
+            switch (cnt) {
+            case 1: e = atlas_fused_fwd_nb<1, false>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            case 2: e = atlas_fused_fwd_nb<2, false>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            case 3: e = atlas_fused_fwd_nb<3, false>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            case 4: e = atlas_fused_fwd_nb<4, false>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            default: e = cudaErrorInvalidValue;
+            }
+        } else {
+            switch (cnt) {
+            case 1: e = atlas_fused_fwd_nb<1, true>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            case 2: e = atlas_fused_fwd_nb<2, true>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            case 3: e = atlas_fused_fwd_nb<3, true>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            case 4: e = atlas_fused_fwd_nb<4, true>(J, js, A, r, eps, metric, coef, coefb, pk, v, P, s); break;
+            default: e = cudaErrorInvalidValue;
+            }
         }
         if (e != cudaSuccess) return e;
     }
@@ -831,10 +841,15 @@ cudaError_t atlas_backward_passes(const float* const* Jrows, int nb, const float
         const bool last = k == K - 1;
         float* go = last ? gout : gacc;
         const float gs = last ? gscale : 1.f;
-        const cudaError_t e = k == 0 ? atlas_step_pass<true>(Jrows + off, cnt, coef, coefb, r, q, nullptr, go, gs,
-                                                             adam && last, v, P, s)
-                                     : atlas_step_pass<false>(Jrows + off, cnt, coef, coefb, r, q, gacc, go, gs,
-                                                              adam && last, v, P, s);
+        const float* const* J = Jrows + off;
+        const float* gin = k == 0 ? nullptr : gacc;
+        cudaError_t e;
+        if (adam && last)
+            e = k == 0 ? atlas_step_pass<true, true>(J, cnt, coef, coefb, r, q, gin, go, gs, v, P, s)
+                       : atlas_step_pass<false, true>(J, cnt, coef, coefb, r, q, gin, go, gs, v, P, s);
+        else
+            e = k == 0 ? atlas_step_pass<true, false>(J, cnt, coef, coefb, r, q, gin, go, gs, v, P, s)
+                       : atlas_step_pass<false, false>(J, cnt, coef, coefb, r, q, gin, go, gs, v, P, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
