@@ -452,11 +452,22 @@ conv3_wgrad_kernel(WgradArgs a)
 constexpr int WG_KC = 64;                 // rows (K) per stage
 constexpr int WG_RA = WG_KC + 2;          // input window rows per stage
 
+// (tap pair, channel group) items a CTA stacks where cin <= 64: the 9 cin/8
+// items over as few CTAs as 16 lane groups allow, evened out (16 channels:
+// 9 + 9 items; 48 channels: 14 + 14 + 14 + 12); 0 above (a pair a CTA)
+int wgrad_items(int cin)
+{
+    if (cin > 64) return 0;
+    const int total = 9 * std::max(cin / 8, 1), ctas = (total + 15) / 16;
+    return (total + ctas - 1) / ctas;
+}
+
 // With few input channels most of the 128 lanes would idle, so a CTA then
-// stacks `pairs` consecutive (dz, dy) pairs (tap pair index 3 dz + dy) in
-// the M dimension: lane row = (pair within the CTA, channel), each pair's
-// channel groups staged from its own shifted window.  The dx taps shift all
-// of them alike.
+// stacks (dz, dy) pairs in the M dimension: the 9 ng items (tap pair 3 dz +
+// dy, 8-channel group) are dealt out evenly, `items` consecutive ones a
+// CTA (lane row = (item within the CTA, channel within its group)), each
+// staged from its pair's own shifted window.  The dx taps shift all of
+// them alike.
 struct WgradWinArgs {
     const bf16* in;
     int in_stride, cin;                   // cin % 16 == 0
@@ -467,7 +478,7 @@ struct WgradWinArgs {
     int B, sp;                            // splits per batch
     long long chunk;                      // rows per split (multiple of WG_KC)
     int kp, np, ns, slot_bytes;
-    int pairs;                            // (dz, dy) pairs per CTA (> 1 only when cin <= 64)
+    int items;                            // (pair, group) items per CTA (cin <= 64), or 0: one pair a CTA
 };
 
 __global__ void __launch_bounds__(128)
@@ -478,9 +489,9 @@ conv3_wgrad_win_kernel(WgradWinArgs a)
     __shared__ uint32_t tslot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const PadVol g = a.g;
-    const int pair0 = blockIdx.x * a.pairs, npair = min(a.pairs, 9 - pair0);   // tap pairs 3 dz + dy
     const int c0 = blockIdx.y * TC_M, nci = min(TC_M, a.cin - c0), ng = nci / 8;
-    const int used = npair * ng;                                  // 8-lane groups in use (<= 16)
+    const int per = a.items ? a.items : ng;
+    const int item0 = blockIdx.x * per, used = min(per, 9 * ng - item0);   // 8-lane groups in use (<= 16)
     const int b = blockIdx.z / a.sp, spi = blockIdx.z - b * a.sp;
     const long long DP = (long long)g.D * g.P;
     const long long r0 = (long long)spi * a.chunk, r1 = min(DP, r0 + a.chunk);
@@ -518,7 +529,7 @@ conv3_wgrad_win_kernel(WgradWinArgs a)
     for (int i = 0; i < WG_AMAX; ++i) {
         const int e = tid + 128 * i;
         const int grp = e / WG_RA, r = e - grp * WG_RA;
-        const int pl = grp / ng, gi = grp - pl * ng, pr = pair0 + pl;
+        const int item = item0 + grp, pr = item / ng, gi = item - pr * ng;   // tap pair 3 dz + dy, group
         a_sm[i] = grp * (int)strideA + r * 16;
         a_row[i] = (pr / 3 - 1) * (int)g.P + (pr % 3 - 1) * g.Wp - 1 + r;   // window row r (dx = 0 at r = 0)
         a_ch[i] = c0 + 8 * gi;
@@ -576,10 +587,10 @@ conv3_wgrad_win_kernel(WgradWinArgs a)
     }
     if (steps > 0) ok = umma::mbar_wait(&mbar[(steps - 1) % a.ns], (uint32_t)(((steps - 1) / a.ns) & 1), TC_WAIT) && ok;
     umma::fence_after_sync();
-    // epilogue: lane m = 32 w + lane is channel c0 + m % (8 ng) of the CTA's
-    // pair m / (8 ng); columns dx * np + co
-    const int m = 32 * warp + lane, pr = pair0 + m / (8 * ng);
-    const int ci = c0 + m % (8 * ng);
+    // epilogue: lane m = 32 w + lane is channel m % 8 of the CTA's item m / 8;
+    // columns dx * np + co
+    const int m = 32 * warp + lane, item = item0 + m / 8, pr = item / ng;
+    const int ci = c0 + 8 * (item - pr * ng) + m % 8;
     for (int dx = 0; dx < 3; ++dx) {
         const int tap = 3 * pr + dx;                             // 9 dz + 3 dy + dx
         float* out = a.partial + ((size_t)blockIdx.z * a.kp + (size_t)tap * a.cin + ci) * a.np;
@@ -1054,7 +1065,7 @@ cudaError_t conv3_wgrad_win(const void* in, int in_stride, int cin, const void* 
     a.np = np;
     a.slot_bytes = (16 * WG_RA * 16 + np * WG_KC * 2 + 127) / 128 * 128;
     a.ns = (3 * a.slot_bytes <= 200 * 1024) ? 3 : 2;
-    a.pairs = cin <= 64 ? std::min(9, 16 / (cin / 8)) : 1;
+    a.items = wgrad_items(cin);
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(conv3_wgrad_win_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1062,7 +1073,7 @@ cudaError_t conv3_wgrad_win(const void* in, int in_stride, int cin, const void* 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const dim3 grid((9 + a.pairs - 1) / a.pairs, (cin + TC_M - 1) / TC_M, a.sp * batch);
+    const dim3 grid(a.items ? (9 * (cin / 8) + a.items - 1) / a.items : 9, (cin + TC_M - 1) / TC_M, a.sp * batch);
     conv3_wgrad_win_kernel<<<grid, 128, (size_t)a.ns * a.slot_bytes, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1072,8 +1083,8 @@ cudaError_t conv3_wgrad_win(const void* in, int in_stride, int cin, const void* 
 
 int wgrad_ctas_per_split(int cin)
 {
-    const int pairs = cin <= 64 ? std::min(9, 16 / std::max(cin / 8, 1)) : 1;
-    return (9 + pairs - 1) / pairs * ((cin + TC_M - 1) / TC_M);
+    const int items = wgrad_items(cin);
+    return items ? (9 * (cin / 8) + items - 1) / items : 9 * ((cin + TC_M - 1) / TC_M);
 }
 
 int wgrad_resident_ctas(int np)
