@@ -449,7 +449,13 @@ conv3_wgrad_kernel(WgradArgs a)
 // descriptors the leading offset is the distance between 8-row K groups
 // (128 bytes here) and the stride offset the distance between 8-channel
 // groups (checked on the GPU against the oracle's weight gradient).
-constexpr int WG_KC = 64;                 // rows (K) per stage
+#ifndef DARC_WG_KC
+#define DARC_WG_KC 64
+#endif
+#ifndef DARC_WGRAD_NS
+#define DARC_WGRAD_NS 0
+#endif
+constexpr int WG_KC = DARC_WG_KC;         // rows (K) per stage
 constexpr int WG_RA = WG_KC + 2;          // input window rows per stage
 
 // (tap pair, channel group) items a CTA stacks where cin <= 64: the 9 cin/8
@@ -1064,7 +1070,7 @@ cudaError_t conv3_wgrad_win(const void* in, int in_stride, int cin, const void* 
     a.kp = kp;
     a.np = np;
     a.slot_bytes = (16 * WG_RA * 16 + np * WG_KC * 2 + 127) / 128 * 128;
-    a.ns = (3 * a.slot_bytes <= 200 * 1024) ? 3 : 2;
+    a.ns = (DARC_WGRAD_NS == 2 || 3 * a.slot_bytes > 200 * 1024) ? 2 : 3;
     a.items = wgrad_items(cin);
     static bool attr = false;
     if (!attr) {
@@ -1108,7 +1114,7 @@ int wgrad_resident_ctas(int np)
         sms = n;
     }
     const int slot = (16 * WG_RA * 16 + np * WG_KC * 2 + 127) / 128 * 128;
-    const int ns = (3 * slot <= 200 * 1024) ? 3 : 2;
+    const int ns = (DARC_WGRAD_NS == 2 || 3 * slot > 200 * 1024) ? 2 : 3;
     const int per_smem = smem_sm / (ns * slot + smem_static + smem_rsv);
     const int per_regs = 65536 / (((regs + 7) & ~7) * 128);
     return std::max(1, std::min({per_smem, per_regs, 16})) * sms;
