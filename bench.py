@@ -277,6 +277,10 @@ def main():
     # the next step's images into a staging buffer while the current sweep
     # runs; each step starts with a device copy from the staging buffer into
     # the cohort's images.  The first copy is inside the timed region too.
+    # Every step's result (each subject's losses, and the atlas) is copied
+    # to pinned host memory and read on the host: step k's values are read
+    # once step k + 1 is queued behind them, so the GPU never waits for the
+    # host; the last step's are read after it, inside the timed region.
     e2e = None
     if not args.no_e2e:
         host_imgs = images.cpu().pin_memory()
@@ -285,6 +289,10 @@ def main():
         copy_stream = torch.cuda.Stream(device=dev)
         ready = torch.cuda.Event()
         main_stream = torch.cuda.current_stream()
+        loss_dev = torch.empty((wl.n, 2), dtype=torch.float32, device=dev)
+        loss_host = [torch.empty((wl.n, 2), dtype=torch.float32).pin_memory() for _ in range(2)]
+        landed = [torch.cuda.Event(), torch.cuda.Event()]
+        results = []
 
         def prefetch():
             copy_stream.wait_stream(main_stream)     # the staging buffer has been read
@@ -292,18 +300,34 @@ def main():
                 staging.copy_(host_imgs, non_blocking=True)
                 ready.record(copy_stream)
 
+        def read(slot):
+            landed[slot].synchronize()
+            lh = loss_host[slot]
+            if not bool(torch.isfinite(lh).all()):
+                raise RuntimeError("a subject's loss is not finite")
+            results.append((float(lh[:, 0].mean()), float(host_atlas[0, 0, 0])))
+
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         prefetch()
+        pending = None
         for k in range(args.steps):
             main_stream.wait_event(ready)
             images.copy_(staging, non_blocking=True)
             if k + 1 < args.steps:
                 prefetch()
-            st = step(stats=True)                    # waits; reads the step's loss
+            step()
+            c.losses_async(loss_dev)
+            if pending is not None:
+                read(pending)                    # step k - 1's values (step k is queued behind them)
+            slot = k % 2
+            loss_host[slot].copy_(loss_dev, non_blocking=True)
             host_atlas.copy_(c.atlas(), non_blocking=True)
+            landed[slot].record(main_stream)
+            pending = slot
+        read(pending)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         if world > 1:
@@ -312,7 +336,7 @@ def main():
             dt = float(t.item())
         e2e = {"value": units / dt / 1e9, "unit": "GVoxel/s",
                "h2d_bytes_per_step": int(images.numel() * 4),
-               "d2h_bytes_per_step": int(host_atlas.numel() * 4 + 48)}
+               "d2h_bytes_per_step": int(host_atlas.numel() * 4 + loss_dev.numel() * 4)}
 
     if rank != 0:
         if world > 1:

@@ -131,6 +131,14 @@ int darc_subject_step(darc_cohort* c, int first, int count, int steps, float* lo
  * after waiting for the stream.  Errors: ARG, CUDA, NONFINITE. */
 int darc_sweep(darc_cohort* c, darc_sweep_stats* stats);
 
+/* Enqueues, without waiting, a copy of every subject's losses at its last
+ * step into out_dev float [n][2] = (L, R) (the values darc_sweep's stats
+ * average), ordered on the caller's stream after the work already enqueued
+ * on the cohort: a driver can read step k's losses while step k + 1 runs.
+ * Non-finite losses are copied as they are (the next darc_sweep with stats
+ * reports them).  Errors: ARG, CUDA. */
+int darc_sweep_losses(darc_cohort* c, float* out_dev);
+
 /* Centrality activation hat v_i = v_i - 1/n sum_j v_j (Eq. 3 line n+1) on
  * the stored velocities, then the atlas re-estimate (Eq. 3 last line): MSE,
  * A = 1/n sum_i I_i o Exp(hat v_i) (Sec. "Dissimilarity metrics", closed

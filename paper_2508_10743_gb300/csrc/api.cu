@@ -999,6 +999,15 @@ int darc_sweep(darc_cohort* c, darc_sweep_stats* stats)
     return DARC_OK;
 }
 
+int darc_sweep_losses(darc_cohort* c, float* out_dev)
+{
+    if (!c || !out_dev) return fail(DARC_ERR_ARG, "null argument");
+    int rc = begin(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out_dev, c->loss, sizeof(float) * 2 * (size_t)c->n, cudaMemcpyDeviceToDevice, c->st));
+    return end(c);
+}
+
 int darc_propagate_labels(darc_cohort* c, const uint8_t* labels_dev, uint8_t* out_dev, int first, int count)
 {
     if (!c || !labels_dev || !out_dev) return fail(DARC_ERR_ARG, "null argument");

@@ -67,6 +67,7 @@ _SIGS = {
     "darc_init_cohort": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(CConfig), _i, _i, _i, _i, _vp, _vp]),
     "darc_subject_step": (_i, [_vp, _i, _i, _i, _vp]),
     "darc_sweep": (_i, [_vp, ctypes.POINTER(CSweepStats)]),
+    "darc_sweep_losses": (_i, [_vp, _vp]),
     "darc_update_atlas": (_i, [_vp, ctypes.POINTER(CSweepStats)]),
     "darc_propagate_labels": (_i, [_vp, _vp, _vp, _i, _i]),
     "darc_get_atlas": (_i, [_vp, _vp]),
@@ -262,6 +263,17 @@ class Cohort:
         if not stats:
             return None
         return {k: getattr(st, k) for k, _ in CSweepStats._fields_}
+
+    def losses_async(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Every subject's (L, R) at its last step, [n, 2] on the device,
+        copied without waiting (ordered after the work already enqueued)."""
+        if out is None:
+            out = torch.empty((self.n, 2), dtype=torch.float32, device=self.device)
+        _need(out, "losses")
+        if tuple(out.shape) != (self.n, 2):
+            raise ValueError(f"losses: expected shape ({self.n}, 2), got {tuple(out.shape)}")
+        _check(lib().darc_sweep_losses(self._h, _ptr(out)))
+        return out
 
     def update_atlas(self, stats: bool = True):
         st = CSweepStats()

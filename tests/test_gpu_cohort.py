@@ -391,6 +391,25 @@ def test_sharded_hooks_reproduce_the_fused_updates():
     assert np.mean(np.abs(step_f - step_s) <= 1e-3 * np.abs(step_f).max()) > 0.99
 
 
+def test_losses_async_match_the_sweep_statistics():
+    """The non-waiting loss copy returns the per-subject values whose means
+    the sweep's statistics report."""
+    shape, n = (12, 16, 20), 5
+    co = cohort_images(n, shape, 23)
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=5, n_squarings=6, inner_steps=2, atlas_epochs=1,
+                             atlas_batch=2)
+    c = darc.Cohort(co.images.to(DEV).contiguous(), cfg)
+    for i in range(n):
+        c.set_velocity(i, synth.random_field(shape, 3.0, 1.5, 600 + i).to(DEV).contiguous())
+    st = c.sweep(stats=True)
+    got = c.losses_async().cpu().double().numpy()
+    assert got.shape == (n, 2)
+    assert abs(got[:, 0].mean() - st["loss_data"]) <= 1e-6 * abs(st["loss_data"])
+    assert abs(got[:, 1].mean() - st["loss_reg"]) <= 1e-6 * abs(st["loss_reg"]) + 1e-12
+    with pytest.raises(ValueError):
+        c.losses_async(torch.empty((n + 1, 2), device=DEV))
+
+
 def test_sharded_hooks_with_sub_batches_reproduce_the_fused_update():
     """A mini-batch of 7 subjects (sub-batches of 3 and 4): the exchange
     hooks' gradient, stepped by the host-side Adam, follows the cohort's own
