@@ -123,10 +123,12 @@ class ClockSampler:
             self.proc.kill()
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in self.rows if r[3].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w": statistics.median(pw) if pw else None}
 
 
 def cpu_threads():
@@ -310,6 +312,8 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        e2e_sampler = ClockSampler(local)
+        e2e_sampler.start()
         t0 = time.perf_counter()
         prefetch()
         pending = None
@@ -330,13 +334,15 @@ def main():
         read(pending)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        e2e_clocks = e2e_sampler.stop()
         if world > 1:
             t = torch.tensor([dt], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
         e2e = {"value": units / dt / 1e9, "unit": "GVoxel/s",
                "h2d_bytes_per_step": int(images.numel() * 4),
-               "d2h_bytes_per_step": int(host_atlas.numel() * 4 + loss_dev.numel() * 4)}
+               "d2h_bytes_per_step": int(host_atlas.numel() * 4 + loss_dev.numel() * 4),
+               "clocks": e2e_clocks}
 
     if rank != 0:
         if world > 1:
