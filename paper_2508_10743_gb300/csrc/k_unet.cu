@@ -158,9 +158,11 @@ struct WinArgs {
     PadVol g;
     int np, R, ns, slot_bytes;
     int parts, br;                // R = parts x br window rows per channel group (br <= 256, a multiple of 8)
-    long long tiles_per_batch;
+    int mt;                       // 128-row sub-tiles a block owns (1 or 2), one TMEM accumulator each
+    long long tiles_per_batch;    // of mt x 128 rows
 };
 
+template <int MT>
 __global__ void __launch_bounds__(128)
 conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
 {
@@ -171,11 +173,11 @@ conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const PadVol g = a.g;
     const int b = (int)(blockIdx.x / a.tiles_per_batch);
-    const long long q0 = g.P + (long long)(blockIdx.x % a.tiles_per_batch) * TC_M;
+    const long long q0 = g.P + (long long)(blockIdx.x % a.tiles_per_batch) * TC_M * MT;
     const long long base_b = (long long)b * g.Vp;
     uint32_t ncols = 32;
     while ((int)ncols < a.np) ncols <<= 1;
-    if (warp == 0) umma::tmem_alloc(&tslot, ncols);
+    if (warp == 0) umma::tmem_alloc(&tslot, ncols * (uint32_t)MT);
     if (tid == 0) {
         for (int k = 0; k < a.ns; ++k) {
             umma::mbar_init(&full[k], 1);
@@ -216,9 +218,14 @@ conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
             const uint32_t Bs = As + 2 * lboA;
             for (int t9 = 0; t9 < 9; ++t9) {
                 const int dy = t9 / 3, dx = t9 - 3 * dy;
-                const uint64_t da = umma::smem_desc(As + (uint32_t)(dy * g.Wp + dx) * 16u, lboA, 128);
                 const uint64_t db = umma::smem_desc(Bs + (uint32_t)t9 * 2u * lboB, lboB, 128);
-                umma::mma_bf16(tmem, da, db, idesc, (i > 0) || (t9 > 0));
+                // sub-tile h reads the window 128 h rows further on, into accumulator h
+#pragma unroll
+                for (int h = 0; h < MT; ++h) {
+                    const uint32_t row = (uint32_t)(dy * g.Wp + dx + TC_M * h);
+                    const uint64_t da = umma::smem_desc(As + row * 16u, lboA, 128);
+                    umma::mma_bf16(tmem + (uint32_t)h * ncols, da, db, idesc, (i > 0) || (t9 > 0));
+                }
             }
             umma::commit(&empty[slot]);
             // refill the previous stage's slot once its MMAs (queued before these) retire
@@ -235,8 +242,9 @@ conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
     const bool ok = umma::mbar_wait(&empty[(nst - 1) % a.ns], (uint32_t)(((nst - 1) / a.ns) & 1), TC_WAIT) && !bad;
     umma::fence_after_sync();
 
-    // epilogue: warp w holds rows q0 + 32 w + lane
-    const long long q = q0 + 32 * warp + lane;
+    // epilogue: warp w holds rows q0 + 128 h + 32 w + lane of sub-tile h
+    for (int h = 0; h < MT; ++h) {
+    const long long q = q0 + TC_M * h + 32 * warp + lane;
     const int xp = (int)(q % g.Wp), yp = (int)((q / g.Wp) % g.Hp);
     const long long zp = q / g.P;
     const bool valid = zp <= g.D && yp >= 1 && yp <= g.H && xp >= 1 && xp <= g.W;
@@ -245,7 +253,7 @@ conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
     const long long l = ((zp - 1) * g.H + (yp - 1)) * (long long)g.W + (xp - 1);
     for (int c = 0; c < a.np; c += 8) {
         float r8[8];
-        umma::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, r8);
+        umma::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)h * ncols + (uint32_t)c, r8);
         if (!valid || c >= a.cout) continue;
         float y8[8];
 #pragma unroll
@@ -268,9 +276,9 @@ conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
                 if (c + j < a.cout) a.out_f32[((size_t)b * a.cout + c + j) * V + l] = y8[j];
         } else if (a.out_vec && c + 8 <= a.cout) {
             uint4 pk;
-            __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&pk);
+            __nv_bfloat162* hp = reinterpret_cast<__nv_bfloat162*>(&pk);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(y8[2 * j], y8[2 * j + 1]);
+            for (int j = 0; j < 4; ++j) hp[j] = __floats2bfloat162_rn(y8[2 * j], y8[2 * j + 1]);
             *reinterpret_cast<uint4*>(a.out + orow * a.out_stride + c) = pk;
         } else {
 #pragma unroll
@@ -278,9 +286,10 @@ conv3_win_kernel(const __grid_constant__ CUtensorMap tmap, WinArgs a)
                 if (c + j < a.cout) a.out[orow * a.out_stride + c + j] = __float2bfloat16(y8[j]);
         }
     }
+    }
     umma::fence_before_sync();
     __syncthreads();
-    if (warp == 0) umma::tmem_dealloc(tmem, ncols);
+    if (warp == 0) umma::tmem_dealloc(tmem, ncols * (uint32_t)MT);
 }
 
 // packed[(((c 3 + dz) 9 + t9) 2 + grp) nrows + row] [e], tap = 9 dz + t9,
@@ -917,21 +926,30 @@ PadVol make_pad(int D, int H, int W)
 
 // window rows a stage needs, split into parts of br <= 256 rows (a TMA box
 // dimension), br a multiple of 8 (128-byte aligned boxes)
-static void conv_window_split(int W, int& parts, int& br)
+static void conv_window_split(int W, int mt, int& parts, int& br)
 {
-    const int need = TC_M + 2 * (W + 2) + 2;
+    const int need = TC_M * mt + 2 * (W + 2) + 2;
     parts = (need + 255) / 256;
     br = ((need + parts - 1) / parts + 7) / 8 * 8;
 }
 
-int conv_window_rows(int W)
+// 128-row sub-tiles a block owns: two (one window for 256 rows: 1.9 staged
+// rows an output row instead of 2.9 at W = 112) where their two
+// accumulators leave TMEM for the resident blocks (np <= 64) and the grid
+// still has many blocks an SM (large volumes); else one
+static int conv_mt_max(int np) { return np <= 64 ? 2 : 1; }
+static int conv_mt(int np, long long rows) { return conv_mt_max(np) == 2 && rows / (2 * TC_M) >= 24 * 152 ? 2 : 1; }
+
+int conv_window_rows(int W, int mt)
 {
     int parts, br;
-    conv_window_split(W, parts, br);
+    conv_window_split(W, mt, parts, br);
     return parts * br;
 }
 
-int conv_slot_bytes(int W, int np) { return (32 * conv_window_rows(W) + 288 * np + 127) / 128 * 128; }
+static int conv_slot_bytes(int W, int np, int mt) { return (32 * conv_window_rows(W, mt) + 288 * np + 127) / 128 * 128; }
+
+int conv_slot_bytes(int W, int np) { return conv_slot_bytes(W, np, conv_mt_max(np)); }
 
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -971,16 +989,19 @@ cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s)
     a.B = d.batch;
     a.g = make_pad(d.D, d.H, d.W);
     a.np = d.np;
-    conv_window_split(d.W, a.parts, a.br);
+    a.mt = conv_mt(d.np, (long long)d.batch * d.D * a.g.P);
+    conv_window_split(d.W, a.mt, a.parts, a.br);
     a.R = a.parts * a.br;
-    a.slot_bytes = conv_slot_bytes(d.W, d.np);
+    a.slot_bytes = conv_slot_bytes(d.W, d.np, a.mt);
     a.ns = (DARC_CONV_NS == 2 || 3 * a.slot_bytes > 200 * 1024) ? 2 : 3;
-    a.tiles_per_batch = ((long long)d.D * a.g.P + TC_M - 1) / TC_M;
+    a.tiles_per_batch = ((long long)d.D * a.g.P + TC_M * a.mt - 1) / (TC_M * a.mt);
     if (!conv_fits(d.W, d.np)) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv3_win_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(conv3_win_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              CONV_SMEM_MAX);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(conv3_win_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM_MAX);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -1000,7 +1021,10 @@ cudaError_t conv3_forward(const ConvDesc& d, cudaStream_t s)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     const long long blocks = (long long)d.batch * a.tiles_per_batch;
-    conv3_win_kernel<<<(unsigned)blocks, 128, (size_t)a.ns * a.slot_bytes, s>>>(tmap, a);
+    if (a.mt == 2)
+        conv3_win_kernel<2><<<(unsigned)blocks, 128, (size_t)a.ns * a.slot_bytes, s>>>(tmap, a);
+    else
+        conv3_win_kernel<1><<<(unsigned)blocks, 128, (size_t)a.ns * a.slot_bytes, s>>>(tmap, a);
     return cudaGetLastError();
 }
 

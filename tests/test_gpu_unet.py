@@ -89,6 +89,7 @@ CONV_CASES = [
     (1, (3, 4, 112), 16, 16, 256, 256),          # a wide window: two pipeline stages
     (2, (44, 46, 48), 16, 16, 16, 16),           # several tiles per resident CTA
     (2, (32, 36, 40), 48, 64, 16, 16),           # and three channel chunks per tile
+    (2, (64, 96, 112), 16, 16, 16, 16),          # a large volume: two 128-row sub-tiles a block
 ]
 
 
