@@ -375,7 +375,7 @@ def main():
                 "traffic": (traffic if traffic is None else traffic),
                 "algorithmic_bytes_per_launch": by / nl, "avg_launch_ms": tot_ms / nl,
                 "share_of_step": tot_ms / prof_ms,
-                "source": "per-launch CUDA events of a profiled pass over the same number of steps, run after "
+                "source": "per-launch CUDA events of a profiled pass over the same number of steps from the same starting state, run after "
                           "the timed region (value and ms_per_step come from the timed graph replays)"}
     kernels = {k: {"ms": v[0], "launches": v[1], "GB/s": (v[2] / (v[0] / 1e3) / 1e9) if v[2] > 0 else None,
                    "share": v[0] / prof_ms} for k, v in prof.items() if v[1] > 0}
