@@ -42,6 +42,106 @@ namespace {
 #endif
 constexpr int SQ_Z = DARC_SQ_Z;
 
+// Staged squaring of a packed field (u_t, t >= 1): a block of 32 x 8 threads
+// walks SQS_Z planes of a 32 x 8 column tile, keeping planes z - 1, z and
+// z + 1 of u_t with a one-voxel halo in shared memory (a ring of four: the
+// next plane is copied in while the current one is sampled; one block
+// barrier a plane).  A voxel whose cell lies in the staged box (every |u|
+// below one voxel, or a clamped cell at the border) reads its 8 corners
+// there, others through the read-only cache; the corner values and the
+// interpolation are the same either way, so the result equals
+// exp_square_kernel's bit for bit.  Off by default (DARC_SQ_STAGED=1 turns it
+// on): the squaring is bound by its DRAM bytes, which staging does not
+// change, and the halo copies and the barrier a plane cost more than the
+// L1 hits they replace (brain sweep: 148 against 122 ms of squarings).
+#ifndef DARC_SQ_STAGED
+#define DARC_SQ_STAGED 0
+#endif
+#ifndef DARC_SQS_Z
+#define DARC_SQS_Z 16
+#endif
+constexpr int SQS_Z = DARC_SQS_Z;
+constexpr int SQS_TX = VT_X + 2, SQS_TY = VT_Y + 2;
+
+__device__ __forceinline__ void sqs_copy16(float4* dst_smem, const float4* src, bool in)
+{
+    // 16-byte asynchronous copy into shared memory; zeros where !in
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst_smem))), "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(VT_THREADS)
+exp_square_staged_kernel(PackedField src_all, float scale, float4* __restrict__ dst, Vol v, int nzt,
+                         float4* __restrict__ zero)
+{
+    __shared__ __align__(16) float4 tile[4][SQS_TY][SQS_TX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * VT_X + tx;
+    const int x0 = blockIdx.x * VT_X, y0 = blockIdx.y * VT_Y;
+    const int x = x0 + tx, y = y0 + ty;
+    const int zt = blockIdx.z % nzt, b = blockIdx.z / nzt;
+    const int z0 = zt * SQS_Z;
+    const PackedField f = src_all.subject(b);
+    float4* d0 = dst + (size_t)b * v.V;
+    const int plane = v.H * v.W;
+    // plane zz into its ring slot by asynchronous copies (one commit group)
+    auto stage = [&](int zz) {
+        float4 (*t)[SQS_TX] = tile[(zz - z0 + 1) & 3];
+        for (int e = tid; e < SQS_TY * SQS_TX; e += VT_THREADS) {
+            const int ry = e / SQS_TX, rx = e - ry * SQS_TX;
+            const int gy = y0 - 1 + ry, gx = x0 - 1 + rx;
+            const bool in = zz >= 0 && zz < v.D && gy >= 0 && gy < v.H && gx >= 0 && gx < v.W;
+            sqs_copy16(&t[ry][rx], in ? f.p + (size_t)zz * plane + gy * v.W + gx : f.p, in);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // planes z0 - 1 .. z0 + 2 (one commit group each); then each plane's
+    // group is committed two planes before it is sampled
+    stage(z0 - 1);
+    stage(z0);
+    stage(z0 + 1);
+    stage(z0 + 2);
+    const bool in_xy = x < v.W && y < v.H;
+    for (int k = 0; k < SQS_Z; ++k) {
+        const int z = z0 + k;
+        if (z >= v.D) break;                         // uniform over the block
+        // planes z - 1 .. z + 1 landed (the last group, plane z + 2, may be in flight)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        if (in_xy) {
+            const float4 o = tile[(k + 1) & 3][ty + 1][tx + 1];
+            const float uz = scale * o.x, uy = scale * o.y, ux = scale * o.z;
+            const Cell c = make_cell(z, y, x, uz, uy, ux, v);
+            float4 q[8];
+            if (c.iz >= z - 1 && c.iz <= z && c.iy >= y0 - 1 && c.iy <= y0 + VT_Y - 1 && c.ix >= x0 - 1 &&
+                c.ix <= x0 + VT_X - 1) {
+                const int sz = (c.iz - z0 + 1) & 3, ry = c.iy - y0 + 1, rx = c.ix - x0 + 1;
+                const int sz1 = (sz + 1) & 3;
+                q[0] = tile[sz][ry][rx];
+                q[1] = tile[sz][ry][rx + 1];
+                q[2] = tile[sz][ry + 1][rx];
+                q[3] = tile[sz][ry + 1][rx + 1];
+                q[4] = tile[sz1][ry][rx];
+                q[5] = tile[sz1][ry][rx + 1];
+                q[6] = tile[sz1][ry + 1][rx];
+                q[7] = tile[sz1][ry + 1][rx + 1];
+            } else {
+                f.corners(c, v, q);
+            }
+            const float sx = tri_corners(c, q[0].x, q[1].x, q[2].x, q[3].x, q[4].x, q[5].x, q[6].x, q[7].x);
+            const float sy = tri_corners(c, q[0].y, q[1].y, q[2].y, q[3].y, q[4].y, q[5].y, q[6].y, q[7].y);
+            const float sz_ = tri_corners(c, q[0].z, q[1].z, q[2].z, q[3].z, q[4].z, q[5].z, q[6].z, q[7].z);
+            const int l = z * plane + y * v.W + x;
+            d0[l] = make_float4(fmaf(scale, sx, uz), fmaf(scale, sy, uy), fmaf(scale, sz_, ux), 0.f);
+            if (zero) zero[(size_t)b * v.V + l] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // every thread is done with plane z - 1: its slot takes plane z + 3
+        __syncthreads();
+        stage(z + 3);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Src: PlanarField or PackedField; PACKED_OUT: u_{t+1} written packed
 // (float4 a voxel) instead of planar.  zero (packed only, may be null): a
 // packed buffer of the same shape cleared on the way.
@@ -498,7 +598,12 @@ cudaError_t exp_square_packed(const float* src, int src_packed, float scale, flo
     int nzt;
     const dim3 grid = voxel_grid(B, v, nzt, SQ_Z);
     float* d = reinterpret_cast<float*>(dst);
-    if (src_packed)
+    if (src_packed && DARC_SQ_STAGED) {
+        int nzs;
+        const dim3 gs = voxel_grid(B, v, nzs, SQS_Z);
+        exp_square_staged_kernel<<<gs, dim3(VT_X, VT_Y), 0, s>>>(
+            PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, dst, v, nzs, zero);
+    } else if (src_packed)
         exp_square_kernel<PackedField, true><<<grid, dim3(VT_X, VT_Y), 0, s>>>(
             PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, d, v, nzt, zero);
     else
