@@ -204,6 +204,12 @@ constexpr int FAR_Z = 8;
 #ifndef DARC_ADJ_MINB
 #define DARC_ADJ_MINB 4
 #endif
+// rows of the interleaved adjoint's blocks (32 x ADJ_Y threads; the
+// resident-block cap scales so that a multiprocessor keeps the same threads)
+#ifndef DARC_ADJ_Y
+#define DARC_ADJ_Y 8
+#endif
+constexpr int ADJ_Y = DARC_ADJ_Y;
 // 1: the interleaved adjoint loads the next plane's displacement and
 // gradient while it works on the current one
 #ifndef DARC_ADJ_PREFETCH
@@ -396,15 +402,17 @@ __device__ __forceinline__ bool near_source(float uz, float uy, float ux)
 // outgoing one is always interleaved [V] float4 per field.  FAR: only the
 // transpose terms of far sources, in marked tiles (flags).
 template <bool IN4, class Src, bool FAR = false>
-__global__ void __launch_bounds__(VT_THREADS, DARC_ADJ_MINB)
+__global__ void __launch_bounds__(FAR ? VT_THREADS : VT_X * ADJ_Y,
+                                  FAR ? DARC_ADJ_MINB : DARC_ADJ_MINB * VT_Y / ADJ_Y)
 exp_square_adjoint4_kernel(Src src_all, float scale, const float* __restrict__ gin,
                            float4* __restrict__ gout, float out_scale, Vol v, int nzt, int* flags = nullptr)
 {
     if (FAR && !far_tile(flags)) return;
     constexpr int ZT = FAR ? FAR_Z : ADJ_Z;   // planes per thread
+    constexpr int TY = FAR ? VT_Y : ADJ_Y;    // rows per block
     const int lane = threadIdx.x;
     const int x = blockIdx.x * VT_X + threadIdx.x;
-    const int y = blockIdx.y * VT_Y + threadIdx.y;
+    const int y = blockIdx.y * TY + threadIdx.y;
     const int zt = blockIdx.z % nzt;
     const int b = blockIdx.z / nzt;
     const bool xy_ok = (x < v.W) && (y < v.H);
@@ -629,9 +637,9 @@ void launch_adjoint4(Src f, float scale, const float* gin, int gin_interleaved, 
                      dim3 grid, const Vol& v, int nzt, cudaStream_t s)
 {
     if (gin_interleaved)
-        exp_square_adjoint4_kernel<true, Src><<<grid, dim3(VT_X, VT_Y), 0, s>>>(f, scale, gin, gout, out_scale, v, nzt);
+        exp_square_adjoint4_kernel<true, Src><<<grid, dim3(VT_X, ADJ_Y), 0, s>>>(f, scale, gin, gout, out_scale, v, nzt);
     else
-        exp_square_adjoint4_kernel<false, Src><<<grid, dim3(VT_X, VT_Y), 0, s>>>(f, scale, gin, gout, out_scale, v, nzt);
+        exp_square_adjoint4_kernel<false, Src><<<grid, dim3(VT_X, ADJ_Y), 0, s>>>(f, scale, gin, gout, out_scale, v, nzt);
 }
 
 cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, const float* gin, int gin_interleaved,
@@ -641,7 +649,8 @@ cudaError_t exp_square_adjoint4(const float* src, int src_packed, float scale, c
         (src_packed && (reinterpret_cast<uintptr_t>(src) & 15)))
         return cudaErrorMisalignedAddress;
     int nzt;
-    const dim3 grid = voxel_grid(B, v, nzt, ADJ_Z);
+    dim3 grid = voxel_grid(B, v, nzt, ADJ_Z);
+    grid.y = div_up(v.H, ADJ_Y);
     if (src_packed)
         launch_adjoint4(PackedField{reinterpret_cast<const float4*>(src), v.V}, scale, gin, gin_interleaved, gout,
                         out_scale, grid, v, nzt, s);
