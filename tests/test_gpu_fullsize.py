@@ -180,3 +180,57 @@ def test_full_size_labels_through_the_inverse_map_at_the_cardiac_scale():
           f"fraction inside the 1e-5 band per subject: {', '.join(f'{b:.2e}' for b in band)}")
     assert worst < 1e-5
     c.close()
+
+
+def test_full_size_cardiac_atlas_step_in_sub_batches_matches_the_oracle():
+    """The NCC atlas update (window 9) at the cardiac size on one mini-batch
+    of 10 subjects of 128x128x96 at the 5-voxel scale, which the library
+    runs as three fused sub-batches (3 + 3 + 4 subjects).  The batch
+    gradient of the fused passes (read through the sharding hooks) is held
+    to the gradient bar (relative L2 1e-3) against the oracle's sum of the
+    subjects' NCC gradients, the loss to 1e-4; then one Adam step of the
+    atlas from the same state is compared with the oracle's on the voxels
+    where the step is saturated (|mean gradient| above 100 x Adam's eps):
+    at this size most gradients are of the order of Adam's eps, where the
+    step lr g / (|g| + eps) follows float rounding of g."""
+    shape, n = (128, 128, 96), 10
+    co = synth.make_cohort(n, shape, 5010, phantom="shells", sigma=6.0, max_disp=5.0, device=DEV,
+                           keep_disp=False, out_device="cpu")
+    cfg = configs.DarcConfig(dissim=configs.LNCC, ncc_window=9, n_squarings=7, atlas_epochs=1, atlas_batch=n,
+                             seed=21)
+    vv = np.ascontiguousarray(np64(-co.w))
+    oracle.centrality(vv)
+    vv = np.ascontiguousarray(vv.astype(np.float32).astype(np.float64))
+    c = darc.Cohort(co.images.to(DEV).contiguous(), cfg)
+    for i in range(n):
+        c.set_velocity(i, torch.from_numpy(vv[i]).float().to(DEV).contiguous())
+    A0 = np64(c.atlas())
+    c.atlas_sgd_begin(0)
+    g_gpu, loss_gpu = c.atlas_sgd_grad(0, 0)
+    g_gpu, loss_gpu = np64(g_gpu), float(loss_gpu[0])
+    c.atlas_sgd_end()
+    I = np64(co.images)
+    g_ref, loss_sum = np.zeros_like(A0), 0.0
+    for i in range(n):
+        Wi = oracle.warp(I[i], oracle.exp(vv[i], 7)[-1])
+        out = oracle.lncc(Wi, A0, 9, 1e-5, with_grad=True)
+        loss_sum += out[0]
+        g_ref += out[2]
+    rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    assert rel <= 1e-3, rel
+    assert abs(loss_gpu - loss_sum) <= 1e-4 * abs(loss_sum)
+    stats = c.update_atlas()
+    A = np64(c.atlas())
+    c.close()
+    ocfg = oracle.make_cfg(dissim=cfg.dissim, window=cfg.ncc_window, T=cfg.n_squarings, atlas_epochs=1,
+                           atlas_batch=n, lam=cfg.lam, lr=cfg.lr, seed=cfg.seed)
+    A_ref, loss_ref = oracle.atlas_sgd(I, vv, A0, ocfg, sweep=0)
+    step, step_ref = A - A0, A_ref - A0
+    sat = np.abs(g_ref / n) > 100 * 1e-8
+    flips = int((np.abs(step - step_ref) > 1e-4 * cfg.lr)[sat].sum())
+    print(f"cardiac-size atlas (batch 10 in three sub-batches): gradient rel-L2 {rel:.2e}; "
+          f"{int(sat.sum())} saturated voxels, {flips} steps differ")
+    assert sat.sum() >= 1000
+    assert flips <= 1e-3 * sat.sum()
+    assert np.abs(step).max() <= cfg.lr * (1 + 1e-6)
+    assert abs(stats["atlas_loss"] - loss_ref) <= 1e-4 * abs(loss_ref)
