@@ -62,37 +62,28 @@ __device__ __forceinline__ Cell make_cell(int z, int y, int x, float uz, float u
     return c;
 }
 
-// Whether make_cell reduces to its unclamped case at this voxel: every
-// coordinate at least one voxel inside the faces and every |u_a| < 1, so
-// x_a + u_a lies strictly inside (0, n_a - 1) and no axis clamps.
-__device__ __forceinline__ bool interior_near(int z, int y, int x, float uz, float uy, float ux, const Vol& v)
-{
-    return z >= 1 && z <= v.D - 2 && y >= 1 && y <= v.H - 2 && x >= 1 && x <= v.W - 2 && fabsf(uz) < 1.f &&
-           fabsf(uy) < 1.f && fabsf(ux) < 1.f;
-}
-
-// make_cell where interior_near holds (the same floats, without the clamps)
-__device__ __forceinline__ Cell make_cell_inner(int z, int y, int x, float uz, float uy, float ux, const Vol& v)
-{
-    Cell c;
-    const float fz = floorf(uz), fy = floorf(uy), fx = floorf(ux);
-    c.iz = z + (int)fz;
-    c.iy = y + (int)fy;
-    c.ix = x + (int)fx;
-    c.tz = uz - fz;
-    c.ty = uy - fy;
-    c.tx = ux - fx;
-    c.cz = c.cy = c.cx = false;
-    c.base = (c.iz * v.H + c.iy) * v.W + c.ix;
-    return c;
-}
-
-// make_cell, in the short form when every lane running it together
-// qualifies (both forms give the same cell where interior_near holds)
+// make_cell in its unclamped form when every lane running it together has
+// an unclamped cell on every axis (|u| < 1e6 and 0 <= x + floor(u) <= n - 2:
+// make_cell's middle case, the same floats), else make_cell itself.
 __device__ __forceinline__ Cell make_cell_warp(int z, int y, int x, float uz, float uy, float ux, const Vol& v)
 {
-    if (__all_sync(__activemask(), interior_near(z, y, x, uz, uy, ux, v)))
-        return make_cell_inner(z, y, x, uz, uy, ux, v);
+    const float fz = floorf(uz), fy = floorf(uy), fx = floorf(ux);
+    const bool finite = fabsf(uz) < 1.0e6f && fabsf(uy) < 1.0e6f && fabsf(ux) < 1.0e6f;
+    const int iz = z + (finite ? (int)fz : 0), iy = y + (finite ? (int)fy : 0), ix = x + (finite ? (int)fx : 0);
+    const bool inner = finite && (unsigned)iz <= (unsigned)(v.D - 2) && (unsigned)iy <= (unsigned)(v.H - 2) &&
+                       (unsigned)ix <= (unsigned)(v.W - 2);
+    if (__all_sync(__activemask(), inner)) {
+        Cell c;
+        c.iz = iz;
+        c.iy = iy;
+        c.ix = ix;
+        c.tz = uz - fz;
+        c.ty = uy - fy;
+        c.tx = ux - fx;
+        c.cz = c.cy = c.cx = false;
+        c.base = (iz * v.H + iy) * v.W + ix;
+        return c;
+    }
     return make_cell(z, y, x, uz, uy, ux, v);
 }
 

@@ -53,7 +53,7 @@ warp_kernel(const float* __restrict__ I, size_t I_bstride, U u, float* __restric
         if (z >= v.D) break;
         const int l = (z * v.H + y) * v.W + x;
         const float3 d = ub.own(l);
-        const Cell c = make_cell(z, y, x, d.x, d.y, d.z, v);
+        const Cell c = make_cell_warp(z, y, x, d.x, d.y, d.z, v);
         ob[l] = tri(Ib, c, v);
     }
 }
@@ -170,7 +170,7 @@ mse_warp_reg_kernel(const float* __restrict__ I, size_t I_bstride, const float* 
             if (z >= v.D) break;
             const int l = (z * v.H + y) * v.W + x;
             const float3 d3 = ub.own(l);
-            const Cell c = make_cell(z, y, x, d3.x, d3.y, d3.z, v);
+            const Cell c = make_cell_warp(z, y, x, d3.x, d3.y, d3.z, v);
             float dz, dy, dx;
             const float Wv = tri_grad(Ib, c, v, dz, dy, dx);
             const float d = Wv - __ldg(A + l);
